@@ -1,0 +1,153 @@
+"""Seeded synthetic inputs for the DF/CD DSRG-MRPT2 energy.
+
+This module only draws random numbers and lays them out; it holds none of the
+method's arithmetic. Both the CPU oracle and the CUDA library are fed from it.
+
+What is generated (sizes follow the orbital partition of Sec. II.A: core C,
+active A, virtual V; hole space H = C+A, particle space P = A+V; orbital order
+[core | active | virtual]):
+
+* ``B`` -- the hole x particle block of the three-index factors of Eq. (19),
+  ``B[Q, i, a]`` for ``i`` in H and ``a`` in P, shape ``[naux, nH, nP]``, FP64,
+  row-major. Entries are ``b_scale * N(0,1) * exp(-b_decay * Q)``. The factors
+  are symmetric in their two orbital indices, so the active x active sub-block
+  (hole index active, particle index active) is symmetrised: the entry for the
+  orbital pair (u, x) equals the one for (x, u).
+* ``eps`` -- semicanonical orbital energies (diagonal of the generalized Fock
+  matrix, Eq. (8)), shape ``[n]``: core ~ U[-2.0, -0.3], active ~ U[-0.2, 0.1],
+  virtual ~ U[0.05, 5.0] Eh, each block sorted ascending.
+* ``gamma1`` -- spin-summed active one-particle density matrix, ``[nA, nA]``,
+  symmetric, eigenvalues ``1 + d_k`` in [0, 2] with trace nA (half filling),
+  rotated by a seeded Haar-random orthogonal matrix.
+* ``lambda2`` -- the opposite-spin active two-body cumulant
+  ``lambda2[u, v, x, y]`` (u, x alpha; v, y beta), entries ~ U(-0.05, 0.05),
+  averaged over the 8 index permutations of a real (ux|vy)-type tensor.
+
+Random streams come from numpy's PCG64 seeded with ``SeedSequence(seed)``,
+one child stream per tensor, so each tensor is independent of the others'
+sizes only through its own shape.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+__all__ = ["Problem", "make_problem", "CONFIGS", "batch_sizes"]
+
+
+@dataclasses.dataclass
+class Problem:
+    ncore: int
+    nactive: int
+    nvirt: int
+    naux: int
+    s: float
+    B: np.ndarray        # [naux, nH, nP] float64
+    eps: np.ndarray      # [n] float64, order [core | active | virtual]
+    gamma1: np.ndarray   # [nA, nA] float64
+    lambda2: np.ndarray  # [nA, nA, nA, nA] float64
+
+    @property
+    def nhole(self) -> int:
+        return self.ncore + self.nactive
+
+    @property
+    def npart(self) -> int:
+        return self.nactive + self.nvirt
+
+    @property
+    def norb(self) -> int:
+        return self.ncore + self.nactive + self.nvirt
+
+    def scaled(self, factor: float) -> "Problem":
+        """Same problem with B multiplied by ``factor``."""
+        return dataclasses.replace(self, B=self.B * factor)
+
+
+def _haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
+    if n == 0:
+        return np.zeros((0, 0))
+    z = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(z)
+    q = q * np.sign(np.diag(r))[None, :]
+    return q
+
+
+def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5,
+                 seed: int = 0, b_scale: float = 0.3, b_decay: float = 0.02,
+                 occupation: str = "random") -> Problem:
+    """Draw one synthetic problem.
+
+    ``occupation`` selects gamma1: ``"random"`` (the recipe above), ``"full"``
+    (gamma1 = 2 I: the active orbitals doubly occupied) or ``"empty"``
+    (gamma1 = 0). ``lambda2`` is drawn in all cases; callers zero it when a
+    test needs a one-determinant reference.
+    """
+    if min(ncore, nactive, nvirt) < 0 or naux < 1:
+        raise ValueError("sizes must be >= 0 and naux >= 1")
+    ss = np.random.SeedSequence(seed)
+    kids = ss.spawn(5)
+    rB, re, rg, rl, _ = (np.random.Generator(np.random.PCG64(k)) for k in kids)
+    nH, nP = ncore + nactive, nactive + nvirt
+
+    B = rB.standard_normal((naux, nH, nP))
+    if nactive > 0:
+        # active-active sub-block: hole index ncore+u, particle index x.
+        aa = B[:, ncore:, :nactive]
+        iu = np.triu_indices(nactive, 1)
+        # copy the upper triangle over the lower one so (u, x) == (x, u)
+        aa[:, iu[1], iu[0]] = aa[:, iu[0], iu[1]]
+        B[:, ncore:, :nactive] = aa
+    B *= b_scale * np.exp(-b_decay * np.arange(naux, dtype=np.float64))[:, None, None]
+
+    eC = np.sort(re.uniform(-2.0, -0.3, ncore))
+    eA = np.sort(re.uniform(-0.2, 0.1, nactive))
+    eV = np.sort(re.uniform(0.05, 5.0, nvirt))
+    eps = np.concatenate([eC, eA, eV])
+
+    if occupation == "random":
+        d = rg.uniform(-1.0, 1.0, nactive)
+        if nactive > 0:
+            d = d - d.mean()
+            m = np.abs(d).max()
+            if m > 1.0:
+                d = d / m
+        U = _haar_orthogonal(rg, nactive)
+        gamma1 = (U * (1.0 + d)[None, :]) @ U.T
+        gamma1 = 0.5 * (gamma1 + gamma1.T)
+    elif occupation == "full":
+        gamma1 = 2.0 * np.eye(nactive)
+    elif occupation == "empty":
+        gamma1 = np.zeros((nactive, nactive))
+    else:
+        raise ValueError(occupation)
+
+    L = rl.uniform(-0.05, 0.05, (nactive,) * 4)
+    # (ux|vy)-type 8-fold symmetry of L[u, v, x, y]: u<->x, v<->y, (u,x)<->(v,y)
+    perms = []
+    for t in (L, L.transpose(2, 1, 0, 3)):             # u<->x
+        for t2 in (t, t.transpose(0, 3, 2, 1)):         # v<->y
+            perms.append(t2)
+            perms.append(t2.transpose(1, 0, 3, 2))      # (u,x)<->(v,y)
+    lambda2 = sum(perms) / 8.0
+
+    return Problem(ncore, nactive, nvirt, naux, float(s), B, eps, gamma1, lambda2)
+
+
+# The synthetic workloads, by what they stand for (sizes nC/nA/nV/naux, s).
+CONFIGS = {
+    "tiny-74": dict(ncore=10, nactive=4, nvirt=60, naux=200, s=0.5, seed=0),
+    "naphthyne-vtz-398": dict(ncore=24, nactive=2, nvirt=372, naux=1200, s=0.5, seed=0),
+    "naphthyne-v5z-1240": dict(ncore=24, nactive=2, nvirt=1214, naux=3400, s=0.5, seed=0),
+}
+
+
+def batch_sizes(seed: int) -> dict:
+    """Sizes of molecule ``seed`` of the uneven 64-molecule batch: nC ~ U{8..40},
+    nA ~ U{2..6}, nV ~ U{100..600}, naux = round(3.2 * (nC + nA + nV))."""
+    r = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7919])))
+    nC = int(r.integers(8, 41))
+    nA = int(r.integers(2, 7))
+    nV = int(r.integers(100, 601))
+    return dict(ncore=nC, nactive=nA, nvirt=nV, naux=int(round(3.2 * (nC + nA + nV))))

@@ -1,0 +1,158 @@
+/*
+ * dsrg.h -- C ABI of the GB300 (sm_103a) DF/CD DSRG-MRPT2 energy library.
+ *
+ * The library evaluates the second-order DSRG-MRPT2 energy of Hannon, Li and
+ * Evangelista (arXiv:1603.00561) from factorised two-electron integrals:
+ *
+ *   E2(s) = <[H~(1)(s), T(1)(s)]>                      (Sec. II.B, Eq. (11))
+ *
+ * with the first-order amplitudes of Eqs. (12)-(13), the modified Fock and
+ * integrals of Eqs. (14)-(15), the terms of Table 1 (A-I; J and K need the
+ * three-body cumulant, which is not an input, and are 0), and the split of
+ * term F into the diagrams F1-F8 of Table 2. The energy is reported per
+ * block:
+ *
+ *   out[0] = E_CCVV   diagram F1, Eq. (23): sum over core pairs (m,n) and
+ *                     virtual pairs (e,f) of |v_mn^ef|^2 (1-exp(-2sD^2))/D
+ *   out[1] = E_CAVV   diagram F2 (Table 2)
+ *   out[2] = E_CCAV   diagram F3 (Table 2)
+ *   out[3] = E_active terms A-E, G-I (Table 1) and F4-F8 (Table 2)
+ *   out[4] = E_total  the sum of the four blocks
+ *
+ * Problem statement (Sec. II.A, II.B, II.C):
+ *   - orbitals are partitioned into core C (nC), active A (nA) and virtual
+ *     V (nV), ordered [core | active | virtual]; holes H = C+A (nH = nC+nA),
+ *     particles P = A+V (nP = nA+nV);
+ *   - orbitals are semicanonical: eps[p] is the diagonal of the generalized
+ *     Fock matrix (Eq. (8)); the off-diagonal block f^(1) is taken as 0;
+ *   - two-electron integrals are factorised, (pq|rs) = sum_Q B^Q_pq B^Q_rs
+ *     (Eq. (19)); every term reads B only on hole x particle index pairs, so
+ *     the caller passes that block;
+ *   - the reference is a closed-shell-like (singlet, spin-averaged) CAS
+ *     state: gamma1 is the spin-summed active one-particle density matrix G
+ *     (per spin G/2), lambda2[u][v][x][y] is the opposite-spin cumulant
+ *     lambda_{u alpha, v beta}^{x alpha, y beta}; the same-spin blocks are
+ *     L[u,v,x,y] - L[u,v,y,x].
+ *
+ * Conventions of every entry point:
+ *   - array arguments are DEVICE pointers owned by the caller, FP64,
+ *     row-major, contiguous; the library never frees them;
+ *   - B has layout [naux][nH][nP]: B[(Q*nH + i)*nP + a] = B^Q_{i a}, i a
+ *     hole index (0..nC-1 core, nC..nH-1 active), a a particle index
+ *     (0..nA-1 active, nA..nP-1 virtual); eps has length n = nC+nA+nV;
+ *     gamma1 has nA*nA entries and lambda2 nA^4 (both may be NULL if nA == 0);
+ *   - all work is queued on the plan's CUDA stream; energy and gradient calls
+ *     do not allocate and do not synchronise (results land in device memory);
+ *   - errors are returned as dsrg_status_t, never by abort or exception; a
+ *     one-line detail is kept per plan (dsrg_plan_last_error). Conditions
+ *     detected on the device (a bounded wait that ran out) are reported by
+ *     dsrg_plan_sync.
+ */
+#ifndef DSRG_H
+#define DSRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DSRG_OK = 0,
+  DSRG_ERR_INVALID_ARG = 1,  /* bad size, NULL pointer, s < 0, misaligned pointer */
+  DSRG_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  DSRG_ERR_OOM = 3,          /* workspace allocation failed */
+  DSRG_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+  DSRG_ERR_NONFINITE = 5,    /* s is NaN or infinite */
+  DSRG_ERR_UNSUPPORTED = 6   /* size or mode outside what this build supports */
+} dsrg_status_t;
+
+/* Arithmetic of the pair contractions (the v_mn^ef products over Q of
+ * Eq. (19) for diagrams F1 and F2, and the (A,A|V,V) integrals):
+ *   DSRG_PREC_FP64    plain FP64 products and sums on CUDA cores;
+ *   DSRG_PREC_TF32X3  B = hi + lo split into two TF32 planes, products
+ *                     hi*hi + hi*lo + lo*hi on tcgen05 tensor cores with FP32
+ *                     accumulation;
+ *   DSRG_PREC_BF16X3  same with BF16 planes.
+ * In every mode the regulator (Delta, exp(-s Delta^2), the denominator), the
+ * combination with the exchange integral and every sum of energy
+ * contributions are FP64. */
+typedef enum {
+  DSRG_PREC_FP64 = 0,
+  DSRG_PREC_TF32X3 = 1,
+  DSRG_PREC_BF16X3 = 2
+} dsrg_precision_t;
+
+typedef struct {
+  int32_t ncore;    /* nC >= 1 */
+  int32_t nactive;  /* nA >= 0, nA <= 8 */
+  int32_t nvirt;    /* nV >= 1 */
+  int32_t naux;     /* naux >= 1 */
+} dsrg_sizes_t;
+
+/* Plan flags. */
+#define DSRG_PLAN_HOST_IO 1u  /* also allocate device staging for dsrg_mrpt2_energy_host */
+
+typedef struct dsrg_plan dsrg_plan_t;
+
+/* Create a plan for one problem size and precision. Allocates all device
+ * workspace once (sized from *sz), records the stream (a cudaStream_t, NULL =
+ * legacy default stream). Returns DSRG_ERR_OOM if allocation fails and
+ * DSRG_ERR_UNSUPPORTED for sizes this build does not handle; *plan is NULL
+ * on failure. */
+dsrg_status_t dsrg_df_plan(dsrg_plan_t **plan, const dsrg_sizes_t *sz,
+                           dsrg_precision_t prec, void *cuda_stream, uint32_t flags);
+
+/* Free the plan and its workspace (waits for the plan's stream first). NULL is OK. */
+dsrg_status_t dsrg_plan_destroy(dsrg_plan_t *plan);
+
+/* Replace the plan's stream. */
+dsrg_status_t dsrg_plan_set_stream(dsrg_plan_t *plan, void *cuda_stream);
+
+/* Second-order energy by block (see top of file): out_dev[5] on the device.
+ * B [naux][nH][nP], eps [n], gamma1 [nA][nA], lambda2 [nA]^4, s >= 0 (Eh^-2).
+ * Non-finite s -> DSRG_ERR_NONFINITE; NaN in the arrays propagates to out. */
+dsrg_status_t dsrg_mrpt2_energy(dsrg_plan_t *plan, const double *B, const double *eps,
+                                const double *gamma1, const double *lambda2, double s,
+                                double *out_dev);
+
+/* Pair energies of diagram F1 (Eq. (23)): pairs_dev[nC][nC] on the device,
+ * e_mn = sum_ef v_ef (2 v_ef - v_fe) (1-exp(-2 s D^2))/D with v_ef = (me|nf);
+ * their sum is out[0] of dsrg_mrpt2_energy. Same arguments and rules. */
+dsrg_status_t dsrg_ccvv_pair_energies(dsrg_plan_t *plan, const double *B, const double *eps,
+                                      double s, double *pairs_dev);
+
+/* Energy as dsrg_mrpt2_energy, plus the gradient of E_total with respect to
+ * the inputs: dB_dev [naux][nH][nP] (dE/dB^Q_{ia} for the entries as passed),
+ * deps_dev [n], ds_dev [1]. Outputs are overwritten, not accumulated. */
+dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t *plan, const double *B, const double *eps,
+                                     const double *gamma1, const double *lambda2, double s,
+                                     double *out_dev, double *dB_dev, double *deps_dev,
+                                     double *ds_dev);
+
+/* Same as dsrg_mrpt2_energy with HOST inputs and a HOST out[5]: copies the
+ * inputs into plan-owned device staging (plan created with DSRG_PLAN_HOST_IO),
+ * runs, copies the result back and waits for the stream. Pinned host memory
+ * gives the fastest copies. */
+dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t *plan, const double *B_host,
+                                     const double *eps_host, const double *gamma1_host,
+                                     const double *lambda2_host, double s, double *out_host);
+
+/* Wait for the plan's stream and report any device-side condition recorded
+ * since the last call (DSRG_ERR_TIMEOUT), then clear it. */
+dsrg_status_t dsrg_plan_sync(dsrg_plan_t *plan);
+
+/* Number of kernel launches the last energy/gradient call queued. */
+int32_t dsrg_plan_last_launch_count(const dsrg_plan_t *plan);
+
+/* Bytes of device workspace owned by the plan. */
+size_t dsrg_plan_workspace_bytes(const dsrg_plan_t *plan);
+
+const char *dsrg_status_string(dsrg_status_t st);
+const char *dsrg_plan_last_error(const dsrg_plan_t *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSRG_H */
