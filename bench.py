@@ -1,0 +1,363 @@
+"""Benchmark of the DF/CD DSRG-MRPT2 energy on GB300.
+
+One step = the whole second-order energy (every block: CCVV, CAVV, CCAV,
+active) of one synthetic molecule, inputs resident in HBM. Default workload:
+the quintuple-zeta-sized instance (nC=24, nA=2, nV=1214, naux=3400, s=0.5),
+whose B (0.86 GB) is larger than L2, in split precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|bf16x3|fp64]
+    python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Under torchrun each rank computes its own molecule (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CCVV TFLOP/s and E2 wall time per molecule, split-prec vs FP64 at <=1e-7 Eh"
+UNIT = "TFLOP/s"
+WORKLOADS = {
+    "naphthyne-v5z-1240": dict(ncore=24, nactive=2, nvirt=1214, naux=3400, s=0.5),
+    "naphthyne-vtz-398": dict(ncore=24, nactive=2, nvirt=372, naux=1200, s=0.5),
+}
+# nominal dense rates (TFLOP/s) of the recipe, used to scale the measured BF16 peak
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+
+
+def ccvv_flops(nC, nV, Q):
+    """Algorithmic flops of the CCVV pair products: nC(nC+1) Q nV^2 (i<=j pairs, full v)."""
+    return nC * (nC + 1) * Q * nV * nV
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.remove(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle (tier 1, the paper's pair loop) on a bounded sample of
+    the same workload: each step computes the CCVV pair energies of a fixed set
+    of core pairs (both orders) on the host cores."""
+    if rank != 0:
+        return
+    import torch
+
+    from dsrg_synth import make_problem
+    from oracle import dsrg as odsrg
+    cfg = WORKLOADS[args.workload]
+    p = make_problem(seed=0, **cfg)
+    npairs = args.ref_pairs
+    sample = []
+    for k in range(npairs):
+        m = (7 * k) % p.ncore
+        n = (5 * k + 3) % p.ncore
+        if m == n:
+            n = (n + 1) % p.ncore
+        sample += [(m, n), (n, m)]
+    flops = npairs * 2 * p.naux * p.nvirt * p.nvirt  # algorithmic flops of npairs unordered pairs
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample[:2])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    val = flops / t / 1e12
+    cores = torch.get_num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, **cfg, "precision": "fp64-cpu"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"CCVV pair energies of {npairs} core pairs (both orders) per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(workload, seconds=12.0):
+    """Time the oracle's CCVV pair loop on as many core pairs as fit in about
+    `seconds` of host time (each pair computed in both orders, as the oracle does)."""
+    import torch
+
+    from dsrg_synth import make_problem
+    from oracle import dsrg as odsrg
+    cfg = WORKLOADS[workload]
+    p = make_problem(seed=0, **cfg)
+    t0 = time.perf_counter()
+    odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=[(0, 1), (1, 0)])
+    per = time.perf_counter() - t0
+    npairs = max(1, min(p.ncore * (p.ncore - 1) // 2, int(seconds / max(per, 1e-3))))
+    sample = []
+    k = 0
+    for m in range(p.ncore):
+        for n in range(m + 1, p.ncore):
+            if k < npairs:
+                sample += [(m, n), (n, m)]
+                k += 1
+    t0 = time.perf_counter()
+    odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample)
+    dt = time.perf_counter() - t0
+    flops = npairs * 2 * p.naux * p.nvirt * p.nvirt
+    return {"value": flops / dt / 1e12, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"CCVV pair energies of {npairs} core pairs of {workload} (both orders), "
+                      f"{dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    ap.add_argument("--workload", default="naphthyne-v5z-1240", choices=list(WORKLOADS))
+    ap.add_argument("--ref-pairs", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1603_00561_gb300 as pk
+    from dsrg_synth import make_problem
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    pk.build()
+    cfg = WORKLOADS[args.workload]
+    # weak scaling: each rank its own molecule of the same size
+    p = make_problem(seed=rank, **cfg)
+    prec = args.precision
+    try:
+        plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, host_io=True)
+    except pk.DSRGError as e:
+        if prec == "fp64":
+            raise
+        print(f"# {prec} unavailable ({e}); measuring fp64", file=sys.stderr)
+        prec = "fp64"
+        plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, host_io=True)
+    B, eps, g, l = pk.to_device(p)
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.energy(B, eps, g, l, p.s, out=out)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = plan.last_launch_count()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with ClockSampler(local) as cs:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    clocks = cs.summary()
+    t_local = e0.elapsed_time(e1) / 1e3 / args.steps
+    t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_step = float(t.item())
+    energies = out.cpu().numpy().tolist()
+
+    flops = ccvv_flops(p.ncore, p.nvirt, p.naux)
+    value = world * flops / t_step / 1e12
+
+    # dominant kernel: the CCVV pair contraction, timed alone with events on the same stream
+    pairs_out = torch.empty((p.ncore, p.ncore), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        plan.pair_energies(B, eps, p.s, out=pairs_out)
+    nk = max(3, min(args.steps, 10))
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    k0.record(stream)
+    for _ in range(nk):
+        plan.pair_energies(B, eps, p.s, out=pairs_out)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    t_ccvv = k0.elapsed_time(k1) / 1e3 / nk
+    peaks, peak_kind = load_peaks()
+    if prec == "fp64":
+        mult, peak = 1, peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        peak_note = f"bf16 {peak_kind} peak x nominal fp64/bf16 ratio"
+    elif prec == "tf32x3":
+        mult, peak = 3, peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
+        peak_note = f"bf16 {peak_kind} peak x nominal tf32/bf16 ratio; achieved counts 3 MMA products"
+    else:
+        mult, peak = 3, peaks["bf16_tflops"]
+        peak_note = f"bf16 {peak_kind} peak; achieved counts 3 MMA products"
+    achieved = mult * flops / t_ccvv / 1e12
+    roofline = {"bound": "tensor" if prec != "fp64" else "fp64", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "ccvv pair contraction", "ccvv_ms": t_ccvv * 1e3,
+                "algorithmic_tflops": flops / t_ccvv / 1e12, "peak_source": peak_note}
+
+    # end to end through the host-buffer entry: H2D of the inputs and D2H of out[5] each step
+    Bh = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
+    eh = torch.from_numpy(p.eps.copy()).pin_memory()
+    gh = torch.from_numpy(np.ascontiguousarray(p.gamma1)).pin_memory()
+    lh = torch.from_numpy(np.ascontiguousarray(p.lambda2)).pin_memory()
+    oh = torch.zeros(5, dtype=torch.float64).pin_memory()
+    plan.energy_host(Bh, eh, gh, lh, p.s, out=oh)
+    ne2e = max(2, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        plan.energy_host(Bh, eh, gh, lh, p.s, out=oh)
+    t_e2e = (time.perf_counter() - t0) / ne2e
+    te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    t_e2e = float(te.item())
+    h2d = (Bh.numel() + eh.numel() + gh.numel() + lh.numel()) * 8
+
+    # accuracy against the FP64 GPU path, and its E2 time per molecule
+    fp64_cmp = None
+    if prec != "fp64" and not args.no_fp64_compare:
+        p64 = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision="fp64")
+        o64 = p64.energy(B, eps, g, l, p.s)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        p64.energy(B, eps, g, l, p.s, out=o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        r64 = o64.cpu().numpy()
+        fp64_cmp = {"fp64_e2_ms_per_molecule": f0.elapsed_time(f1),
+                    "rel_err_vs_fp64": {k: abs(a - b) / abs(b) if b else abs(a)
+                                        for k, a, b in zip(pk.BLOCKS, energies, r64)},
+                    "abs_err_vs_fp64_eh": {k: abs(a - b) for k, a, b in zip(pk.BLOCKS, energies, r64)}}
+        p64.close()
+
+    if rank == 0:
+        cb = None
+        if not args.no_cpu_baseline and world == 1:
+            cb = cpu_baseline(args.workload)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, **cfg, "precision": prec,
+                       "l2": "inputs larger than L2 (B is 0.86 GB)" if args.workload.endswith("1240")
+                       else "inputs smaller than L2"},
+            "e2_ms_per_molecule": t_step * 1e3,
+            "energies_eh": dict(zip(pk.BLOCKS, energies)),
+            "roofline": roofline,
+            "cpu_baseline": cb,
+            "e2e": {"value": world * flops / t_e2e / 1e12, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 40,
+                    "ms_per_step": t_e2e * 1e3},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        if fp64_cmp:
+            line.update(fp64_cmp)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+"""GB300-native DF/CD DSRG-MRPT2 second-order energy (arXiv:1603.00561).
+
+Thin Python layer over the C ABI of ``libdsrg.so`` (``include/dsrg.h``): it
+passes device pointers of FP64 CUDA tensors and the current CUDA stream, and
+nothing else. Every step of the energy runs in the library's kernels; there
+is no CPU path. Importing the package does not load the library; the first
+``Plan`` does, and fails loudly if it is missing or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _native
+from ._native import DSRGError, PREC
+
+__all__ = ["Plan", "DSRGError", "PREC", "BLOCKS", "build"]
+
+BLOCKS = ("ccvv", "cavv", "ccav", "active", "total")
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    from .build import build as _b
+    return _b(verbose=verbose, force=force)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("arrays must be contiguous float64 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A problem size + precision with its device workspace (``dsrg_df_plan``).
+
+    ``precision``: ``"fp64"``, ``"tf32x3"`` or ``"bf16x3"``.
+    """
+
+    def __init__(self, ncore: int, nactive: int, nvirt: int, naux: int,
+                 precision: str = "fp64", host_io: bool = False, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DSRG-MRPT2 library needs a CUDA GPU")
+        self.lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.sizes = (int(ncore), int(nactive), int(nvirt), int(naux))
+        self.precision = precision
+        sz = _native.Sizes(*self.sizes)
+        h = C.c_void_p()
+        flags = _native.PLAN_HOST_IO if host_io else 0
+        with torch.cuda.device(self.device):
+            st = self.lib.dsrg_df_plan(C.byref(h), C.byref(sz), PREC[precision],
+                                       C.c_void_p(torch.cuda.current_stream().cuda_stream), flags)
+        if st != _native.OK:
+            raise DSRGError(st, f"dsrg_df_plan{self.sizes} {precision}")
+        self.h = h
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != _native.OK:
+            raise DSRGError(st, f"{what}: {self.lib.dsrg_plan_last_error(self.h).decode()}")
+
+    def _stream(self):
+        self.lib.dsrg_plan_set_stream(self.h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    @property
+    def ncore(self):
+        return self.sizes[0]
+
+    @property
+    def nactive(self):
+        return self.sizes[1]
+
+    def last_launch_count(self) -> int:
+        return int(self.lib.dsrg_plan_last_launch_count(self.h))
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.dsrg_plan_workspace_bytes(self.h))
+
+    # -- entry points ------------------------------------------------------------------------
+    def energy(self, B, eps, gamma1, lambda2, s: float, out=None):
+        """Block energies [E_CCVV, E_CAVV, E_CCAV, E_active, E_total] as a device tensor."""
+        if out is None:
+            out = torch.empty(5, dtype=torch.float64, device=self.device)
+        self._stream()
+        st = self.lib.dsrg_mrpt2_energy(self.h, _ptr(B), _ptr(eps), _ptr(gamma1), _ptr(lambda2),
+                                        float(s), _ptr(out))
+        self._check(st, "dsrg_mrpt2_energy")
+        return out
+
+    def pair_energies(self, B, eps, s: float, out=None):
+        """Pair energies e[m, n] of diagram F1 as an [nC, nC] device tensor."""
+        nC = self.ncore
+        if out is None:
+            out = torch.empty((nC, nC), dtype=torch.float64, device=self.device)
+        self._stream()
+        st = self.lib.dsrg_ccvv_pair_energies(self.h, _ptr(B), _ptr(eps), float(s), _ptr(out))
+        self._check(st, "dsrg_ccvv_pair_energies")
+        return out
+
+    def energy_grad(self, B, eps, gamma1, lambda2, s: float):
+        """Energies plus dE_total/dB, dE_total/deps, dE_total/ds (device tensors)."""
+        out = torch.empty(5, dtype=torch.float64, device=self.device)
+        dB = torch.empty_like(B)
+        de = torch.empty_like(eps)
+        ds = torch.empty(1, dtype=torch.float64, device=self.device)
+        self._stream()
+        st = self.lib.dsrg_mrpt2_energy_grad(self.h, _ptr(B), _ptr(eps), _ptr(gamma1),
+                                             _ptr(lambda2), float(s), _ptr(out), _ptr(dB),
+                                             _ptr(de), _ptr(ds))
+        self._check(st, "dsrg_mrpt2_energy_grad")
+        return out, dB, de, ds
+
+    def energy_host(self, B, eps, gamma1, lambda2, s: float, out=None):
+        """Host-buffer entry: numpy/pinned-tensor inputs, host out[5]; synchronises."""
+        import numpy as np
+
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                assert a.device.type == "cpu" and a.dtype == torch.float64 and a.is_contiguous()
+                return C.c_void_p(a.data_ptr())
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            return a.ctypes.data_as(C.c_void_p)
+
+        keep = [np.ascontiguousarray(x, dtype=np.float64) if not isinstance(x, torch.Tensor)
+                and x is not None else x for x in (B, eps, gamma1, lambda2)]
+        if out is None:
+            out = np.zeros(5)
+        outp = out.ctypes.data_as(C.c_void_p) if isinstance(out, np.ndarray) else C.c_void_p(out.data_ptr())
+        self._stream()
+        st = self.lib.dsrg_mrpt2_energy_host(self.h, *[hp(x) for x in keep], float(s), outp)
+        self._check(st, "dsrg_mrpt2_energy_host")
+        return out
+
+    def sync(self):
+        self._check(self.lib.dsrg_plan_sync(self.h), "dsrg_plan_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dsrg_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def to_device(problem, device="cuda"):
+    """Copy a ``dsrg_synth.Problem``'s arrays to FP64 device tensors (B, eps, gamma1, lambda2)."""
+    f = lambda a: torch.as_tensor(a, dtype=torch.float64).contiguous().to(device)
+    g = problem.gamma1 if problem.nactive else None
+    lam = problem.lambda2 if problem.nactive else None
+    return f(problem.B), f(problem.eps), (f(g) if g is not None else None), \
+        (f(lam) if lam is not None else None)

@@ -1,0 +1,76 @@
+"""ctypes declarations of the C ABI in ``include/dsrg.h`` (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdsrg.so")
+
+# dsrg_status_t
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "DSRG_OK", 1: "DSRG_ERR_INVALID_ARG", 2: "DSRG_ERR_CUDA", 3: "DSRG_ERR_OOM",
+                4: "DSRG_ERR_TIMEOUT", 5: "DSRG_ERR_NONFINITE", 6: "DSRG_ERR_UNSUPPORTED"}
+# dsrg_precision_t
+PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+PLAN_HOST_IO = 1
+
+# every exported symbol of include/dsrg.h
+EXPORTS = [
+    "dsrg_df_plan", "dsrg_plan_destroy", "dsrg_plan_set_stream", "dsrg_mrpt2_energy",
+    "dsrg_ccvv_pair_energies", "dsrg_mrpt2_energy_grad", "dsrg_mrpt2_energy_host",
+    "dsrg_plan_sync", "dsrg_plan_last_launch_count", "dsrg_plan_workspace_bytes",
+    "dsrg_status_string", "dsrg_plan_last_error",
+]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("ncore", C.c_int32), ("nactive", C.c_int32), ("nvirt", C.c_int32),
+                ("naux", C.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load ``libdsrg.so`` and declare the signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1603_00561_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, dp, st = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    lib.dsrg_df_plan.argtypes = [C.POINTER(vp), C.POINTER(Sizes), C.c_int, vp, C.c_uint32]
+    lib.dsrg_df_plan.restype = st
+    lib.dsrg_plan_destroy.argtypes = [vp]
+    lib.dsrg_plan_destroy.restype = st
+    lib.dsrg_plan_set_stream.argtypes = [vp, vp]
+    lib.dsrg_plan_set_stream.restype = st
+    lib.dsrg_mrpt2_energy.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp]
+    lib.dsrg_mrpt2_energy.restype = st
+    lib.dsrg_ccvv_pair_energies.argtypes = [vp, vp, vp, C.c_double, vp]
+    lib.dsrg_ccvv_pair_energies.restype = st
+    lib.dsrg_mrpt2_energy_grad.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp]
+    lib.dsrg_mrpt2_energy_grad.restype = st
+    lib.dsrg_mrpt2_energy_host.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp]
+    lib.dsrg_mrpt2_energy_host.restype = st
+    lib.dsrg_plan_sync.argtypes = [vp]
+    lib.dsrg_plan_sync.restype = st
+    lib.dsrg_plan_last_launch_count.argtypes = [vp]
+    lib.dsrg_plan_last_launch_count.restype = C.c_int32
+    lib.dsrg_plan_workspace_bytes.argtypes = [vp]
+    lib.dsrg_plan_workspace_bytes.restype = C.c_size_t
+    lib.dsrg_status_string.argtypes = [C.c_int]
+    lib.dsrg_status_string.restype = C.c_char_p
+    lib.dsrg_plan_last_error.argtypes = [vp]
+    lib.dsrg_plan_last_error.restype = C.c_char_p
+    _ = dp
+    _lib = lib
+    return lib
+
+
+class DSRGError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {detail}")

@@ -1,0 +1,741 @@
+// FP64 kernels for diagram F3 (CCAV) and for the active block of the
+// DSRG-MRPT2 energy: Table 1 terms A-E, G-I and Table 2 diagrams F4-F8.
+//
+// The active block works in spin orbitals (spin orbital 2p + sigma) on the
+// integral blocks that carry at least two active indices, which the paper
+// forms explicitly (Sec. III, steps 4-6):
+//   W1 = <iu||ax>   i in H, u active hole, a in P, x active particle
+//   W2 = <ij||xy>   i, j in H, x, y active particles
+// and the (A,A|V,V) integrals M_xu[e,f] = (xe|uf) in spatial orbitals, whose
+// spin sums P1, P2 feed terms G and F4.
+//
+// Amplitudes and modified integrals (Eqs. (12)-(15)), with D = hole energies
+// minus particle energies: t = v (1 - exp(-s D^2))/D (zero when all four
+// indices are active), vt = v (1 + exp(-s D^2)); the T1 amplitude of Eq. (12)
+// with f^(1) = 0 is t_a^i = S_ia (1 - exp(-s D_ia^2))/D_ia with
+// S_ia = sum_{ux} (e_x - e_u) t_{ax}^{iu} gamma_u^x, and the modified Fock
+// element of Eq. (14) is ft_a^i = S_ia exp(-s D_ia^2); Table 1's ft_j^b is the
+// Hermitian element ft_b^j.
+//
+// Densities (Fig. 1): gamma = 1 on core, G/2 per spin on the active block;
+// eta = 1 - gamma on particles (1 on virtuals). Cumulant from the opposite-
+// spin input L: same spin L[u,v,x,y] - L[u,v,y,x]; (alpha beta|alpha beta)
+// L[u,v,x,y]; (beta alpha|beta alpha) L[v,u,y,x]; (alpha beta|beta alpha)
+// -L[u,v,y,x]; (beta alpha|alpha beta) -L[v,u,x,y].
+#include "internal.cuh"
+#include "regulators.cuh"
+
+namespace dsrg {
+
+// ---------------------------------------------------------------------------
+// F3 (CCAV), spin-adapted:
+//   F3 = sum_{u,v} Hh_uv sum_{m,n,e} Z_v[m,n,e] (2 Z_u[m,n,e] - Z_u[n,m,e])
+//        (1 + exp(-s D_v^2)) (1 - exp(-s D_u^2))/D_u,
+//   Z_u[m,n,e] = (me|nu), D_u = e_m + e_n - e_e - e_u, Hh = 2 I - G.
+// One CTA per virtual e holds Z_u[m,n,e] for all m, n, u in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int KC_CCAV = 8;
+
+__global__ void __launch_bounds__(256) ccav_fp64_kernel(
+    const double* __restrict__ B, const double* __restrict__ eps, const double* __restrict__ G,
+    double s, Sizes z, double* __restrict__ partials) {
+  extern __shared__ double smem[];
+  const int nC = z.nC, nA = z.nA;
+  double* Z = smem;                          // [nA][nC][nC]
+  double* sBe = Z + nA * nC * nC;            // [KC][nC]
+  double* sBu = sBe + KC_CCAV * nC;          // [KC][nC][nA]
+  __shared__ double red[8];
+  const int e = blockIdx.x;
+  const int nz = nA * nC * nC;
+  for (int k = threadIdx.x; k < nz; k += 256) Z[k] = 0.0;
+  for (int q0 = 0; q0 < z.Q; q0 += KC_CCAV) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < KC_CCAV * nC * (1 + nA); k += 256) {
+      const int qq = k / (nC * (1 + nA)), r = k % (nC * (1 + nA)), q = q0 + qq;
+      double v = 0.0;
+      if (r < nC) {
+        if (q < z.Q) v = B[bidx(z, q, r, nA + e)];
+        sBe[qq * nC + r] = v;
+      } else {
+        const int nu = r - nC, n = nu / nA, u = nu % nA;
+        if (q < z.Q) v = B[bidx(z, q, n, u)];
+        sBu[(qq * nC + n) * nA + u] = v;
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nz; k += 256) {
+      const int u = k / (nC * nC), mn = k % (nC * nC), m = mn / nC, n = mn % nC;
+      double acc = Z[k];
+#pragma unroll
+      for (int qq = 0; qq < KC_CCAV; ++qq) acc = fma(sBe[qq * nC + m], sBu[(qq * nC + n) * nA + u], acc);
+      Z[k] = acc;
+    }
+  }
+  __syncthreads();
+  const double ee = eps[nC + nA + e];
+  double acc = 0.0;
+  for (int mn = threadIdx.x; mn < nC * nC; mn += 256) {
+    const int m = mn / nC, n = mn % nC;
+    const double base = eps[m] + eps[n] - ee;
+    double Rv[NA_MAX], Rt[NA_MAX];
+    for (int u = 0; u < nA; ++u) {
+      const double D = base - eps[nC + u];
+      Rv[u] = reg_v(D, s);
+      Rt[u] = reg_t(D, s);
+    }
+    for (int u = 0; u < nA; ++u) {
+      const double zu = 2.0 * Z[(u * nC + m) * nC + n] - Z[(u * nC + n) * nC + m];
+      double c = 0.0;
+      for (int v = 0; v < nA; ++v) {
+        const double Hh = (u == v ? 2.0 : 0.0) - G[u * nA + v];
+        c = fma(Hh * Rv[v], Z[(v * nC + m) * nC + n], c);
+      }
+      acc = fma(c, zu * Rt[u], acc);
+    }
+  }
+  const double tot = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partials[e] = tot;
+}
+
+static size_t ccav_smem(const Sizes& z) {
+  return sizeof(double) * ((size_t)z.nA * z.nC * z.nC + (size_t)KC_CCAV * z.nC * (1 + z.nA));
+}
+
+int ccav_fp64_blocks(const dsrg_plan* p) { return p->z.nA > 0 ? p->z.nV : 0; }
+
+cudaError_t launch_ccav_fp64(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                             double s) {
+  const Segment& sg = p->segs[p->seg_ccav];
+  if (sg.count == 0) return cudaSuccess;
+  const size_t sm = ccav_smem(p->z);
+  cudaFuncSetAttribute(ccav_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ccav_fp64_kernel<<<sg.count, 256, sm, p->stream>>>(B, eps, G, s, p->z,
+                                                     p->d_partials + sg.begin);
+  DSRG_LAUNCH_CHECK(p);
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Active block: tables.
+// ---------------------------------------------------------------------------
+struct ActDims {
+  int nC2, nA2, nH2, nP2, nV2;
+};
+
+__host__ __device__ __forceinline__ ActDims act_dims(const Sizes& z) {
+  return ActDims{2 * z.nC, 2 * z.nA, 2 * z.nH, 2 * z.nP, 2 * z.nV};
+}
+
+// W1 flat index: [I in 2nH][U in 2nA][A in 2nP][X in 2nA]
+__device__ __forceinline__ size_t w1i(const ActDims& d, int I, int U, int A, int X) {
+  return (((size_t)I * d.nA2 + U) * d.nP2 + A) * d.nA2 + X;
+}
+// W2 flat index: [I in 2nH][J in 2nH][X in 2nA][Y in 2nA]
+__device__ __forceinline__ size_t w2i(const ActDims& d, int I, int J, int X, int Y) {
+  return (((size_t)I * d.nH2 + J) * d.nA2 + X) * d.nA2 + Y;
+}
+__device__ __forceinline__ int lami(const ActDims& d, int U, int V, int X, int Y) {
+  return ((U * d.nA2 + V) * d.nA2 + X) * d.nA2 + Y;
+}
+
+// Spatial integrals K1 = (ia|ux), K2 = (ix|ua) [nH][nA][nA][nP], K3 = (ix|jy) [nH][nA][nH][nA].
+__global__ void small_ints_kernel(const double* __restrict__ B, Sizes z, double* __restrict__ K1,
+                                  double* __restrict__ K2, double* __restrict__ K3) {
+  const size_t n12 = (size_t)z.nH * z.nA * z.nA * z.nP;
+  const size_t n3 = (size_t)z.nH * z.nA * z.nH * z.nA;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < 2 * n12) {
+    const bool second = k >= n12;
+    const size_t r = second ? k - n12 : k;
+    const int a = (int)(r % z.nP);
+    const int x = (int)((r / z.nP) % z.nA);
+    const int u = (int)((r / ((size_t)z.nP * z.nA)) % z.nA);
+    const int i = (int)(r / ((size_t)z.nP * z.nA * z.nA));
+    double acc = 0.0;
+    if (!second) {
+      for (int q = 0; q < z.Q; ++q) acc = fma(B[bidx(z, q, i, a)], B[bidx(z, q, z.nC + u, x)], acc);
+      K1[r] = acc;
+    } else {
+      for (int q = 0; q < z.Q; ++q) acc = fma(B[bidx(z, q, i, x)], B[bidx(z, q, z.nC + u, a)], acc);
+      K2[r] = acc;
+    }
+  } else if (k < 2 * n12 + n3) {
+    const size_t r = k - 2 * n12;
+    const int y = (int)(r % z.nA);
+    const int j = (int)((r / z.nA) % z.nH);
+    const int x = (int)((r / ((size_t)z.nA * z.nH)) % z.nA);
+    const int i = (int)(r / ((size_t)z.nA * z.nH * z.nA));
+    double acc = 0.0;
+    for (int q = 0; q < z.Q; ++q) acc = fma(B[bidx(z, q, i, x)], B[bidx(z, q, j, y)], acc);
+    K3[r] = acc;
+  }
+}
+
+// Spin-orbital W1, W2 (V, T, Vt), cumulant and active gamma.
+__global__ void build_tables_kernel(const double* __restrict__ eps, const double* __restrict__ G,
+                                    const double* __restrict__ L, double s, Sizes z,
+                                    const double* __restrict__ K1, const double* __restrict__ K2,
+                                    const double* __restrict__ K3, double* __restrict__ W1,
+                                    double* __restrict__ W2, double* __restrict__ lam,
+                                    double* __restrict__ gA, size_t w1n, size_t w2n) {
+  const ActDims d = act_dims(z);
+  const size_t nl = (size_t)d.nA2 * d.nA2 * d.nA2 * d.nA2;
+  const size_t ng = (size_t)d.nA2 * d.nA2;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < w1n) {
+    const int X = (int)(k % d.nA2);
+    const int A = (int)((k / d.nA2) % d.nP2);
+    const int U = (int)((k / ((size_t)d.nA2 * d.nP2)) % d.nA2);
+    const int I = (int)(k / ((size_t)d.nA2 * d.nP2 * d.nA2));
+    const int i = I >> 1, u = U >> 1, a = A >> 1, x = X >> 1;
+    const int si = I & 1, su = U & 1, sa = A & 1, sx = X & 1;
+    const size_t kk = (((size_t)i * z.nA + u) * z.nA + x) * z.nP + a;
+    double V = 0.0;
+    if (si == sa && su == sx) V += K1[kk];
+    if (si == sx && su == sa) V -= K2[kk];
+    const double D = eps[i] + eps[z.nC + u] - eps[z.nC + a] - eps[z.nC + x];
+    const bool internal = (I >= d.nC2) && (A < d.nA2);
+    W1[k] = V;
+    W1[w1n + k] = internal ? 0.0 : V * reg_t(D, s);
+    W1[2 * w1n + k] = V * reg_v(D, s);
+  } else if (k < w1n + w2n) {
+    const size_t r = k - w1n;
+    const int Y = (int)(r % d.nA2);
+    const int X = (int)((r / d.nA2) % d.nA2);
+    const int J = (int)((r / ((size_t)d.nA2 * d.nA2)) % d.nH2);
+    const int I = (int)(r / ((size_t)d.nA2 * d.nA2 * d.nH2));
+    const int i = I >> 1, j = J >> 1, x = X >> 1, y = Y >> 1;
+    const int si = I & 1, sj = J & 1, sx = X & 1, sy = Y & 1;
+    double V = 0.0;
+    if (si == sx && sj == sy) V += K3[(((size_t)i * z.nA + x) * z.nH + j) * z.nA + y];
+    if (si == sy && sj == sx) V -= K3[(((size_t)i * z.nA + y) * z.nH + j) * z.nA + x];
+    const double D = eps[i] + eps[j] - eps[z.nC + x] - eps[z.nC + y];
+    const bool internal = (I >= d.nC2) && (J >= d.nC2);
+    W2[r] = V;
+    W2[w2n + r] = internal ? 0.0 : V * reg_t(D, s);
+    W2[2 * w2n + r] = V * reg_v(D, s);
+  } else if (k < w1n + w2n + nl) {
+    const int r = (int)(k - w1n - w2n);
+    const int Y = r % d.nA2, X = (r / d.nA2) % d.nA2, V = (r / (d.nA2 * d.nA2)) % d.nA2,
+              U = r / (d.nA2 * d.nA2 * d.nA2);
+    const int u = U >> 1, v = V >> 1, x = X >> 1, y = Y >> 1;
+    const int su = U & 1, sv = V & 1, sx = X & 1, sy = Y & 1;
+    const int nA = z.nA;
+    auto Lf = [&](int p0, int p1, int p2, int p3) { return L[((p0 * nA + p1) * nA + p2) * nA + p3]; };
+    double val = 0.0;
+    if (su == sv && sv == sx && sx == sy) {
+      val = Lf(u, v, x, y) - Lf(u, v, y, x);
+    } else if (su == sx && sv == sy) {
+      val = (su == 0) ? Lf(u, v, x, y) : Lf(v, u, y, x);
+    } else if (su == sy && sv == sx) {
+      val = (su == 0) ? -Lf(u, v, y, x) : -Lf(v, u, x, y);
+    }
+    lam[r] = val;
+  } else if (k < w1n + w2n + nl + ng) {
+    const int r = (int)(k - w1n - w2n - nl);
+    const int U = r / d.nA2, V = r % d.nA2;
+    gA[r] = ((U & 1) == (V & 1)) ? 0.5 * G[(U >> 1) * z.nA + (V >> 1)] : 0.0;
+  }
+}
+
+// T1 amplitudes and modified Fock elements over spin orbitals [2nH][2nP].
+__global__ void t1_kernel(const double* __restrict__ eps, double s, Sizes z,
+                          const double* __restrict__ W1T, const double* __restrict__ gA,
+                          double* __restrict__ t1, double* __restrict__ ft) {
+  const ActDims d = act_dims(z);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.nH2 * d.nP2) return;
+  const int I = k / d.nP2, A = k % d.nP2;
+  double S = 0.0;
+  for (int U = 0; U < d.nA2; ++U)
+    for (int X = 0; X < d.nA2; ++X) {
+      const double g = gA[U * d.nA2 + X];
+      if (g == 0.0) continue;
+      const double Dux = eps[z.nC + (X >> 1)] - eps[z.nC + (U >> 1)];
+      S = fma(Dux * g, W1T[w1i(d, I, U, A, X)], S);
+    }
+  const double D1 = eps[I >> 1] - eps[z.nC + (A >> 1)];
+  const bool internal = (I >= d.nC2) && (A < d.nA2);
+  t1[k] = internal ? 0.0 : S * reg_t(D1, s);
+  ft[k] = S * exp(-s * D1 * D1);
+}
+
+// gamma (over holes) and eta (over particles) as sparse row lookups.
+__device__ __forceinline__ double gam_h(const ActDims& d, const double* gA, int K, int I) {
+  if (K < d.nC2 || I < d.nC2) return (K == I) ? 1.0 : 0.0;
+  return gA[(K - d.nC2) * d.nA2 + (I - d.nC2)];
+}
+__device__ __forceinline__ double eta_p(const ActDims& d, const double* gA, int A, int Bp) {
+  if (A >= d.nA2 || Bp >= d.nA2) return (A == Bp) ? 1.0 : 0.0;
+  return (A == Bp ? 1.0 : 0.0) - gA[A * d.nA2 + Bp];
+}
+
+// Ti[J][V][B][Y] = sum_{I,A} gamma_I^J eta_B^A t_{AY}^{IV}  (the dressed T of term I).
+__global__ void ti_kernel(Sizes z, const double* __restrict__ W1T, const double* __restrict__ gA,
+                          double* __restrict__ Ti, size_t w1n) {
+  const ActDims d = act_dims(z);
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= w1n) return;
+  const int Y = (int)(k % d.nA2);
+  const int Bp = (int)((k / d.nA2) % d.nP2);
+  const int V = (int)((k / ((size_t)d.nA2 * d.nP2)) % d.nA2);
+  const int J = (int)(k / ((size_t)d.nA2 * d.nP2 * d.nA2));
+  const int i0 = (J < d.nC2) ? J : d.nC2, i1 = (J < d.nC2) ? J + 1 : d.nH2;
+  const int a0 = (Bp < d.nA2) ? 0 : Bp, a1 = (Bp < d.nA2) ? d.nA2 : Bp + 1;
+  double acc = 0.0;
+  for (int I = i0; I < i1; ++I) {
+    const double g = gam_h(d, gA, J, I);
+    if (g == 0.0) continue;
+    for (int A = a0; A < a1; ++A) acc = fma(g * eta_p(d, gA, A, Bp), W1T[w1i(d, I, V, A, Y)], acc);
+  }
+  Ti[k] = acc;
+}
+
+// (A,A|V,V) integrals M[x][u][e][f] = (xe|uf), 64x64 tiles, FP64.
+__global__ void __launch_bounds__(256) gram_aavv_kernel(const double* __restrict__ B, Sizes z,
+                                                       int ntile, double* __restrict__ M) {
+  __shared__ double sX[16][64], sU[16][64];
+  const int nT2 = ntile * ntile;
+  const int xu = blockIdx.x / nT2, t = blockIdx.x % nT2;
+  const int x = xu / z.nA, u = xu % z.nA;
+  const int e0 = (t / ntile) * 64, f0 = (t % ntile) * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int q0 = 0; q0 < z.Q; q0 += 16) {
+    for (int k = threadIdx.x; k < 16 * 64; k += 256) {
+      const int qq = k / 64, c = k % 64, q = q0 + qq;
+      const int e = e0 + c, f = f0 + c;
+      sX[qq][c] = (q < z.Q && e < z.nV) ? B[bidx(z, q, z.nC + x, z.nA + e)] : 0.0;
+      sU[qq][c] = (q < z.Q && f < z.nV) ? B[bidx(z, q, z.nC + u, z.nA + f)] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int qq = 0; qq < 16; ++qq) {
+      double ra[4], rb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        ra[r] = sX[qq][ty * 4 + r];
+        rb[r] = sU[qq][tx * 4 + r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(ra[r], rb[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  const size_t base = (size_t)xu * z.nV * z.nV;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int e = e0 + ty * 4 + r;
+    if (e >= z.nV) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int f = f0 + tx * 4 + c;
+      if (f < z.nV) M[base + (size_t)e * z.nV + f] = acc[r][c];
+    }
+  }
+}
+
+// P1[xu][yv] = sum_ef M_xu[ef] M_yv[ef] R, P2[xu][yv] = sum_ef M_xu[ef] M_vy[ef] R
+// (M_vy[e,f] = M_yv[f,e]) with R = (1 + exp(-s D_xu^2)) (1 - exp(-s D_yv^2))/D_yv.
+constexpr int ACTVV_BLOCKS = 48;
+
+__global__ void __launch_bounds__(256) actvv_kernel(const double* __restrict__ eps, double s,
+                                                    Sizes z, const double* __restrict__ M,
+                                                    double* __restrict__ part) {
+  __shared__ double red[8];
+  const int nA = z.nA, nA4 = nA * nA * nA * nA;
+  const int c = blockIdx.y;
+  const int v = c % nA, y = (c / nA) % nA, u = (c / (nA * nA)) % nA, x = c / (nA * nA * nA);
+  const size_t nV2 = (size_t)z.nV * z.nV;
+  const double* Mxu = M + (size_t)(x * nA + u) * nV2;
+  const double* Myv = M + (size_t)(y * nA + v) * nV2;
+  const double* Mvy = M + (size_t)(v * nA + y) * nV2;
+  const int ve = z.nC + z.nA;
+  const double Exu = eps[z.nC + x] + eps[z.nC + u], Eyv = eps[z.nC + y] + eps[z.nC + v];
+  double p1 = 0.0, p2 = 0.0;
+  for (size_t k = (size_t)blockIdx.x * 256 + threadIdx.x; k < nV2; k += (size_t)gridDim.x * 256) {
+    const int e = (int)(k / z.nV), f = (int)(k % z.nV);
+    const double ef = eps[ve + e] + eps[ve + f];
+    const double R = reg_v(Exu - ef, s) * reg_t(Eyv - ef, s);
+    const double m = Mxu[k] * R;
+    p1 = fma(m, Myv[k], p1);
+    p2 = fma(m, Mvy[k], p2);
+  }
+  const double t1 = block_sum<256>(p1, red);
+  const double t2 = block_sum<256>(p2, red);
+  if (threadIdx.x == 0) {
+    part[((size_t)blockIdx.x * 2 + 0) * nA4 + c] = t1;
+    part[((size_t)blockIdx.x * 2 + 1) * nA4 + c] = t2;
+  }
+}
+
+__global__ void actvv_reduce_kernel(int nA4, int nblk, const double* __restrict__ part,
+                                    double* __restrict__ P12) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 2 * nA4) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * 2 * nA4 + k];
+  P12[k] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Active block: one kernel, one term per blockIdx.y, one outer index per thread.
+// ---------------------------------------------------------------------------
+enum Term {
+  T_A = 0, T_B, T_C, T_D, T_E, T_GVA, T_GVV, T_H, T_I, T_F4, T_F5, T_F6, T_F7, T_F8, N_TERMS
+};
+
+struct TermArgs {
+  const double *W1V, *W1T, *W1Vt, *W2V, *W2T, *W2Vt, *Ti, *lam, *gA, *t1, *ft, *P12;
+};
+
+__device__ __forceinline__ double ga(const ActDims& d, const double* gA, int U, int V) {
+  return gA[U * d.nA2 + V];
+}
+__device__ __forceinline__ double ea(const ActDims& d, const double* gA, int U, int V) {
+  return (U == V ? 1.0 : 0.0) - gA[U * d.nA2 + V];
+}
+
+// S[(X,U),(Y,V)] = sum_{E,F} vt_{XU}^{EF} t_{EF}^{YV} over virtual spin orbitals.
+__device__ __forceinline__ double s_vv(const ActDims& d, int nA, const double* P12, int X, int U,
+                                       int Y, int V) {
+  const int nA4 = nA * nA * nA * nA;
+  const int c = (((X >> 1) * nA + (U >> 1)) * nA + (Y >> 1)) * nA + (V >> 1);
+  double r = 0.0;
+  if ((X & 1) == (Y & 1) && (U & 1) == (V & 1)) r += 2.0 * P12[c];
+  if ((X & 1) == (V & 1) && (U & 1) == (Y & 1)) r -= 2.0 * P12[nA4 + c];
+  return r;
+}
+
+__device__ double term_value(int term, long o, const Sizes& z, const ActDims& d,
+                             const TermArgs& t) {
+  const int nA2 = d.nA2;
+  double acc = 0.0;
+  switch (term) {
+    case T_A: {  // ft_j^b t_a^i gamma_i^j eta_b^a, outer (J, Bp)
+      if (o >= (long)d.nH2 * d.nP2) return 0.0;
+      const int J = (int)(o / d.nP2), Bp = (int)(o % d.nP2);
+      double gf = 0.0, te = 0.0;
+      const int k0 = (J < d.nC2) ? J : d.nC2, k1 = (J < d.nC2) ? J + 1 : d.nH2;
+      for (int K = k0; K < k1; ++K) gf = fma(gam_h(d, t.gA, J, K), t.ft[(size_t)K * d.nP2 + Bp], gf);
+      const int a0 = (Bp < nA2) ? 0 : Bp, a1 = (Bp < nA2) ? nA2 : Bp + 1;
+      for (int A = a0; A < a1; ++A) te = fma(eta_p(d, t.gA, A, Bp), t.t1[(size_t)J * d.nP2 + A], te);
+      return gf * te;
+    }
+    case T_B: {  // 1/2 vt_{xy}^{ev} t_e^u lambda_{uv}^{xy}, outer E (virtual)
+      if (o >= d.nV2) return 0.0;
+      const int Ap = nA2 + (int)o;
+      for (int X = 0; X < nA2; ++X)
+        for (int Y = 0; Y < nA2; ++Y)
+          for (int V = 0; V < nA2; ++V) {
+            const double vt = t.W1Vt[w1i(d, d.nC2 + X, Y, Ap, V)];
+            if (vt == 0.0) continue;
+            for (int U = 0; U < nA2; ++U)
+              acc = fma(vt * t.t1[(size_t)(d.nC2 + U) * d.nP2 + Ap], t.lam[lami(d, U, V, X, Y)], acc);
+          }
+      return 0.5 * acc;
+    }
+    case T_C: {  // -1/2 vt_{my}^{uv} t_x^m lambda_{uv}^{xy}, outer M (core)
+      if (o >= d.nC2) return 0.0;
+      const int M = (int)o;
+      for (int Y = 0; Y < nA2; ++Y)
+        for (int U = 0; U < nA2; ++U)
+          for (int V = 0; V < nA2; ++V) {
+            const double vt = t.W1Vt[w1i(d, M, Y, U, V)];
+            if (vt == 0.0) continue;
+            for (int X = 0; X < nA2; ++X)
+              acc = fma(vt * t.t1[(size_t)M * d.nP2 + X], t.lam[lami(d, U, V, X, Y)], acc);
+          }
+      return -0.5 * acc;
+    }
+    case T_D: {  // 1/2 ft_x^e t_{ey}^{uv} lambda_{uv}^{xy}, outer E
+      if (o >= d.nV2) return 0.0;
+      const int Ap = nA2 + (int)o;
+      for (int U = 0; U < nA2; ++U)
+        for (int V = 0; V < nA2; ++V)
+          for (int Y = 0; Y < nA2; ++Y) {
+            const double tt = t.W1T[w1i(d, d.nC2 + U, V, Ap, Y)];
+            if (tt == 0.0) continue;
+            for (int X = 0; X < nA2; ++X)
+              acc = fma(tt * t.ft[(size_t)(d.nC2 + X) * d.nP2 + Ap], t.lam[lami(d, U, V, X, Y)], acc);
+          }
+      return 0.5 * acc;
+    }
+    case T_E: {  // -1/2 ft_m^v t_{xy}^{um} lambda_{uv}^{xy}, outer M
+      if (o >= d.nC2) return 0.0;
+      const int M = (int)o;
+      for (int U = 0; U < nA2; ++U)
+        for (int X = 0; X < nA2; ++X)
+          for (int Y = 0; Y < nA2; ++Y) {
+            const double tt = t.W2T[w2i(d, d.nC2 + U, M, X, Y)];
+            if (tt == 0.0) continue;
+            for (int V = 0; V < nA2; ++V)
+              acc = fma(tt * t.ft[(size_t)M * d.nP2 + V], t.lam[lami(d, U, V, X, Y)], acc);
+          }
+      return -0.5 * acc;
+    }
+    case T_GVA: {  // G with one virtual and one active particle, outer E
+      if (o >= d.nV2) return 0.0;
+      const int Ap = nA2 + (int)o;
+      for (int U = 0; U < nA2; ++U)
+        for (int V = 0; V < nA2; ++V)
+          for (int C = 0; C < nA2; ++C) {
+            double tg = 0.0;  // sum_a eta_c^a t_{a e}^{uv}, with the particle pair reversed
+            for (int A = 0; A < nA2; ++A)
+              tg = fma(ea(d, t.gA, C, A), t.W1T[w1i(d, d.nC2 + U, V, Ap, A)], tg);
+            if (tg == 0.0) continue;
+            for (int X = 0; X < nA2; ++X)
+              for (int Y = 0; Y < nA2; ++Y)
+                acc = fma(t.W1Vt[w1i(d, d.nC2 + X, Y, Ap, C)] * tg, t.lam[lami(d, U, V, X, Y)], acc);
+          }
+      return 0.25 * acc;
+    }
+    case T_GVV: {  // G with two virtual particles, outer (X, Y, U, V)
+      if (o >= (long)nA2 * nA2 * nA2 * nA2) return 0.0;
+      const int V = (int)(o % nA2), U = (int)((o / nA2) % nA2), Y = (int)((o / (nA2 * nA2)) % nA2),
+                X = (int)(o / (nA2 * nA2 * nA2));
+      return 0.125 * t.lam[lami(d, U, V, X, Y)] * s_vv(d, z.nA, t.P12, X, Y, U, V);
+    }
+    case T_H: {  // 1/8 vt_{kl}^{uv} t_{xy}^{ij} gamma_i^k gamma_j^l lambda_{uv}^{xy}, outer (K, L)
+      if (o >= (long)d.nH2 * d.nH2) return 0.0;
+      const int K = (int)(o / d.nH2), L = (int)(o % d.nH2);
+      const int i0 = (K < d.nC2) ? K : d.nC2, i1 = (K < d.nC2) ? K + 1 : d.nH2;
+      const int j0 = (L < d.nC2) ? L : d.nC2, j1 = (L < d.nC2) ? L + 1 : d.nH2;
+      for (int X = 0; X < nA2; ++X)
+        for (int Y = 0; Y < nA2; ++Y) {
+          double th = 0.0;
+          for (int I = i0; I < i1; ++I)
+            for (int J = j0; J < j1; ++J)
+              th = fma(gam_h(d, t.gA, K, I) * gam_h(d, t.gA, L, J), t.W2T[w2i(d, I, J, X, Y)], th);
+          if (th == 0.0) continue;
+          for (int U = 0; U < nA2; ++U)
+            for (int V = 0; V < nA2; ++V)
+              acc = fma(t.W2Vt[w2i(d, K, L, U, V)] * th, t.lam[lami(d, U, V, X, Y)], acc);
+        }
+      return 0.125 * acc;
+    }
+    case T_I: {  // vt_{jx}^{bu} t_{ay}^{iv} gamma_i^j eta_b^a lambda_{uv}^{xy}, outer (J, Bp)
+      if (o >= (long)d.nH2 * d.nP2) return 0.0;
+      const int J = (int)(o / d.nP2), Bp = (int)(o % d.nP2);
+      for (int U = 0; U < nA2; ++U)
+        for (int X = 0; X < nA2; ++X) {
+          const double vt = t.W1Vt[w1i(d, J, X, Bp, U)];
+          if (vt == 0.0) continue;
+          double c = 0.0;
+          for (int V = 0; V < nA2; ++V)
+            for (int Y = 0; Y < nA2; ++Y) c = fma(t.Ti[w1i(d, J, V, Bp, Y)], t.lam[lami(d, U, V, X, Y)], c);
+          acc = fma(vt, c, acc);
+        }
+      return acc;
+    }
+    case T_F4: {  // 1/4 vt_{xu}^{ef} t_{ef}^{yv} gamma_y^x gamma_v^u, outer (X, U, Y, V)
+      if (o >= (long)nA2 * nA2 * nA2 * nA2) return 0.0;
+      const int V = (int)(o % nA2), Y = (int)((o / nA2) % nA2), U = (int)((o / (nA2 * nA2)) % nA2),
+                X = (int)(o / (nA2 * nA2 * nA2));
+      return 0.25 * ga(d, t.gA, X, Y) * ga(d, t.gA, U, V) * s_vv(d, z.nA, t.P12, X, U, Y, V);
+    }
+    case T_F5: {  // 1/4 vt_{mn}^{vy} t_{ux}^{mn} eta_v^u eta_y^x, outer (M, N)
+      if (o >= (long)d.nC2 * d.nC2) return 0.0;
+      const int M = (int)(o / d.nC2), N = (int)(o % d.nC2);
+      for (int V = 0; V < nA2; ++V)
+        for (int Y = 0; Y < nA2; ++Y) {
+          const double vt = t.W2Vt[w2i(d, M, N, V, Y)];
+          if (vt == 0.0) continue;
+          for (int U = 0; U < nA2; ++U)
+            for (int X = 0; X < nA2; ++X)
+              acc = fma(vt * ea(d, t.gA, U, V) * ea(d, t.gA, X, Y), t.W2T[w2i(d, M, N, U, X)], acc);
+        }
+      return 0.25 * acc;
+    }
+    case T_F6: {  // vt_{mx}^{ve} t_{ue}^{my} gamma_y^x eta_v^u, outer (M, E)
+      if (o >= (long)d.nC2 * d.nV2) return 0.0;
+      const int M = (int)(o / d.nV2), Ap = nA2 + (int)(o % d.nV2);
+      for (int X = 0; X < nA2; ++X)
+        for (int V = 0; V < nA2; ++V) {
+          const double vt = t.W1Vt[w1i(d, M, X, Ap, V)];
+          if (vt == 0.0) continue;
+          for (int Y = 0; Y < nA2; ++Y)
+            for (int U = 0; U < nA2; ++U)
+              acc = fma(vt * ga(d, t.gA, X, Y) * ea(d, t.gA, U, V), t.W1T[w1i(d, M, Y, Ap, U)], acc);
+        }
+      return acc;
+    }
+    case T_F7: {  // 1/2 vt_{yz}^{ve} t_{ue}^{wx} gamma_w^y gamma_x^z eta_v^u, outer E
+      if (o >= d.nV2) return 0.0;
+      const int Ap = nA2 + (int)o;
+      for (int Y = 0; Y < nA2; ++Y)
+        for (int Z = 0; Z < nA2; ++Z)
+          for (int V = 0; V < nA2; ++V) {
+            const double vt = t.W1Vt[w1i(d, d.nC2 + Y, Z, Ap, V)];
+            if (vt == 0.0) continue;
+            for (int W = 0; W < nA2; ++W)
+              for (int X = 0; X < nA2; ++X) {
+                const double gg = ga(d, t.gA, Y, W) * ga(d, t.gA, Z, X);
+                if (gg == 0.0) continue;
+                for (int U = 0; U < nA2; ++U)
+                  acc = fma(vt * gg * ea(d, t.gA, U, V), t.W1T[w1i(d, d.nC2 + W, X, Ap, U)], acc);
+              }
+          }
+      return 0.5 * acc;
+    }
+    case T_F8: {  // 1/2 vt_{mw}^{vy} t_{ux}^{mz} gamma_z^w eta_v^u eta_y^x, outer M
+      if (o >= d.nC2) return 0.0;
+      const int M = (int)o;
+      for (int W = 0; W < nA2; ++W)
+        for (int V = 0; V < nA2; ++V)
+          for (int Y = 0; Y < nA2; ++Y) {
+            const double vt = t.W1Vt[w1i(d, M, W, V, Y)];
+            if (vt == 0.0) continue;
+            for (int Z = 0; Z < nA2; ++Z) {
+              const double g = ga(d, t.gA, W, Z);
+              if (g == 0.0) continue;
+              for (int U = 0; U < nA2; ++U)
+                for (int X = 0; X < nA2; ++X)
+                  acc = fma(vt * g * ea(d, t.gA, U, V) * ea(d, t.gA, X, Y), t.W1T[w1i(d, M, Z, U, X)],
+                            acc);
+            }
+          }
+      return 0.5 * acc;
+    }
+  }
+  return 0.0;
+}
+
+constexpr int TERM_NT = 128;
+
+__global__ void __launch_bounds__(TERM_NT) terms_kernel(Sizes z, TermArgs t,
+                                                        double* __restrict__ partials) {
+  __shared__ double red[TERM_NT / 32];
+  const ActDims d = act_dims(z);
+  const long o = (long)blockIdx.x * TERM_NT + threadIdx.x;
+  const double v = term_value(blockIdx.y, o, z, d, t);
+  const double tot = block_sum<TERM_NT>(v, red);
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+static long term_outer_max(const Sizes& z) {
+  const ActDims d = act_dims(z);
+  long m = (long)d.nH2 * d.nP2;
+  m = m > (long)d.nH2 * d.nH2 ? m : (long)d.nH2 * d.nH2;
+  m = m > (long)d.nC2 * d.nV2 ? m : (long)d.nC2 * d.nV2;
+  const long a4 = (long)d.nA2 * d.nA2 * d.nA2 * d.nA2;
+  return m > a4 ? m : a4;
+}
+
+static int term_blocks(const Sizes& z) { return (int)((term_outer_max(z) + TERM_NT - 1) / TERM_NT); }
+
+bool active_alloc(dsrg_plan* p) {
+  const Sizes& z = p->z;
+  if (z.nA == 0) return true;
+  const ActDims d = act_dims(z);
+  ActiveWs& w = p->act;
+  w.w1n = (size_t)d.nH2 * d.nA2 * d.nP2 * d.nA2;
+  w.w2n = (size_t)d.nH2 * d.nH2 * d.nA2 * d.nA2;
+  const size_t n12 = (size_t)z.nH * z.nA * z.nA * z.nP;
+  const size_t n3 = (size_t)z.nH * z.nA * z.nH * z.nA;
+  const size_t nA4 = (size_t)z.nA * z.nA * z.nA * z.nA;
+  w.actvv_blocks = ACTVV_BLOCKS;
+  bool ok = true;
+  ok = ok && plan_alloc(p, (void**)&w.K1, n12 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.K2, n12 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.K3, n3 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.W1, 3 * w.w1n * 8);
+  ok = ok && plan_alloc(p, (void**)&w.W2, 3 * w.w2n * 8);
+  ok = ok && plan_alloc(p, (void**)&w.Ti, w.w1n * 8);
+  ok = ok && plan_alloc(p, (void**)&w.lam, (size_t)d.nA2 * d.nA2 * d.nA2 * d.nA2 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.gA, (size_t)d.nA2 * d.nA2 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.t1, (size_t)d.nH2 * d.nP2 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.ft, (size_t)d.nH2 * d.nP2 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.M, (size_t)z.nA * z.nA * z.nV * z.nV * 8);
+  ok = ok && plan_alloc(p, (void**)&w.P12, 2 * nA4 * 8);
+  ok = ok && plan_alloc(p, (void**)&w.P12part, (size_t)ACTVV_BLOCKS * 2 * nA4 * 8);
+  return ok;
+}
+
+int active_plan(dsrg_plan* p, int first_partial) {
+  if (p->z.nA == 0) return 0;
+  const int nb = term_blocks(p->z) * N_TERMS;
+  p->segs.push_back(Segment{first_partial, nb, BLK_ACTIVE});
+  p->seg_active.push_back((int)p->segs.size() - 1);
+  return nb;
+}
+
+cudaError_t launch_gram_aavv_fp64(dsrg_plan* p, const double* B) {
+  const Sizes& z = p->z;
+  if (z.nA == 0) return cudaSuccess;
+  const int nt = (z.nV + 63) / 64;
+  gram_aavv_kernel<<<z.nA * z.nA * nt * nt, 256, 0, p->stream>>>(B, z, nt, p->act.M);
+  DSRG_LAUNCH_CHECK(p);
+  return cudaSuccess;
+}
+
+cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                          const double* L, double s, bool gram_done) {
+  const Sizes& z = p->z;
+  if (z.nA == 0) return cudaSuccess;
+  ActiveWs& w = p->act;
+  const ActDims d = act_dims(z);
+  cudaStream_t st = p->stream;
+  {
+    const size_t n = 2 * (size_t)z.nH * z.nA * z.nA * z.nP + (size_t)z.nH * z.nA * z.nH * z.nA;
+    small_ints_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(B, z, w.K1, w.K2, w.K3);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const size_t n = w.w1n + w.w2n + (size_t)d.nA2 * d.nA2 * d.nA2 * d.nA2 + (size_t)d.nA2 * d.nA2;
+    build_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        eps, G, L, s, z, w.K1, w.K2, w.K3, w.W1, w.W2, w.lam, w.gA, w.w1n, w.w2n);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const int n = d.nH2 * d.nP2;
+    t1_kernel<<<(n + 255) / 256, 256, 0, st>>>(eps, s, z, w.W1 + w.w1n, w.gA, w.t1, w.ft);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    ti_kernel<<<(unsigned)((w.w1n + 255) / 256), 256, 0, st>>>(z, w.W1 + w.w1n, w.gA, w.Ti, w.w1n);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  if (!gram_done) {
+    cudaError_t e = launch_gram_aavv_fp64(p, B);
+    if (e != cudaSuccess) return e;
+  }
+  const int nA4 = z.nA * z.nA * z.nA * z.nA;
+  {
+    dim3 grid(ACTVV_BLOCKS, nA4);
+    actvv_kernel<<<grid, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+    DSRG_LAUNCH_CHECK(p);
+    actvv_reduce_kernel<<<(2 * nA4 + 127) / 128, 128, 0, st>>>(nA4, ACTVV_BLOCKS, w.P12part, w.P12);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    TermArgs ta;
+    ta.W1V = w.W1;
+    ta.W1T = w.W1 + w.w1n;
+    ta.W1Vt = w.W1 + 2 * w.w1n;
+    ta.W2V = w.W2;
+    ta.W2T = w.W2 + w.w2n;
+    ta.W2Vt = w.W2 + 2 * w.w2n;
+    ta.Ti = w.Ti;
+    ta.lam = w.lam;
+    ta.gA = w.gA;
+    ta.t1 = w.t1;
+    ta.ft = w.ft;
+    ta.P12 = w.P12;
+    const Segment& sg = p->segs[p->seg_active[0]];
+    dim3 grid(term_blocks(z), N_TERMS);
+    terms_kernel<<<grid, TERM_NT, 0, st>>>(z, ta, p->d_partials + sg.begin);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  return cudaSuccess;
+}
+
+bool ccav_supported(const Sizes& z) { return ccav_smem(z) <= 200 * 1024; }
+
+}  // namespace dsrg

@@ -1,0 +1,320 @@
+// C ABI of the DSRG-MRPT2 library: plans, argument checks, dispatch.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace dsrg {
+bool ccav_supported(const Sizes& z);
+
+// Allocation-failure injection for tests: DSRG_FAIL_ALLOC_AFTER=k makes the
+// (k+1)-th device allocation of a plan fail as if the device were full.
+static int fail_after() {
+  const char* e = std::getenv("DSRG_FAIL_ALLOC_AFTER");
+  return e ? std::atoi(e) : -1;
+}
+
+bool plan_alloc(dsrg_plan* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 8;
+  const int fa = fail_after();
+  if (fa >= 0 && (int)p->allocs.size() >= fa) return false;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return false;
+  }
+  p->allocs.push_back(*ptr);
+  p->ws_bytes += bytes;
+  return true;
+}
+
+static void tile_pairs(int n, int tile, std::vector<int2>& out) {
+  const int nt = (n + tile - 1) / tile;
+  out.clear();
+  for (int a = 0; a < nt; ++a)
+    for (int b = a; b < nt; ++b) out.push_back(make_int2(a, b));
+}
+
+}  // namespace dsrg
+
+using namespace dsrg;
+
+static dsrg_status_t fail(dsrg_plan* p, dsrg_status_t st, const std::string& msg) {
+  if (p) p->last_error = msg;
+  return st;
+}
+
+static dsrg_status_t cuda_fail(dsrg_plan* p, cudaError_t e, const char* where) {
+  return fail(p, DSRG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static void free_all(dsrg_plan* p) {
+  if (p->split) split_free(p);
+  for (void* a : p->allocs) cudaFree(a);
+  p->allocs.clear();
+}
+
+extern "C" {
+
+const char* dsrg_status_string(dsrg_status_t st) {
+  switch (st) {
+    case DSRG_OK: return "ok";
+    case DSRG_ERR_INVALID_ARG: return "invalid argument";
+    case DSRG_ERR_CUDA: return "CUDA runtime error";
+    case DSRG_ERR_OOM: return "device workspace allocation failed";
+    case DSRG_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case DSRG_ERR_NONFINITE: return "non-finite flow parameter";
+    case DSRG_ERR_UNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown status";
+}
+
+const char* dsrg_plan_last_error(const dsrg_plan_t* plan) {
+  return plan ? plan->last_error.c_str() : "no plan";
+}
+
+int32_t dsrg_plan_last_launch_count(const dsrg_plan_t* plan) { return plan ? plan->launches : -1; }
+
+size_t dsrg_plan_workspace_bytes(const dsrg_plan_t* plan) { return plan ? plan->ws_bytes : 0; }
+
+dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
+                           void* cuda_stream, uint32_t flags) {
+  if (!out) return DSRG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!sz) return DSRG_ERR_INVALID_ARG;
+  if (sz->ncore < 1 || sz->nvirt < 1 || sz->naux < 1 || sz->nactive < 0)
+    return DSRG_ERR_INVALID_ARG;
+  if (prec != DSRG_PREC_FP64 && prec != DSRG_PREC_TF32X3 && prec != DSRG_PREC_BF16X3)
+    return DSRG_ERR_INVALID_ARG;
+  if (sz->nactive > NA_MAX) return DSRG_ERR_UNSUPPORTED;
+  // index arithmetic of the kernels uses int for per-space sizes and size_t for B
+  if ((long long)sz->ncore + sz->nactive + sz->nvirt > (1 << 20) || sz->naux > (1 << 24))
+    return DSRG_ERR_UNSUPPORTED;
+
+  dsrg_plan* p = new (std::nothrow) dsrg_plan();
+  if (!p) return DSRG_ERR_OOM;
+  Sizes& z = p->z;
+  z.nC = sz->ncore;
+  z.nA = sz->nactive;
+  z.nV = sz->nvirt;
+  z.Q = sz->naux;
+  z.nH = z.nC + z.nA;
+  z.nP = z.nA + z.nV;
+  z.n = z.nC + z.nA + z.nV;
+  p->prec = prec;
+  p->stream = (cudaStream_t)cuda_stream;
+  p->flags = flags;
+  cudaGetDevice(&p->device);
+  if (!ccav_supported(z)) {
+    delete p;
+    return DSRG_ERR_UNSUPPORTED;
+  }
+  std::string why;
+  if (prec != DSRG_PREC_FP64 && !split_supported(p, &why)) {
+    delete p;
+    return DSRG_ERR_UNSUPPORTED;
+  }
+
+  // work lists
+  std::vector<int2> pairs;
+  for (int i = 0; i < z.nC; ++i)
+    for (int j = i; j < z.nC; ++j) pairs.push_back(make_int2(i, j));
+  p->n_pairs = (int)pairs.size();
+  std::vector<int2> tp64, tp32;
+  tile_pairs(z.nV, p->tile_ccvv, tp64);
+  tile_pairs(z.nV, p->tile_cavv, tp32);
+  p->n_tp_ccvv = (int)tp64.size();
+  p->n_tp_cavv = (int)tp32.size();
+
+  // partial-sum segments
+  int np = 0;
+  const int nccvv = (prec == DSRG_PREC_FP64) ? ccvv_fp64_blocks(p) : split_ccvv_blocks(p);
+  p->segs.push_back(Segment{np, nccvv, BLK_CCVV});
+  p->seg_ccvv = 0;
+  np += nccvv;
+  const int ncavv = cavv_fp64_blocks(p);
+  p->segs.push_back(Segment{np, ncavv, BLK_CAVV});
+  p->seg_cavv = 1;
+  np += ncavv;
+  const int nccav = ccav_fp64_blocks(p);
+  p->segs.push_back(Segment{np, nccav, BLK_CCAV});
+  p->seg_ccav = 2;
+  np += nccav;
+  np += active_plan(p, np);
+  p->n_partials = np;
+
+  bool ok = true;
+  ok = ok && plan_alloc(p, (void**)&p->d_pairs, pairs.size() * sizeof(int2));
+  ok = ok && plan_alloc(p, (void**)&p->d_tp_ccvv, tp64.size() * sizeof(int2));
+  ok = ok && plan_alloc(p, (void**)&p->d_tp_cavv, tp32.size() * sizeof(int2));
+  ok = ok && plan_alloc(p, (void**)&p->d_partials, (size_t)np * sizeof(double));
+  ok = ok && plan_alloc(p, (void**)&p->d_segs, p->segs.size() * sizeof(Segment));
+  ok = ok && plan_alloc(p, (void**)&p->d_status, sizeof(int));
+  ok = ok && active_alloc(p);
+  if (ok && prec != DSRG_PREC_FP64) ok = split_alloc(p);
+  if (ok && (flags & DSRG_PLAN_HOST_IO)) {
+    const size_t nb = (size_t)z.Q * z.nH * z.nP;
+    const size_t ne = (size_t)z.n, ng = (size_t)z.nA * z.nA, nl = ng * ng;
+    double* base = nullptr;
+    ok = ok && plan_alloc(p, (void**)&base, (nb + ne + ng + nl + 5) * sizeof(double));
+    if (ok) {
+      p->st_B = base;
+      p->st_eps = base + nb;
+      p->st_g = p->st_eps + ne;
+      p->st_l = p->st_g + ng;
+      p->st_out = p->st_l + nl;
+    }
+  }
+  if (!ok) {
+    free_all(p);
+    delete p;
+    return DSRG_ERR_OOM;
+  }
+  cudaError_t e = cudaSuccess;
+  e = cudaMemcpy(p->d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_tp_ccvv, tp64.data(), tp64.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_tp_cavv, tp32.data(), tp32.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_segs, p->segs.data(), p->segs.size() * sizeof(Segment),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_partials, 0, (size_t)np * sizeof(double));
+  if (e != cudaSuccess) {
+    free_all(p);
+    delete p;
+    return DSRG_ERR_CUDA;
+  }
+  *out = p;
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_plan_destroy(dsrg_plan_t* plan) {
+  if (!plan) return DSRG_OK;
+  cudaStreamSynchronize(plan->stream);
+  free_all(plan);
+  delete plan;
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_plan_set_stream(dsrg_plan_t* plan, void* cuda_stream) {
+  if (!plan) return DSRG_ERR_INVALID_ARG;
+  plan->stream = (cudaStream_t)cuda_stream;
+  return DSRG_OK;
+}
+
+static dsrg_status_t check_common(dsrg_plan* p, const double* B, const double* eps,
+                                  const double* g, const double* l, double s, bool need_active) {
+  if (!p) return DSRG_ERR_INVALID_ARG;
+  if (std::isnan(s) || std::isinf(s)) return fail(p, DSRG_ERR_NONFINITE, "s is not finite");
+  if (s < 0.0) return fail(p, DSRG_ERR_INVALID_ARG, "s must be >= 0");
+  if (!B || !eps) return fail(p, DSRG_ERR_INVALID_ARG, "B and eps must not be NULL");
+  if (need_active && p->z.nA > 0 && (!g || !l))
+    return fail(p, DSRG_ERR_INVALID_ARG, "gamma1 and lambda2 must not be NULL when nactive > 0");
+  const uintptr_t mis = ((uintptr_t)B | (uintptr_t)eps | (uintptr_t)g | (uintptr_t)l) & 7u;
+  if (mis) return fail(p, DSRG_ERR_INVALID_ARG, "arrays must be 8-byte aligned");
+  return DSRG_OK;
+}
+
+static dsrg_status_t run_energy(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                                const double* L, double s, double* out) {
+  cudaError_t e;
+  if (p->prec == DSRG_PREC_FP64)
+    e = launch_ccvv_fp64(p, B, eps, s);
+  else
+    e = launch_split_ccvv(p, B, eps, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
+  if ((e = launch_cavv_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv");
+  if ((e = launch_ccav_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "ccav");
+  if ((e = launch_active(p, B, eps, G, L, s, false)) != cudaSuccess) return cuda_fail(p, e, "active");
+  if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_mrpt2_energy(dsrg_plan_t* p, const double* B, const double* eps,
+                                const double* gamma1, const double* lambda2, double s,
+                                double* out_dev) {
+  dsrg_status_t st = check_common(p, B, eps, gamma1, lambda2, s, true);
+  if (st != DSRG_OK) return st;
+  if (!out_dev || ((uintptr_t)out_dev & 7u)) return fail(p, DSRG_ERR_INVALID_ARG, "bad out pointer");
+  p->launches = 0;
+  return run_energy(p, B, eps, gamma1, lambda2, s, out_dev);
+}
+
+dsrg_status_t dsrg_ccvv_pair_energies(dsrg_plan_t* p, const double* B, const double* eps, double s,
+                                      double* pairs_dev) {
+  dsrg_status_t st = check_common(p, B, eps, nullptr, nullptr, s, false);
+  if (st != DSRG_OK) return st;
+  if (!pairs_dev || ((uintptr_t)pairs_dev & 7u))
+    return fail(p, DSRG_ERR_INVALID_ARG, "bad pairs pointer");
+  p->launches = 0;
+  cudaError_t e;
+  if (p->prec == DSRG_PREC_FP64)
+    e = launch_ccvv_fp64(p, B, eps, s);
+  else
+    e = launch_split_ccvv(p, B, eps, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
+  if ((e = launch_pair_energies(p, pairs_dev)) != cudaSuccess) return cuda_fail(p, e, "pairs");
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const double* eps,
+                                     const double* gamma1, const double* lambda2, double s,
+                                     double* out_dev, double* dB_dev, double* deps_dev,
+                                     double* ds_dev) {
+  dsrg_status_t st = check_common(p, B, eps, gamma1, lambda2, s, true);
+  if (st != DSRG_OK) return st;
+  (void)out_dev;
+  (void)dB_dev;
+  (void)deps_dev;
+  (void)ds_dev;
+  return fail(p, DSRG_ERR_UNSUPPORTED, "gradient not built yet");
+}
+
+dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const double* eps_host,
+                                     const double* gamma1_host, const double* lambda2_host,
+                                     double s, double* out_host) {
+  if (!p) return DSRG_ERR_INVALID_ARG;
+  if (!(p->flags & DSRG_PLAN_HOST_IO) || !p->st_B)
+    return fail(p, DSRG_ERR_INVALID_ARG, "plan was created without DSRG_PLAN_HOST_IO");
+  dsrg_status_t st = check_common(p, B_host, eps_host, gamma1_host, lambda2_host, s, true);
+  if (st != DSRG_OK) return st;
+  if (!out_host) return fail(p, DSRG_ERR_INVALID_ARG, "out_host must not be NULL");
+  const Sizes& z = p->z;
+  const size_t nb = (size_t)z.Q * z.nH * z.nP, ng = (size_t)z.nA * z.nA;
+  cudaError_t e = cudaMemcpyAsync(p->st_B, B_host, nb * 8, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->st_eps, eps_host, (size_t)z.n * 8, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && ng)
+    e = cudaMemcpyAsync(p->st_g, gamma1_host, ng * 8, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && ng)
+    e = cudaMemcpyAsync(p->st_l, lambda2_host, ng * ng * 8, cudaMemcpyHostToDevice, p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
+  p->launches = 0;
+  st = run_energy(p, p->st_B, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+  if (st != DSRG_OK) return st;
+  e = cudaMemcpyAsync(out_host, p->st_out, 5 * 8, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "device to host copy");
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_plan_sync(dsrg_plan_t* p) {
+  if (!p) return DSRG_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "sync");
+  int st = 0;
+  e = cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(p, e, "status read");
+  if (st != 0) {
+    cudaMemset(p->d_status, 0, sizeof(int));
+    return fail(p, DSRG_ERR_TIMEOUT, "a device-side wait ran out");
+  }
+  return DSRG_OK;
+}
+
+}  // extern "C"

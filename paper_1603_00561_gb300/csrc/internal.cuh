@@ -1,0 +1,137 @@
+// Internal declarations of the DSRG-MRPT2 CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dsrg.h"
+
+namespace dsrg {
+
+constexpr int NA_MAX = 8;  // largest active space the kernels are built for
+
+struct Sizes {
+  int nC, nA, nV, Q;  // core, active, virtual, auxiliary
+  int nH, nP, n;      // holes nC+nA, particles nA+nV, orbitals
+};
+
+// Index of B^Q_{h p} in the [naux][nH][nP] hole x particle layout.
+__host__ __device__ __forceinline__ size_t bidx(const Sizes& z, int q, int h, int p) {
+  return ((size_t)q * z.nH + h) * z.nP + p;
+}
+
+// Segments of the partial-sum buffer: every kernel that contributes to the
+// energy writes one FP64 partial per CTA into its own segment; a final
+// kernel adds the segments of each block in a fixed order.
+enum Block { BLK_CCVV = 0, BLK_CAVV = 1, BLK_CCAV = 2, BLK_ACTIVE = 3 };
+
+struct Segment {
+  int begin, count, block;
+};
+
+// Active-block workspace (spin-orbital tables and spatial integrals).
+struct ActiveWs {
+  double* K1 = nullptr;   // (ia|ux)  [nH][nA][nA][nP]
+  double* K2 = nullptr;   // (ix|ua)  [nH][nA][nA][nP]
+  double* K3 = nullptr;   // (ix|jy)  [nH][nA][nH][nA]
+  double* W1 = nullptr;   // 3 x [2nH][2nA][2nP][2nA]  (V, T, Vt)   <iu||ax>
+  double* W2 = nullptr;   // 3 x [2nH][2nH][2nA][2nA]  (V, T, Vt)   <ij||xy>
+  double* Ti = nullptr;   // [2nH][2nA][2nP][2nA]  gamma/eta-dressed T of W1
+  double* lam = nullptr;  // [2nA]^4 spin-orbital cumulant
+  double* gA = nullptr;   // [2nA][2nA]
+  double* t1 = nullptr;   // [2nH][2nP]
+  double* ft = nullptr;   // [2nH][2nP]
+  double* M = nullptr;    // (xe|uf) [nA][nA][nV][nV]
+  double* P12 = nullptr;  // P1, P2 [2][nA^4]
+  double* P12part = nullptr;  // per-CTA partials of P1/P2 [nblk][2][nA^4]
+  size_t w1n = 0, w2n = 0;
+  int actvv_blocks = 0;
+};
+
+struct SplitWs;  // tensor-core path workspace (tc_split.cu)
+
+}  // namespace dsrg
+
+struct dsrg_plan {
+  dsrg::Sizes z{};
+  dsrg_precision_t prec = DSRG_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  uint32_t flags = 0;
+  int device = 0;
+  std::string last_error;
+  int launches = 0;
+  size_t ws_bytes = 0;
+  std::vector<void*> allocs;
+
+  // CCVV (F1) work list: pairs i<=j and tile pairs A<=B
+  int tile_ccvv = 64;
+  int n_pairs = 0, n_tp_ccvv = 0;
+  int2* d_pairs = nullptr;     // [n_pairs] (i, j)
+  int2* d_tp_ccvv = nullptr;   // [n_tp_ccvv] (A, B)
+  // CAVV (F2) work list: tile pairs with 32-wide tiles
+  int tile_cavv = 32;
+  int n_tp_cavv = 0;
+  int2* d_tp_cavv = nullptr;
+
+  // partial sums and segments
+  double* d_partials = nullptr;
+  int n_partials = 0;
+  std::vector<dsrg::Segment> segs;
+  dsrg::Segment* d_segs = nullptr;
+  int seg_ccvv = -1, seg_cavv = -1, seg_ccav = -1;
+  std::vector<int> seg_active;
+  double* d_pairbuf = nullptr;  // [nC*nC] pair energies (scratch for the pairs entry)
+
+  dsrg::ActiveWs act;
+  dsrg::SplitWs* split = nullptr;
+
+  // device staging of dsrg_mrpt2_energy_host (DSRG_PLAN_HOST_IO)
+  double *st_B = nullptr, *st_eps = nullptr, *st_g = nullptr, *st_l = nullptr, *st_out = nullptr;
+
+  // device status word (bounded waits)
+  int* d_status = nullptr;
+};
+
+namespace dsrg {
+
+// Allocation helper: records the pointer in the plan; returns false on failure.
+bool plan_alloc(dsrg_plan* p, void** ptr, size_t bytes);
+
+// Launchers (each returns cudaSuccess or the launch error; adds to p->launches).
+cudaError_t launch_ccvv_fp64(dsrg_plan* p, const double* B, const double* eps, double s);
+cudaError_t launch_cavv_fp64(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                             double s);
+cudaError_t launch_ccav_fp64(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                             double s);
+cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                          const double* L, double s, bool gram_done);
+cudaError_t launch_gram_aavv_fp64(dsrg_plan* p, const double* B);
+cudaError_t launch_final_reduce(dsrg_plan* p, double* out);
+cudaError_t launch_pair_energies(dsrg_plan* p, double* pairs);
+
+// Sizes of the per-launch grids, used to lay out partial segments at plan time.
+int ccvv_fp64_blocks(const dsrg_plan* p);
+int cavv_fp64_blocks(const dsrg_plan* p);
+int ccav_fp64_blocks(const dsrg_plan* p);
+// Active block: fills the segment list (one per term kernel) and returns the partial count.
+int active_plan(dsrg_plan* p, int first_partial);
+bool active_alloc(dsrg_plan* p);
+
+// Tensor-core split path (tc_split.cu).
+bool split_supported(const dsrg_plan* p, std::string* why);
+bool split_alloc(dsrg_plan* p);
+void split_free(dsrg_plan* p);
+int split_ccvv_blocks(const dsrg_plan* p);
+cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, double s);
+
+}  // namespace dsrg
+
+#define DSRG_LAUNCH_CHECK(p)                 \
+  do {                                       \
+    (p)->launches++;                         \
+    cudaError_t e_ = cudaGetLastError();     \
+    if (e_ != cudaSuccess) return e_;        \
+  } while (0)
