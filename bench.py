@@ -30,6 +30,8 @@ UNIT = "TFLOP/s"
 WORKLOADS = {
     "naphthyne-v5z-1240": dict(ncore=24, nactive=2, nvirt=1214, naux=3400, s=0.5),
     "naphthyne-vtz-398": dict(ncore=24, nactive=2, nvirt=372, naux=1200, s=0.5),
+    # a smaller case of the same shape family, for ncu captures (B = 147 MB > L2)
+    "profile-16x600": dict(ncore=16, nactive=2, nvirt=600, naux=1700, s=0.5),
 }
 # nominal dense rates (TFLOP/s) of the recipe, used to scale the measured BF16 peak
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
@@ -190,7 +192,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--workload", default="naphthyne-v5z-1240", choices=list(WORKLOADS))
     ap.add_argument("--ref-pairs", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -339,8 +341,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, **cfg, "precision": prec,
-                       "l2": "inputs larger than L2 (B is 0.86 GB)" if args.workload.endswith("1240")
-                       else "inputs smaller than L2"},
+                       "l2": ("inputs larger than L2 (B is %.2f GB, L2 129 MB)" % (p.B.nbytes / 1e9))
+                       if p.B.nbytes > 129e6 else "inputs smaller than L2"},
             "e2_ms_per_molecule": t_step * 1e3,
             "energies_eh": dict(zip(pk.BLOCKS, energies)),
             "roofline": roofline,

@@ -53,6 +53,7 @@ static dsrg_status_t cuda_fail(dsrg_plan* p, cudaError_t e, const char* where) {
 
 static void free_all(dsrg_plan* p) {
   if (p->split) split_free(p);
+  if (p->cavv_state) cavv_split_free(p);
   for (void* a : p->allocs) cudaFree(a);
   p->allocs.clear();
 }
@@ -135,7 +136,8 @@ dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_preci
   p->segs.push_back(Segment{np, nccvv, BLK_CCVV});
   p->seg_ccvv = 0;
   np += nccvv;
-  const int ncavv = cavv_fp64_blocks(p);
+  p->cavv_tc = (prec != DSRG_PREC_FP64) && cavv_split_supported(p);
+  const int ncavv = p->cavv_tc ? cavv_split_blocks(p) : cavv_fp64_blocks(p);
   p->segs.push_back(Segment{np, ncavv, BLK_CAVV});
   p->seg_cavv = 1;
   np += ncavv;
@@ -155,6 +157,7 @@ dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_preci
   ok = ok && plan_alloc(p, (void**)&p->d_status, sizeof(int));
   ok = ok && active_alloc(p);
   if (ok && prec != DSRG_PREC_FP64) ok = split_alloc(p);
+  if (ok && p->cavv_tc) ok = cavv_split_alloc(p);
   if (ok && (flags & DSRG_PLAN_HOST_IO)) {
     const size_t nb = (size_t)z.Q * z.nH * z.nP;
     const size_t ne = (size_t)z.n, ng = (size_t)z.nA * z.nA, nl = ng * ng;
@@ -228,9 +231,14 @@ static dsrg_status_t run_energy(dsrg_plan* p, const double* B, const double* eps
   else
     e = launch_split_ccvv(p, B, eps, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
-  if ((e = launch_cavv_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv");
+  if (p->cavv_tc)
+    e = launch_split_cavv(p, eps, G, s);  // also forms the (A,A|V,V) integrals
+  else
+    e = launch_cavv_fp64(p, B, eps, G, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cavv");
   if ((e = launch_ccav_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "ccav");
-  if ((e = launch_active(p, B, eps, G, L, s, false)) != cudaSuccess) return cuda_fail(p, e, "active");
+  if ((e = launch_active(p, B, eps, G, L, s, p->cavv_tc)) != cudaSuccess)
+    return cuda_fail(p, e, "active");
   if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
   return DSRG_OK;
 }

@@ -1,6 +1,7 @@
 // Internal declarations of the DSRG-MRPT2 CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -87,6 +88,8 @@ struct dsrg_plan {
 
   dsrg::ActiveWs act;
   dsrg::SplitWs* split = nullptr;
+  void* cavv_state = nullptr;  // tensor-core CAVV tables (tc_cavv.cu)
+  bool cavv_tc = false;        // CAVV and the (A,A|V,V) integrals on the tensor cores
 
   // device staging of dsrg_mrpt2_energy_host (DSRG_PLAN_HOST_IO)
   double *st_B = nullptr, *st_eps = nullptr, *st_g = nullptr, *st_l = nullptr, *st_out = nullptr;
@@ -126,6 +129,15 @@ bool split_alloc(dsrg_plan* p);
 void split_free(dsrg_plan* p);
 int split_ccvv_blocks(const dsrg_plan* p);
 cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, double s);
+int split_qpad(const dsrg_plan* p);
+const CUtensorMap* split_map(const dsrg_plan* p, bool hi);
+
+// Tensor-core CAVV (tc_cavv.cu); needs the planes staged by launch_split_ccvv.
+bool cavv_split_supported(const dsrg_plan* p);
+int cavv_split_blocks(const dsrg_plan* p);
+bool cavv_split_alloc(dsrg_plan* p);
+void cavv_split_free(dsrg_plan* p);
+cudaError_t launch_split_cavv(dsrg_plan* p, const double* eps, const double* G, double s);
 
 }  // namespace dsrg
 

@@ -31,6 +31,7 @@
 
 #include "internal.cuh"
 #include "regulators.cuh"
+#include "tc_common.cuh"
 
 namespace dsrg {
 
@@ -41,7 +42,6 @@ constexpr int SLOT_BYTES = TT * KB_BYTES;    // one operand tile of one plane: 8
 constexpr int STAGE_BYTES = 4 * 2 * SLOT_BYTES;
 constexpr int SPLIT_THREADS = 192;
 constexpr int TMEM_COLS = 512;
-constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 struct SplitWs {
   int elt = 4, kb_elems = 16;
@@ -68,118 +68,6 @@ struct SplitArgs {
   double* partials;
   int* status;
 };
-
-// ------------------------------- PTX helpers -------------------------------
-__device__ __forceinline__ uint32_t su32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait on phase `parity`; false if it ran out or another role aborted.
-__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
-                                       int* status) {
-  if (mbar_try(b, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  while (true) {
-    if (mbar_try(b, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > WAIT_NS) {
-      *abort_flag = 1;
-      atomicExch(status, 1);
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
-      "%4}], [%2];" ::"r"(su32(dst)),
-      "l"((unsigned long long)map), "r"(su32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   su32(bar))
-               : "memory");
-}
-template <bool BF16>
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t acc) {
-  if (BF16) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-  }
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-      " [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void named_bar(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows at a
-// 64-byte pitch (8-row groups 512 bytes apart).
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset: 8 rows x 64 B
-  d |= (uint64_t)1 << 46;           // descriptor version of tcgen05
-  d |= (uint64_t)4 << 61;           // 64-byte swizzle
-  return d;
-}
-// Instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), both K-major, M = N = 128.
-template <bool BF16>
-__host__ __device__ constexpr uint32_t idesc_128x128() {
-  return (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) | ((128u >> 3) << 17) |
-         ((128u >> 4) << 24);
-}
 
 // Operand slots of one stage: 0 = rows (i, A), 1 = (j, B), 2 = (j, A), 3 = (i, B).
 // x = slot g1a . slot g1b^T, y = slot g2a . slot g2b^T; duplicate tiles are
@@ -318,7 +206,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
             ph ^= 1u;
           }
           const unsigned long long t0 = gtimer();
-          while (!mbar_try(&full[s], ph) && gtimer() - t0 < WAIT_NS) {
+          while (!mbar_try(&full[s], ph) && gtimer() - t0 < TC_WAIT_NS) {
           }
         }
       }
@@ -388,7 +276,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
         // drain: every MMA issued so far completes before the TMEM is released
         tc_commit(drain);
         const unsigned long long t0 = gtimer();
-        while (!mbar_try(drain, 0) && gtimer() - t0 < WAIT_NS) {
+        while (!mbar_try(drain, 0) && gtimer() - t0 < TC_WAIT_NS) {
         }
       }
     }
@@ -646,6 +534,12 @@ bool split_alloc(dsrg_plan* p) {
   if (!make_map(&w->map_hi, w->hi, bf16, w->rows, w->Qpad, w->kb_elems)) return false;
   if (!make_map(&w->map_lo, w->lo, bf16, w->rows, w->Qpad, w->kb_elems)) return false;
   return true;
+}
+
+int split_qpad(const dsrg_plan* p) { return p->split->Qpad; }
+
+const CUtensorMap* split_map(const dsrg_plan* p, bool hi) {
+  return hi ? &p->split->map_hi : &p->split->map_lo;
 }
 
 void split_free(dsrg_plan* p) {

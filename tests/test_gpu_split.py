@@ -1,0 +1,128 @@
+"""Parity of the split-precision tensor-core path (tcgen05) with the oracle.
+
+The CCVV products run as hi*hi + hi*lo + lo*hi with B = hi + lo in TF32 or
+BF16 planes, accumulated in FP32 in tensor memory. The tensor-core
+accumulator does not round to nearest: every MMA instruction truncates
+toward zero, which shrinks |v_ef| by up to about half an FP32 ulp per
+instruction. With 3 instructions per K step of 8 (TF32) or 16 (BF16)
+auxiliary functions, the relative error of E_CCVV is bounded by
+    2 * (3 * ceil(naux / K)) * 2^-24        (the factor 2: E is quadratic in v)
+which is the tolerance used here; the measured errors sit well inside it.
+All other blocks run the FP64 kernels and keep the FP64 bar (1e-10).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from dsrg_synth import CONFIGS, make_problem
+from oracle import dsrg as odsrg
+
+pytestmark = pytest.mark.gpu
+
+BLOCKS = ["ccvv", "cavv", "ccav", "active", "total"]
+KSTEP = {"tf32x3": 8, "bf16x3": 16}
+
+
+def split_tol(prec, naux):
+    return 2.0 * 3 * math.ceil(naux / KSTEP[prec]) * 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1603_00561_gb300 as pk
+    pk.build()
+    return pk
+
+
+def _run(pk, p, prec):
+    plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec)
+    dev = pk.to_device(p)
+    out = plan.energy(*dev, p.s).cpu().numpy()
+    pairs = plan.pair_energies(dev[0], dev[1], p.s).cpu().numpy()
+    plan.sync()
+    return dict(zip(BLOCKS, out)), pairs
+
+
+CASES = [
+    (10, 4, 60, 200, 0.5, 0),    # the small synthetic system
+    (5, 2, 130, 77, 0.37, 1),    # ragged tail: 2 virtual tiles of 128, second one partial
+    (3, 0, 300, 64, 1.0, 2),     # no active orbitals, three tiles
+    (1, 1, 257, 40, 0.1, 3),     # one core orbital (diagonal pairs only), 3 tiles, tail of 1
+    (4, 3, 128, 33, 0.5, 4),     # exactly one tile; naux not a multiple of the K block
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("nC,nA,nV,Q,s,seed", CASES)
+def test_split_blocks_small(pk, prec, nC, nA, nV, Q, s, seed):
+    p = make_problem(nC, nA, nV, Q, s=s, seed=seed)
+    gpu, pairs = _run(pk, p, prec)
+    ref = odsrg.energy(p.B, p.eps, p.gamma1, p.lambda2, p.s, nC, nA, nV, with_pairs=True)
+    tol = split_tol(prec, Q)
+    for k in BLOCKS:
+        rel = abs(gpu[k] - ref[k]) / max(abs(ref[k]), 1e-300)
+        print(f"{prec} {nC}/{nA}/{nV}/{Q} {k:7s} gpu={gpu[k]:+.12e} oracle={ref[k]:+.12e} rel={rel:.2e}")
+        bar = tol if k in ("ccvv", "total") else 1e-10
+        if ref[k] == 0.0:
+            assert gpu[k] == 0.0
+        else:
+            assert rel <= bar, (k, rel, bar)
+    # every pair energy, including the diagonal ones, within the same bound
+    rel_pairs = np.abs(pairs - ref["pairs"]) / np.abs(ref["pairs"])
+    assert rel_pairs.max() <= 2 * tol, rel_pairs.max()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_split_vtz_against_fp64_path(pk, prec):
+    p = make_problem(**CONFIGS["naphthyne-vtz-398"])
+    gs, ps = _run(pk, p, prec)
+    g64, p64 = _run(pk, p, "fp64")
+    rel = abs(gs["ccvv"] - g64["ccvv"]) / abs(g64["ccvv"])
+    print(prec, "vtz ccvv rel vs fp64", rel)
+    assert rel <= split_tol(prec, p.naux)
+    for k in ("cavv", "ccav", "active"):
+        assert gs[k] == g64[k]
+
+
+@pytest.mark.parametrize("s", [0.1, 0.5, 1.0])
+def test_split_v5z_s_sweep(pk, s):
+    """Quintuple-zeta size, s in {0.1, 0.5, 1.0}: BF16x3 against the FP64 GPU
+    path per block, and sampled pair energies against the oracle."""
+    cfg = dict(CONFIGS["naphthyne-v5z-1240"])
+    cfg["s"] = s
+    p = make_problem(**cfg)
+    gs, ps = _run(pk, p, "bf16x3")
+    g64, p64 = _run(pk, p, "fp64")
+    tol = split_tol("bf16x3", p.naux)
+    for k in BLOCKS:
+        rel = abs(gs[k] - g64[k]) / abs(g64[k])
+        print(f"v5z s={s} {k:7s} split={gs[k]:+.12e} fp64={g64[k]:+.12e} rel={rel:.2e}")
+        assert rel <= (tol if k in ("ccvv", "total") else 1e-14)
+    sample = [(0, 0), (3, 19), (23, 23)]
+    ref = odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample).numpy()
+    for (m, n) in sample:
+        assert abs(ps[m, n] - ref[m, n]) / abs(ref[m, n]) <= 2 * tol
+        assert abs(p64[m, n] - ref[m, n]) / abs(ref[m, n]) <= 1e-10
+
+
+def test_split_deterministic_and_scaling(pk):
+    """Fixed work decomposition and reduction order: bitwise repeatable; B -> 2B
+    scales the split planes exactly, so E -> 16 E bit for bit."""
+    p = make_problem(4, 2, 200, 96, s=0.5, seed=12)
+    a, _ = _run(pk, p, "bf16x3")
+    b, _ = _run(pk, p, "bf16x3")
+    c, _ = _run(pk, p.scaled(2.0), "bf16x3")
+    for k in BLOCKS:
+        assert a[k] == b[k]
+        assert c[k] == 16.0 * a[k]
+
+
+def test_split_s_zero(pk):
+    p = make_problem(3, 2, 140, 50, s=0.0, seed=13)
+    g, pairs = _run(pk, p, "tf32x3")
+    for k in BLOCKS:
+        assert g[k] == 0.0
