@@ -93,6 +93,7 @@ typedef struct {
 
 /* Plan flags. */
 #define DSRG_PLAN_HOST_IO 1u  /* also allocate device staging for dsrg_mrpt2_energy_host */
+#define DSRG_PLAN_GRAD 2u     /* also allocate the workspace of dsrg_mrpt2_energy_grad */
 
 typedef struct dsrg_plan dsrg_plan_t;
 
@@ -125,7 +126,12 @@ dsrg_status_t dsrg_ccvv_pair_energies(dsrg_plan_t *plan, const double *B, const 
 
 /* Energy as dsrg_mrpt2_energy, plus the gradient of E_total with respect to
  * the inputs: dB_dev [naux][nH][nP] (dE/dB^Q_{ia} for the entries as passed),
- * deps_dev [n], ds_dev [1]. Outputs are overwritten, not accumulated. */
+ * deps_dev [n], ds_dev [1]. Outputs are overwritten, not accumulated. Needs a
+ * plan created with DSRG_PLAN_GRAD (else DSRG_ERR_INVALID_ARG). The adjoint is
+ * the derivative of the energy expression (Table 1, Table 2, Eqs. (12)-(15),
+ * (23)) evaluated in FP64 for every precision mode; each core row recomputes
+ * its pair integrals v^{kj} instead of storing them. dB is bit-reproducible;
+ * deps and ds are summed with FP64 atomics. */
 dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t *plan, const double *B, const double *eps,
                                      const double *gamma1, const double *lambda2, double s,
                                      double *out_dev, double *dB_dev, double *deps_dev,
@@ -138,6 +144,39 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t *plan, const double *B, const d
 dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t *plan, const double *B_host,
                                      const double *eps_host, const double *gamma1_host,
                                      const double *lambda2_host, double s, double *out_host);
+
+/* ---- Batches: many molecules of uneven size in one call. ----
+ * A batch plan holds one plan per molecule. In the split modes every
+ * molecule's hi/lo planes share one buffer and the CCVV work of all molecules
+ * (items = molecule x core pair x virtual tile pair) runs in ONE persistent
+ * tensor-core launch, its items dealt to the CTAs by a cost-balancing static
+ * scheduler; the other blocks run per molecule. The first call (and any call
+ * whose input pointers, s values or out pointer differ from the previous one)
+ * captures the whole call into a CUDA graph on an internal stream, so it should
+ * not itself be made while the caller's stream is being captured; later calls
+ * replay the graph on `cuda_stream`. Results are bitwise those of one plan per
+ * molecule. */
+typedef struct dsrg_batch dsrg_batch_t;
+
+/* nmol >= 1 sizes; flags as for dsrg_df_plan (DSRG_PLAN_HOST_IO, DSRG_PLAN_GRAD
+ * apply to the per-molecule plans). */
+dsrg_status_t dsrg_batch_plan(dsrg_batch_t **batch, int32_t nmol, const dsrg_sizes_t *sizes,
+                              dsrg_precision_t prec, void *cuda_stream, uint32_t flags);
+dsrg_status_t dsrg_batch_destroy(dsrg_batch_t *batch);
+
+/* B, eps, gamma1, lambda2: HOST arrays of nmol DEVICE pointers (per molecule,
+ * layouts as for dsrg_mrpt2_energy); s: HOST array of nmol flow parameters;
+ * out_dev: DEVICE [nmol][5]. */
+dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t *batch, const double *const *B,
+                                        const double *const *eps, const double *const *gamma1,
+                                        const double *const *lambda2, const double *s,
+                                        double *out_dev);
+
+/* Wait for the batch's stream and report device-side conditions of any molecule. */
+dsrg_status_t dsrg_batch_sync(dsrg_batch_t *batch);
+/* Kernel launches recorded in the batch's graph. */
+int32_t dsrg_batch_launch_count(const dsrg_batch_t *batch);
+const char *dsrg_batch_last_error(const dsrg_batch_t *batch);
 
 /* Wait for the plan's stream and report any device-side condition recorded
  * since the last call (DSRG_ERR_TIMEOUT), then clear it. */

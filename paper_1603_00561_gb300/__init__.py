@@ -15,13 +15,13 @@ import torch
 from . import _native
 from ._native import DSRGError, PREC
 
-__all__ = ["Plan", "DSRGError", "PREC", "BLOCKS", "build"]
+__all__ = ["Plan", "Batch", "DSRGError", "PREC", "BLOCKS", "build", "DSRGEnergy", "energy_total"]
 
 BLOCKS = ("ccvv", "cavv", "ccav", "active", "total")
 
 
 def build(verbose: bool = False, force: bool = False) -> str:
-    from .build import build as _b
+    from ._buildlib import build as _b
     return _b(verbose=verbose, force=force)
 
 
@@ -42,7 +42,7 @@ class Plan:
     """
 
     def __init__(self, ncore: int, nactive: int, nvirt: int, naux: int,
-                 precision: str = "fp64", host_io: bool = False, device=None):
+                 precision: str = "fp64", host_io: bool = False, grad: bool = False, device=None):
         if not torch.cuda.is_available():
             raise RuntimeError("the DSRG-MRPT2 library needs a CUDA GPU")
         self.lib = _native.load()
@@ -51,7 +51,7 @@ class Plan:
         self.precision = precision
         sz = _native.Sizes(*self.sizes)
         h = C.c_void_p()
-        flags = _native.PLAN_HOST_IO if host_io else 0
+        flags = (_native.PLAN_HOST_IO if host_io else 0) | (_native.PLAN_GRAD if grad else 0)
         with torch.cuda.device(self.device):
             st = self.lib.dsrg_df_plan(C.byref(h), C.byref(sz), PREC[precision],
                                        C.c_void_p(torch.cuda.current_stream().cuda_stream), flags)
@@ -151,6 +151,90 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many molecules of uneven size in one call (``dsrg_batch_plan``): one
+    persistent tensor-core CCVV launch over all molecules, the whole call
+    captured in a CUDA graph and replayed while inputs stay the same."""
+
+    def __init__(self, sizes, precision: str = "bf16x3", device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DSRG-MRPT2 library needs a CUDA GPU")
+        self.lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.sizes = [tuple(int(v) for v in sz) for sz in sizes]
+        arr = (_native.Sizes * len(self.sizes))(*[_native.Sizes(*sz) for sz in self.sizes])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.dsrg_batch_plan(C.byref(h), len(self.sizes), arr, PREC[precision],
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream), 0)
+        if st != _native.OK:
+            raise DSRGError(st, f"dsrg_batch_plan({len(self.sizes)} molecules) {precision}")
+        self.h = h
+        self.n = len(self.sizes)
+
+    def energy(self, inputs, s, out=None):
+        """``inputs``: list of (B, eps, gamma1, lambda2) device tensors per molecule;
+        ``s``: list of flow parameters. Returns [nmol, 5] block energies (device)."""
+        if out is None:
+            out = torch.empty((self.n, 5), dtype=torch.float64, device=self.device)
+        P = C.c_void_p * self.n
+        cols = list(zip(*inputs))
+        ptrs = [P(*[_ptr(t) for t in col]) for col in cols]
+        svals = (C.c_double * self.n)(*[float(x) for x in s])
+        st = self.lib.dsrg_mrpt2_energy_batched(self.h, *ptrs, svals, _ptr(out))
+        if st != _native.OK:
+            raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
+        return out
+
+    def sync(self):
+        st = self.lib.dsrg_batch_sync(self.h)
+        if st != _native.OK:
+            raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
+
+    def launch_count(self) -> int:
+        return int(self.lib.dsrg_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dsrg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DSRGEnergy(torch.autograd.Function):
+    """E_total(B, eps, s) as a differentiable scalar. The backward pass calls the
+    library's adjoint (``dsrg_mrpt2_energy_grad``), which recomputes the pair
+    integrals per core row instead of storing anything from the forward pass.
+    gamma1 and lambda2 are treated as constants."""
+
+    @staticmethod
+    def forward(ctx, B, eps, s, gamma1, lambda2, plan):
+        sval = float(s)
+        out = plan.energy(B, eps, gamma1, lambda2, sval)
+        ctx.save_for_backward(B, eps)
+        ctx.extra = (gamma1, lambda2, sval, plan)
+        return out[4].clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        B, eps = ctx.saved_tensors
+        gamma1, lambda2, sval, plan = ctx.extra
+        _, dB, de, ds = plan.energy_grad(B, eps, gamma1, lambda2, sval)
+        return g * dB, g * de, (g * ds[0]).reshape(()), None, None, None
+
+
+def energy_total(plan, B, eps, s, gamma1=None, lambda2=None):
+    """Differentiable E_total (see ``DSRGEnergy``); ``s`` may be a tensor."""
+    if not isinstance(s, torch.Tensor):
+        s = torch.tensor(float(s), dtype=torch.float64, device=B.device)
+    return DSRGEnergy.apply(B, eps, s, gamma1, lambda2, plan)
 
 
 def to_device(problem, device="cuda"):

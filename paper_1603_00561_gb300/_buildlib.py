@@ -2,7 +2,7 @@
 
 Each ``csrc/*.cu`` is compiled to an object in parallel, then linked into one
 shared library with a plain C ABI (``include/dsrg.h``). Usage:
-``python -m paper_1603_00561_gb300.build`` or ``build()`` from Python.
+``python -m paper_1603_00561_gb300._buildlib`` or ``build()`` from Python.
 """
 from __future__ import annotations
 

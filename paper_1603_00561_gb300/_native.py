@@ -14,6 +14,7 @@ STATUS_NAMES = {0: "DSRG_OK", 1: "DSRG_ERR_INVALID_ARG", 2: "DSRG_ERR_CUDA", 3: 
 # dsrg_precision_t
 PREC = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
 PLAN_HOST_IO = 1
+PLAN_GRAD = 2
 
 # every exported symbol of include/dsrg.h
 EXPORTS = [
@@ -21,6 +22,8 @@ EXPORTS = [
     "dsrg_ccvv_pair_energies", "dsrg_mrpt2_energy_grad", "dsrg_mrpt2_energy_host",
     "dsrg_plan_sync", "dsrg_plan_last_launch_count", "dsrg_plan_workspace_bytes",
     "dsrg_status_string", "dsrg_plan_last_error",
+    "dsrg_batch_plan", "dsrg_batch_destroy", "dsrg_mrpt2_energy_batched", "dsrg_batch_sync",
+    "dsrg_batch_launch_count", "dsrg_batch_last_error",
 ]
 
 
@@ -38,7 +41,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise RuntimeError(f"{path} is missing: build it with paper_1603_00561_gb300.build.build()")
+        raise RuntimeError(f"{path} is missing: build it with paper_1603_00561_gb300.build()")
     lib = C.CDLL(path)
     vp, dp, st = C.c_void_p, C.POINTER(C.c_double), C.c_int
     lib.dsrg_df_plan.argtypes = [C.POINTER(vp), C.POINTER(Sizes), C.c_int, vp, C.c_uint32]
@@ -65,6 +68,19 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_status_string.restype = C.c_char_p
     lib.dsrg_plan_last_error.argtypes = [vp]
     lib.dsrg_plan_last_error.restype = C.c_char_p
+    lib.dsrg_batch_plan.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(Sizes), C.c_int, vp, C.c_uint32]
+    lib.dsrg_batch_plan.restype = st
+    lib.dsrg_batch_destroy.argtypes = [vp]
+    lib.dsrg_batch_destroy.restype = st
+    lib.dsrg_mrpt2_energy_batched.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                              C.POINTER(vp), C.POINTER(C.c_double), vp]
+    lib.dsrg_mrpt2_energy_batched.restype = st
+    lib.dsrg_batch_sync.argtypes = [vp]
+    lib.dsrg_batch_sync.restype = st
+    lib.dsrg_batch_launch_count.argtypes = [vp]
+    lib.dsrg_batch_launch_count.restype = C.c_int32
+    lib.dsrg_batch_last_error.argtypes = [vp]
+    lib.dsrg_batch_last_error.restype = C.c_char_p
     _ = dp
     _lib = lib
     return lib

@@ -54,6 +54,7 @@ static dsrg_status_t cuda_fail(dsrg_plan* p, cudaError_t e, const char* where) {
 static void free_all(dsrg_plan* p) {
   if (p->split) split_free(p);
   if (p->cavv_state) cavv_split_free(p);
+  if (p->grad) grad_free(p);
   for (void* a : p->allocs) cudaFree(a);
   p->allocs.clear();
 }
@@ -81,8 +82,11 @@ int32_t dsrg_plan_last_launch_count(const dsrg_plan_t* plan) { return plan ? pla
 
 size_t dsrg_plan_workspace_bytes(const dsrg_plan_t* plan) { return plan ? plan->ws_bytes : 0; }
 
-dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
-                           void* cuda_stream, uint32_t flags) {
+}  // extern "C"
+
+namespace dsrg {
+dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
+                          void* cuda_stream, uint32_t flags, const SplitShare* share) {
   if (!out) return DSRG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!sz) return DSRG_ERR_INVALID_ARG;
@@ -156,8 +160,11 @@ dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_preci
   ok = ok && plan_alloc(p, (void**)&p->d_segs, p->segs.size() * sizeof(Segment));
   ok = ok && plan_alloc(p, (void**)&p->d_status, sizeof(int));
   ok = ok && active_alloc(p);
-  if (ok && prec != DSRG_PREC_FP64) ok = split_alloc(p);
+  if (ok && prec != DSRG_PREC_FP64)
+    ok = share ? split_alloc_at(p, share->hi, share->lo, share->Qld, share->row_base, nullptr, nullptr)
+               : split_alloc(p);
   if (ok && p->cavv_tc) ok = cavv_split_alloc(p);
+  if (ok && (flags & DSRG_PLAN_GRAD)) ok = grad_alloc(p);
   if (ok && (flags & DSRG_PLAN_HOST_IO)) {
     const size_t nb = (size_t)z.Q * z.nH * z.nP;
     const size_t ne = (size_t)z.n, ng = (size_t)z.nA * z.nA, nl = ng * ng;
@@ -196,6 +203,15 @@ dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_preci
   return DSRG_OK;
 }
 
+}  // namespace dsrg
+
+extern "C" {
+
+dsrg_status_t dsrg_df_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
+                           void* cuda_stream, uint32_t flags) {
+  return create_plan(out, sz, prec, cuda_stream, flags, nullptr);
+}
+
 dsrg_status_t dsrg_plan_destroy(dsrg_plan_t* plan) {
   if (!plan) return DSRG_OK;
   cudaStreamSynchronize(plan->stream);
@@ -223,14 +239,13 @@ static dsrg_status_t check_common(dsrg_plan* p, const double* B, const double* e
   return DSRG_OK;
 }
 
-static dsrg_status_t run_energy(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                                const double* L, double s, double* out) {
+}  // extern "C"
+
+namespace dsrg {
+// Everything after the CCVV launch: CAVV, CCAV, active block, final reduction.
+dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                       const double* L, double s, double* out) {
   cudaError_t e;
-  if (p->prec == DSRG_PREC_FP64)
-    e = launch_ccvv_fp64(p, B, eps, s);
-  else
-    e = launch_split_ccvv(p, B, eps, s);
-  if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
   if (p->cavv_tc)
     e = launch_split_cavv(p, eps, G, s);  // also forms the (A,A|V,V) integrals
   else
@@ -242,6 +257,20 @@ static dsrg_status_t run_energy(dsrg_plan* p, const double* B, const double* eps
   if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
   return DSRG_OK;
 }
+}  // namespace dsrg
+
+static dsrg_status_t run_energy(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                                const double* L, double s, double* out) {
+  cudaError_t e;
+  if (p->prec == DSRG_PREC_FP64)
+    e = launch_ccvv_fp64(p, B, eps, s);
+  else
+    e = launch_split_ccvv(p, B, eps, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
+  return run_rest(p, B, eps, G, L, s, out);
+}
+
+extern "C" {
 
 dsrg_status_t dsrg_mrpt2_energy(dsrg_plan_t* p, const double* B, const double* eps,
                                 const double* gamma1, const double* lambda2, double s,
@@ -276,11 +305,23 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const doub
                                      double* ds_dev) {
   dsrg_status_t st = check_common(p, B, eps, gamma1, lambda2, s, true);
   if (st != DSRG_OK) return st;
-  (void)out_dev;
-  (void)dB_dev;
-  (void)deps_dev;
-  (void)ds_dev;
-  return fail(p, DSRG_ERR_UNSUPPORTED, "gradient not built yet");
+  if (!p->grad) return fail(p, DSRG_ERR_INVALID_ARG, "plan was created without DSRG_PLAN_GRAD");
+  if (!out_dev || !dB_dev || !deps_dev || !ds_dev)
+    return fail(p, DSRG_ERR_INVALID_ARG, "gradient outputs must not be NULL");
+  if (((uintptr_t)out_dev | (uintptr_t)dB_dev | (uintptr_t)deps_dev | (uintptr_t)ds_dev) & 7u)
+    return fail(p, DSRG_ERR_INVALID_ARG, "outputs must be 8-byte aligned");
+  p->launches = 0;
+  st = run_energy(p, B, eps, gamma1, lambda2, s, out_dev);
+  if (st != DSRG_OK) return st;
+  if (p->cavv_tc) {
+    // the adjoint reads the FP64 (A,A|V,V) integrals: re-form them in FP64
+    cudaError_t e0 = launch_gram_aavv_fp64(p, B);
+    if (e0 == cudaSuccess) e0 = launch_active(p, B, eps, gamma1, lambda2, s, true);
+    if (e0 != cudaSuccess) return cuda_fail(p, e0, "active (fp64 tables)");
+  }
+  cudaError_t e = launch_grad(p, B, eps, gamma1, lambda2, s, dB_dev, deps_dev, ds_dev);
+  if (e != cudaSuccess) return cuda_fail(p, e, "gradient");
+  return DSRG_OK;
 }
 
 dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const double* eps_host,

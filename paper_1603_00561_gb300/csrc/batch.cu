@@ -1,0 +1,290 @@
+// Batched energies of many molecules of uneven size.
+//
+// One plan per molecule provides the workspace of its blocks. In the split
+// precision modes all molecules' hi/lo planes live in one shared buffer
+// (molecule m's rows start at row_base[m], common row pitch = the largest
+// padded naux), so a single persistent tcgen05 launch covers the CCVV work of
+// every molecule: its work list holds (molecule, pair, tile pair) items, dealt
+// to the CTAs by the cost-balancing scheduler of tc_split.cu. The whole call
+// (staging, the batched CCVV launch, every molecule's remaining blocks and
+// reductions) is captured once into a CUDA graph and replayed while the input
+// pointers and flow parameters stay the same.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+struct dsrg_batch {
+  int nmol = 0;
+  dsrg_precision_t prec = DSRG_PREC_FP64;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<dsrg_plan*> plans;
+  std::vector<void*> allocs;
+  void* hi = nullptr;
+  void* lo = nullptr;
+  CUtensorMap map_hi, map_lo;
+  void* d_mols = nullptr;
+  int4* d_items = nullptr;
+  int* d_begin = nullptr;
+  int grid = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> key;
+  std::string last_error;
+  int launches = 0;
+  size_t ws_bytes = 0;
+};
+
+namespace {
+
+bool balloc(dsrg_batch* b, void** p, size_t bytes) {
+  *p = nullptr;
+  if (cudaMalloc(p, bytes ? bytes : 8) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  b->allocs.push_back(*p);
+  b->ws_bytes += bytes;
+  return true;
+}
+
+void bfree(dsrg_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  for (dsrg_plan* p : b->plans)
+    if (p) dsrg_plan_destroy(p);
+  b->plans.clear();
+  for (void* a : b->allocs) cudaFree(a);
+  b->allocs.clear();
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  b->cap_stream = nullptr;
+}
+
+dsrg_status_t bfail(dsrg_batch* b, dsrg_status_t st, const std::string& m) {
+  b->last_error = m;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes_t* sizes,
+                              dsrg_precision_t prec, void* cuda_stream, uint32_t flags) {
+  if (!out) return DSRG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nmol < 1 || !sizes) return DSRG_ERR_INVALID_ARG;
+  if (prec != DSRG_PREC_FP64 && prec != DSRG_PREC_TF32X3 && prec != DSRG_PREC_BF16X3)
+    return DSRG_ERR_INVALID_ARG;
+  dsrg_batch* b = new (std::nothrow) dsrg_batch();
+  if (!b) return DSRG_ERR_OOM;
+  b->nmol = nmol;
+  b->prec = prec;
+  b->user_stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return DSRG_ERR_CUDA;
+  }
+  const bool split = prec != DSRG_PREC_FP64;
+  const bool bf16 = prec == DSRG_PREC_BF16X3;
+  std::vector<long long> row_base(nmol, 0);
+  long long rows = 0;
+  int Qld = 64;
+  for (int m = 0; m < nmol; ++m) {
+    const dsrg_sizes_t& s = sizes[m];
+    if (s.ncore < 1 || s.nvirt < 1 || s.naux < 1 || s.nactive < 0 || s.nactive > dsrg::NA_MAX) {
+      bfree(b);
+      delete b;
+      return DSRG_ERR_INVALID_ARG;
+    }
+    dsrg::Sizes z{s.ncore, s.nactive, s.nvirt, s.naux, s.ncore + s.nactive, s.nactive + s.nvirt,
+                  s.ncore + s.nactive + s.nvirt};
+    row_base[m] = rows;
+    rows += dsrg::split_plane_rows(z);
+    const int qp = dsrg::split_plane_qpad(z);
+    Qld = qp > Qld ? qp : Qld;
+  }
+  if (split && rows >= (1ll << 31)) {
+    bfree(b);
+    delete b;
+    return DSRG_ERR_UNSUPPORTED;
+  }
+  const int elt = bf16 ? 2 : 4;
+  if (split) {
+    const size_t plane = (size_t)rows * Qld * elt;
+    if (!balloc(b, &b->hi, plane) || !balloc(b, &b->lo, plane)) {
+      bfree(b);
+      delete b;
+      return DSRG_ERR_OOM;
+    }
+    if (cudaMemset(b->hi, 0, plane) != cudaSuccess || cudaMemset(b->lo, 0, plane) != cudaSuccess ||
+        !dsrg::split_make_map(&b->map_hi, b->hi, bf16, rows, Qld, dsrg::split_kb_elems(bf16)) ||
+        !dsrg::split_make_map(&b->map_lo, b->lo, bf16, rows, Qld, dsrg::split_kb_elems(bf16))) {
+      bfree(b);
+      delete b;
+      return DSRG_ERR_CUDA;
+    }
+  }
+  b->plans.assign(nmol, nullptr);
+  for (int m = 0; m < nmol; ++m) {
+    dsrg::SplitShare sh;
+    sh.hi = split ? (char*)b->hi + (size_t)row_base[m] * Qld * elt : nullptr;
+    sh.lo = split ? (char*)b->lo + (size_t)row_base[m] * Qld * elt : nullptr;
+    sh.Qld = Qld;
+    sh.row_base = row_base[m];
+    dsrg_status_t st =
+        dsrg::create_plan(&b->plans[m], &sizes[m], prec, b->cap_stream, flags, split ? &sh : nullptr);
+    if (st != DSRG_OK) {
+      bfree(b);
+      delete b;
+      return st;
+    }
+    b->ws_bytes += dsrg_plan_workspace_bytes(b->plans[m]);
+  }
+  if (split) {
+    const size_t mdb = dsrg::split_mol_desc_bytes();
+    std::vector<char> mols(mdb * nmol);
+    std::vector<int4> items, sched;
+    std::vector<double> cost;
+    std::vector<int> begin;
+    for (int m = 0; m < nmol; ++m) {
+      dsrg::split_fill_mol_desc(b->plans[m], row_base[m], mols.data() + m * mdb);
+      const int kblocks = dsrg::split_plane_qpad(b->plans[m]->z) / dsrg::split_kb_elems(bf16);
+      dsrg::split_item_list(b->plans[m]->z, m, kblocks, items, cost);
+    }
+    int nsm = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = (int)items.size() < nsm ? (int)items.size() : nsm;
+    dsrg::split_schedule(items, cost, b->grid, sched, begin);
+    if (!balloc(b, &b->d_mols, mols.size()) ||
+        !balloc(b, (void**)&b->d_items, sched.size() * sizeof(int4)) ||
+        !balloc(b, (void**)&b->d_begin, begin.size() * sizeof(int)) ||
+        cudaMemcpy(b->d_mols, mols.data(), mols.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      bfree(b);
+      delete b;
+      return DSRG_ERR_OOM;
+    }
+  }
+  *out = b;
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_batch_destroy(dsrg_batch_t* b) {
+  if (!b) return DSRG_OK;
+  if (b->user_stream) cudaStreamSynchronize(b->user_stream);
+  cudaStreamSynchronize(b->cap_stream);
+  bfree(b);
+  delete b;
+  return DSRG_OK;
+}
+
+const char* dsrg_batch_last_error(const dsrg_batch_t* b) {
+  return b ? b->last_error.c_str() : "no batch";
+}
+
+dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
+                                        const double* const* eps, const double* const* gamma1,
+                                        const double* const* lambda2, const double* s,
+                                        double* out_dev) {
+  if (!b) return DSRG_ERR_INVALID_ARG;
+  if (!B || !eps || !s || !out_dev) return bfail(b, DSRG_ERR_INVALID_ARG, "NULL argument");
+  const int n = b->nmol;
+  std::vector<uintptr_t> key;
+  key.reserve(6 * n + 1);
+  for (int m = 0; m < n; ++m) {
+    const dsrg_plan* p = b->plans[m];
+    const double* g = gamma1 ? gamma1[m] : nullptr;
+    const double* l = lambda2 ? lambda2[m] : nullptr;
+    if (std::isnan(s[m]) || std::isinf(s[m])) return bfail(b, DSRG_ERR_NONFINITE, "s is not finite");
+    if (s[m] < 0.0) return bfail(b, DSRG_ERR_INVALID_ARG, "s must be >= 0");
+    if (!B[m] || !eps[m]) return bfail(b, DSRG_ERR_INVALID_ARG, "B and eps must not be NULL");
+    if (p->z.nA > 0 && (!g || !l))
+      return bfail(b, DSRG_ERR_INVALID_ARG, "gamma1 and lambda2 must not be NULL when nactive > 0");
+    if (((uintptr_t)B[m] | (uintptr_t)eps[m] | (uintptr_t)g | (uintptr_t)l) & 7u)
+      return bfail(b, DSRG_ERR_INVALID_ARG, "arrays must be 8-byte aligned");
+    uint64_t sbits;
+    memcpy(&sbits, &s[m], 8);
+    key.push_back((uintptr_t)B[m]);
+    key.push_back((uintptr_t)eps[m]);
+    key.push_back((uintptr_t)g);
+    key.push_back((uintptr_t)l);
+    key.push_back((uintptr_t)sbits);
+  }
+  if ((uintptr_t)out_dev & 7u) return bfail(b, DSRG_ERR_INVALID_ARG, "bad out pointer");
+  key.push_back((uintptr_t)out_dev);
+  cudaError_t e;
+  if (!b->exec || key != b->key) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->launches = 0;
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+    dsrg_status_t st = DSRG_OK;
+    const bool split = b->prec != DSRG_PREC_FP64;
+    for (int m = 0; m < n && st == DSRG_OK; ++m) {
+      dsrg_plan* p = b->plans[m];
+      p->stream = b->cap_stream;
+      p->launches = 0;
+      e = split ? dsrg::split_stage(p, B[m], eps[m], s[m]) : dsrg::launch_ccvv_fp64(p, B[m], eps[m], s[m]);
+      if (e != cudaSuccess) st = DSRG_ERR_CUDA;
+    }
+    if (st == DSRG_OK && split) {
+      dsrg_plan* p0 = b->plans[0];
+      e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
+      if (e == cudaSuccess)
+        e = dsrg::split_launch_ccvv(p0, b->map_hi, b->map_lo, b->d_mols, b->d_items, b->d_begin,
+                                    b->grid, b->prec == DSRG_PREC_BF16X3);
+      if (e != cudaSuccess) st = DSRG_ERR_CUDA;
+    }
+    for (int m = 0; m < n && st == DSRG_OK; ++m) {
+      dsrg_plan* p = b->plans[m];
+      st = dsrg::run_rest(p, B[m], eps[m], gamma1 ? gamma1[m] : nullptr,
+                          lambda2 ? lambda2[m] : nullptr, s[m], out_dev + 5 * m);
+    }
+    for (int m = 0; m < n; ++m) b->launches += b->plans[m]->launches;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (st != DSRG_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return bfail(b, st != DSRG_OK ? st : DSRG_ERR_CUDA, "graph capture failed");
+    }
+    b->graph = graph;
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    b->key = key;
+  }
+  e = cudaGraphLaunch(b->exec, b->user_stream);
+  if (e != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+  return DSRG_OK;
+}
+
+int32_t dsrg_batch_launch_count(const dsrg_batch_t* b) { return b ? b->launches : -1; }
+
+dsrg_status_t dsrg_batch_sync(dsrg_batch_t* b) {
+  if (!b) return DSRG_ERR_INVALID_ARG;
+  cudaError_t e = b->user_stream ? cudaStreamSynchronize(b->user_stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+  for (dsrg_plan* p : b->plans) {
+    dsrg_status_t st = dsrg_plan_sync(p);
+    if (st != DSRG_OK) return bfail(b, st, "a device-side wait ran out");
+  }
+  return DSRG_OK;
+}
+
+}  // extern "C"

@@ -53,6 +53,7 @@ struct ActiveWs {
 };
 
 struct SplitWs;  // tensor-core path workspace (tc_split.cu)
+struct GradWs;   // gradient workspace (grad.cu)
 
 }  // namespace dsrg
 
@@ -89,6 +90,7 @@ struct dsrg_plan {
   dsrg::ActiveWs act;
   dsrg::SplitWs* split = nullptr;
   void* cavv_state = nullptr;  // tensor-core CAVV tables (tc_cavv.cu)
+  dsrg::GradWs* grad = nullptr;  // gradient workspace (DSRG_PLAN_GRAD)
   bool cavv_tc = false;        // CAVV and the (A,A|V,V) integrals on the tensor cores
 
   // device staging of dsrg_mrpt2_energy_host (DSRG_PLAN_HOST_IO)
@@ -131,6 +133,44 @@ int split_ccvv_blocks(const dsrg_plan* p);
 cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, double s);
 int split_qpad(const dsrg_plan* p);
 const CUtensorMap* split_map(const dsrg_plan* p, bool hi);
+
+// Plan construction and the energy pipeline (api.cu), reused by batches.
+struct SplitShare {
+  void* hi;
+  void* lo;
+  int Qld;
+  long long row_base;
+};
+dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
+                          void* cuda_stream, uint32_t flags, const SplitShare* share);
+dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                       const double* L, double s, double* out);
+
+// Split planes shared by several molecules (tc_split.cu).
+bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
+                    const CUtensorMap* shared_hi, const CUtensorMap* shared_lo);
+bool split_make_map(CUtensorMap* m, void* ptr, bool bf16, long long rows, int Qld, int kb_elems);
+int split_plane_rows(const Sizes& z);
+int split_plane_qpad(const Sizes& z);
+int split_kb_elems(bool bf16);
+size_t split_mol_desc_bytes();
+void split_fill_mol_desc(const dsrg_plan* p, long long row0, void* out);
+cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double s);
+cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols, int first, int n,
+                             const double* const* eps, const double* s);
+cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,
+                              const void* d_mols, const int4* d_items, const int* d_begin,
+                              int grid, bool bf16);
+void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
+                     std::vector<double>& cost);
+void split_schedule(const std::vector<int4>& items, const std::vector<double>& cost, int ncta,
+                    std::vector<int4>& out, std::vector<int>& begin);
+
+// Gradient (grad.cu).
+bool grad_alloc(dsrg_plan* p);
+void grad_free(dsrg_plan* p);
+cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                        const double* L, double s, double* dB, double* deps, double* ds);
 
 // Tensor-core CAVV (tc_cavv.cu); needs the planes staged by launch_split_ccvv.
 bool cavv_split_supported(const dsrg_plan* p);

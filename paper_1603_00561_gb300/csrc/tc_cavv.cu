@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(C_THREADS, 1)
             }
             continue;
           }
-#pragma unroll 2
+#pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int cb = c0 + k;
             if (cb >= ncols) break;

@@ -20,7 +20,8 @@
 // Roles (one CTA per SM, persistent over the work list):
 //   warp 0      TMA producer (one elected thread)
 //   warp 1      TMEM allocator and MMA issuer (one elected thread)
-//   warps 2-5   epilogue: 128 threads, thread = TMEM lane = tile row
+//   warps 2-9   epilogue: 256 threads; warp w reads TMEM lanes 32*(w%4).. and
+//               columns 64*((w-2)/4).. of the tile (two warps per lane quarter)
 // Shared memory: 3 stages x 4 operand slots x 2 planes x (128 rows x 64 B),
 // 64-byte swizzle. TMEM: 2 buffers x (x, y) x 128 columns = 512 columns.
 // Every wait is bounded (about 2 s); on expiry the CTA records a status word,
@@ -28,6 +29,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cstring>
 
 #include "internal.cuh"
 #include "regulators.cuh"
@@ -40,32 +43,45 @@ constexpr int KB_BYTES = 64;                 // K bytes per row per stage (64-by
 constexpr int STAGES = 3;
 constexpr int SLOT_BYTES = TT * KB_BYTES;    // one operand tile of one plane: 8 KB
 constexpr int STAGE_BYTES = 4 * 2 * SLOT_BYTES;
-constexpr int SPLIT_THREADS = 192;
+constexpr int SPLIT_THREADS = 320;  // warps 0-1 roles, warps 2-9 epilogue
+constexpr int EPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
 
 struct SplitWs {
   int elt = 4, kb_elems = 16;
-  int nVpad = 0, Qpad = 0, rows = 0, nT = 0, n_tp = 0, n_items = 0, grid = 0;
+  int nVpad = 0, Qpad = 0, Qld = 0, rows = 0, nT = 0, n_tp = 0, n_items = 0, grid = 0;
+  long long row_base = 0;   // first row of this molecule in a shared (batched) plane buffer
   void* hi = nullptr;
   void* lo = nullptr;
   CUtensorMap map_hi, map_lo;
   double* alpha = nullptr;  // [n_pairs][nVpad]  exp(4 s E_p e_b)
   double* pinfo = nullptr;  // [n_pairs][4]      E_p, exp(-2 s E_p^2), factorisable flag
   double* tau = nullptr;    // [nVpad][nVpad]    exp(-2 s (e_a + e_b)^2)
-  int2* d_tp = nullptr;
+  double* trange = nullptr; // [nT][2]           min, max of e over the virtuals of a tile
+  void* d_mol = nullptr;    // device MolDesc of this molecule
+  int4* d_items = nullptr;  // single-molecule schedule
+  int* d_begin = nullptr;
 };
 
-struct SplitArgs {
-  const double* eps;
+// One molecule of a (possibly batched) CCVV launch.
+struct MolDesc {
+  const double* eps;      // orbital energies [core | active | virtual]
   double s;
-  Sizes z;
-  int nVpad, kblocks, n_tp, n_items;
-  const int2* pairs;
-  const int2* tps;
-  const double* alpha;
-  const double* pinfo;
-  const double* tau;
-  double* partials;
+  int nC, nA, nV, nVpad, row0, kblocks, n_tp;
+  const double* alpha;    // [pairs][nVpad]  exp(4 s E_p e_b)
+  const double* pinfo;    // [pairs][4]      E_p, exp(-2 s E_p^2), factorisable flag
+  const double* tau;      // [nVpad][nVpad]  exp(-2 s (e_a + e_b)^2)
+  const double* trange;   // [tiles][2]      min, max of e over the virtuals of a tile
+  double* partials;       // one FP64 partial per work item of this molecule
+};
+
+// Work item: x = molecule, y = i << 16 | j, z = A << 16 | B, w = item index within
+// the molecule (pair-major; pair = w / n_tp). Items are stored CTA by CTA
+// (the host scheduler's order); CTA b processes [cta_begin[b], cta_begin[b+1]).
+struct SplitArgs {
+  const MolDesc* mols;
+  const int4* items;
+  const int* cta_begin;
   int* status;
 };
 
@@ -73,22 +89,25 @@ struct SplitArgs {
 // x = slot g1a . slot g1b^T, y = slot g2a . slot g2b^T; duplicate tiles are
 // loaded once (i = j: y not formed; A = B: (j,B) = (j,A), (i,B) = (i,A)).
 struct ItemPlan {
-  int i, j, A, Bt, p;
+  int i, j, A, Bt, p, slot, mol;
   bool two;             // form y
   int nload;            // slots to load: 0 .. nload-1 of the list `load`
   int load[4];          // slot ids to load
   int g1a, g1b, g2a, g2b;
 };
 
-__device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int item) {
+__device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const MolDesc** mdp) {
   ItemPlan ip;
-  ip.p = item / a.n_tp;
-  const int2 ij = a.pairs[ip.p];
-  const int2 ab = a.tps[item % a.n_tp];
-  ip.i = ij.x;
-  ip.j = ij.y;
-  ip.A = ab.x;
-  ip.Bt = ab.y;
+  const int4 it = a.items[idx];
+  const MolDesc* md = a.mols + it.x;
+  *mdp = md;
+  ip.mol = it.x;
+  ip.i = it.y >> 16;
+  ip.j = it.y & 0xffff;
+  ip.A = it.z >> 16;
+  ip.Bt = it.z & 0xffff;
+  ip.slot = it.w;
+  ip.p = it.w / md->n_tp;
   ip.two = ip.i != ip.j;
   const bool dt = ip.A == ip.Bt;
   if (ip.two && !dt) {
@@ -137,9 +156,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
   double* sEps = (double*)(smem + STAGES * STAGE_BYTES + 256);
   double* sAlpha = sEps + TT;
   double* sRed = sAlpha + TT;
+  float* sEpsF = (float*)(sRed + EPI_WARPS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Sizes& z = a.z;
+  const int it0 = a.cta_begin[blockIdx.x], it1 = a.cta_begin[blockIdx.x + 1];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -148,7 +168,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], EPI_WARPS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -174,9 +194,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
-        const ItemPlan ip = plan_item(a, item);
-        for (int kb = 0; kb < a.kblocks; ++kb) {
+      for (int idx = it0; ok && idx < it1; ++idx) {
+        const MolDesc* md;
+        const ItemPlan ip = plan_item(a, idx, &md);
+        const int kblocks = md->kblocks, row0 = md->row0, nVpad = md->nVpad;
+        for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.status)) {
             ok = false;
             break;
@@ -186,7 +208,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           const int kq = kb * (KB_BYTES / (BF16 ? 2 : 4));
           for (int l = 0; l < ip.nload; ++l) {
             const int sl = ip.load[l];
-            const int row = slot_row(ip, sl, a.nVpad);
+            const int row = row0 + slot_row(ip, sl, nVpad);
             tma_load_2d(st + (sl * 2 + 0) * SLOT_BYTES, &map_hi, &full[stage], kq, row);
             tma_load_2d(st + (sl * 2 + 1) * SLOT_BYTES, &map_lo, &full[stage], kq, row);
           }
@@ -221,8 +243,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       uint32_t tphase = 0;
       bool ok = true;
       bool issued = false;
-      for (int item = blockIdx.x; ok && item < a.n_items; item += gridDim.x) {
-        const ItemPlan ip = plan_item(a, item);
+      for (int idx = it0; ok && idx < it1; ++idx) {
+        const MolDesc* md;
+        const ItemPlan ip = plan_item(a, idx, &md);
+        const int kblocks = md->kblocks;
         if (!mbar_wait(&tempty[tbuf], tphase ^ 1u, abort_flag, a.status)) {
           ok = false;
           break;
@@ -230,7 +254,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
         tc_fence_after();
         const uint32_t dx = tmem_base + (uint32_t)(tbuf * 256);
         const uint32_t dy = dx + 128;
-        for (int kb = 0; kb < a.kblocks; ++kb) {
+        for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
             ok = false;
             break;
@@ -282,32 +306,44 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     }
   } else {
     // ------------------------------ epilogue ------------------------------
-    const int et = threadIdx.x - 64;          // 0..127
+    const int et = threadIdx.x - 64;           // 0..255
     const int quarter = warp & 3;              // TMEM lanes this warp may access
     const int row = quarter * 32 + lane;       // tile row held by this thread
-    const int ve = z.nC + z.nA;
+    const int cbeg = ((warp - 2) >> 2) * 64;   // this warp's half of the columns
     int tbuf = 0;
     uint32_t tphase = 0;
-    for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-      const ItemPlan ip = plan_item(a, item);
-      const double* pi = a.pinfo + 4 * ip.p;
+    for (int idx = it0; idx < it1; ++idx) {
+      const MolDesc* md;
+      const ItemPlan ip = plan_item(a, idx, &md);
+      const int nV = md->nV, nVpad = md->nVpad;
+      const int ve = md->nC + md->nA;
+      const double* eps = md->eps;
+      const double* pi = md->pinfo + 4 * ip.p;
       const double E = pi[0], beta = pi[1];
-      const bool fact = pi[2] != 0.0;
-      const double* alpha = a.alpha + (size_t)ip.p * a.nVpad;
-      named_bar(1, 128);
-      {
+      const double* alpha = md->alpha + (size_t)ip.p * nVpad;
+      // every D of the tile pair is away from 0: no per-element guard needed
+      const double dmax = E - md->trange[2 * ip.A] - md->trange[2 * ip.Bt];
+      const double dmin = E - md->trange[2 * ip.A + 1] - md->trange[2 * ip.Bt + 1];
+      const bool fast = (pi[2] != 0.0) && (dmax <= -0.25 || dmin >= 0.25);
+      named_bar(1, 32 * EPI_WARPS);
+      if (et < TT) {
         const int b = ip.Bt * TT + et;
-        sEps[et] = (b < z.nV) ? a.eps[ve + b] : 0.0;
-        sAlpha[et] = (b < z.nV) ? alpha[b] : 0.0;
+        const double eb = (b < nV) ? eps[ve + b] : 0.0;
+        sEps[et] = eb;
+        sEpsF[et] = (float)eb;
+        sAlpha[et] = (b < nV) ? alpha[b] : 0.0;
       }
-      named_bar(1, 128);
+      named_bar(1, 32 * EPI_WARPS);
       const int arow = ip.A * TT + row;
-      const bool rok = arow < z.nV;
-      const double ea = rok ? a.eps[ve + arow] : 0.0;
+      const bool rok = arow < nV;
+      const double ea = rok ? eps[ve + arow] : 0.0;
       const double ca = E - ea;
+      const float caf = (float)ca;
       const double ha = rok ? beta * alpha[arow] : 0.0;
-      const int ncols = min(TT, z.nV - ip.Bt * TT);
-      const double s = a.s;
+      const int ncols = min(TT, nV - ip.Bt * TT);
+      const int cend = min(cbeg + 64, ncols);
+      const double s = md->s;
+      const double* taucol = md->tau + (size_t)(ip.Bt * TT) * nVpad + arow;
 
       bool ok = mbar_wait(&tfull[tbuf], tphase, abort_flag, a.status);
       tc_fence_after();
@@ -315,36 +351,39 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       if (ok) {
         const uint32_t tx = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * 256);
         const uint32_t ty = tx + 128;
-        for (int c0 = 0; c0 < ncols; c0 += 16) {
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
           uint32_t xr[16], yr[16];
           tmem_ld16(tx + c0, xr);
           if (ip.two) tmem_ld16(ty + c0, yr);
           tmem_ld_wait();
           if (!rok) continue;
+          if (fast) {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int cb = c0 + k;
-            if (cb >= ncols) break;
-            const float xf = __uint_as_float(xr[k]);
-            const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
-            const double D = ca - sEps[cb];
-            double R, q;
-            if (fabs(D) >= 0.25) {
-              const double g = fact ? ha * sAlpha[cb] * a.tau[(size_t)(ip.Bt * TT + cb) * a.nVpad + arow]
-                                    : exp(-2.0 * s * D * D);
+            for (int k = 0; k < 16; ++k) {
+              const int cb = c0 + k;
+              if (cb >= cend) break;
+              const float xf = __uint_as_float(xr[k]);
+              const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+              const double D = ca - sEps[cb];
+              const double g = ha * sAlpha[cb] * taucol[(size_t)cb * nVpad];
               float r0f;
-              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
-              const double r0 = (double)r0f;
-              const double e = fma(-D, r0, 1.0);
-              const double R0 = (1.0 - g) * r0;
-              R = fma(R0, e, R0);
-              q = (double)fmaf(xf, xf - yf, yf * yf);
-            } else {
-              R = reg_f1(D, s);
-              const double xd = xf, yd = yf;
-              q = fma(xd, xd - yd, yd * yd);
+              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
+              const double r0 = (double)r0f;             // 1/D to ~2^-22
+              const double e = fma(-D, r0, 1.0);         // Newton-Raphson residual
+              const double R0 = fma(-g, r0, r0);         // (1 - g) / D, seed accuracy
+              const double R = fma(R0, e, R0);           // one Newton step: ~2^-44
+              acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
             }
-            acc = fma(q, R, acc);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int cb = c0 + k;
+              if (cb >= cend) break;
+              const double xd = __uint_as_float(xr[k]);
+              const double yd = ip.two ? (double)__uint_as_float(yr[k]) : xd;
+              const double D = ca - sEps[cb];
+              acc = fma(fma(xd, xd - yd, yd * yd), reg_f1(D, s), acc);
+            }
           }
         }
       }
@@ -359,12 +398,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       // fixed-order CTA sum of the item's contribution
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) sRed[warp - 2] = acc;
-      named_bar(1, 128);
+      named_bar(1, 32 * EPI_WARPS);
       if (et == 0) {
         const double w = (ip.two ? 2.0 : 1.0) * (ip.A < ip.Bt ? 2.0 : 1.0);
-        a.partials[item] = ok ? w * (((sRed[0] + sRed[1]) + sRed[2]) + sRed[3]) : 0.0;
+        double t = 0.0;
+        for (int k = 0; k < EPI_WARPS; ++k) t += sRed[k];
+        md->partials[ip.slot] = ok ? w * t : 0.0;
       }
-      // after an abort the loop keeps running without waits, so that all four
+      // after an abort the loop keeps running without waits, so that all
       // epilogue warps keep meeting at the same named barriers
     }
   }
@@ -391,7 +432,7 @@ __device__ __forceinline__ float tf32_rne(float x) {
 }
 
 template <bool BF16>
-__global__ void split_planes_kernel(const double* __restrict__ B, Sizes z, int nVpad, int Qpad,
+__global__ void split_planes_kernel(const double* __restrict__ B, Sizes z, int nVpad, int Qld,
                                     void* __restrict__ hi, void* __restrict__ lo) {
   __shared__ double t[32][33];
   const int q0 = blockIdx.x * 32, a0 = blockIdx.y * 32, h = blockIdx.z;
@@ -404,7 +445,7 @@ __global__ void split_planes_kernel(const double* __restrict__ B, Sizes z, int n
   for (int r = ty; r < 32; r += 8) {
     const int a = a0 + r, q = q0 + tx;
     const double x = t[tx][r];
-    const size_t o = ((size_t)h * nVpad + a) * Qpad + q;
+    const size_t o = ((size_t)h * nVpad + a) * Qld + q;
     if (BF16) {
       const __nv_bfloat16 xh = __float2bfloat16_rn((float)x);
       const __nv_bfloat16 xl = __float2bfloat16_rn((float)(x - (double)__bfloat162float(xh)));
@@ -425,7 +466,7 @@ __global__ void split_planes_kernel(const double* __restrict__ B, Sizes z, int n
 __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Sizes z,
                                     const int2* __restrict__ pairs, int n_pairs, int nVpad,
                                     double* __restrict__ alpha, double* __restrict__ pinfo,
-                                    double* __restrict__ tau) {
+                                    double* __restrict__ tau, double* __restrict__ trange) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int ve = z.nC + z.nA;
   const size_t na = (size_t)n_pairs * nVpad, nt = (size_t)nVpad * nVpad;
@@ -453,6 +494,29 @@ __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Si
       v = exp(-2.0 * s * t * t);
     }
     tau[r] = v;
+  } else if (k < na + nt + (size_t)(nVpad / TT)) {
+    const int t = (int)(k - na - nt);
+    double lo = 1e300, hi = -1e300;
+    for (int b = t * TT; b < min((t + 1) * TT, z.nV); ++b) {
+      lo = fmin(lo, eps[ve + b]);
+      hi = fmax(hi, eps[ve + b]);
+    }
+    trange[2 * t] = lo;
+    trange[2 * t + 1] = hi;
+  }
+}
+
+// Per-call inputs of the molecules of a launch (eps pointers and s values).
+constexpr int MOL_PER_UPDATE = 64;
+struct MolInputs {
+  const double* eps[MOL_PER_UPDATE];
+  double s[MOL_PER_UPDATE];
+};
+__global__ void mol_inputs_kernel(MolDesc* mols, int first, int n, MolInputs in) {
+  const int k = threadIdx.x;
+  if (k < n) {
+    mols[first + k].eps = in.eps[k];
+    mols[first + k].s = in.s[k];
   }
 }
 
@@ -473,19 +537,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 bool split_supported(const dsrg_plan* p, std::string* why) {
   const Sizes& z = p->z;
   const long long nVpad = (z.nV + TT - 1) / TT * TT;
-  if ((long long)z.nH * nVpad >= (1ll << 31)) {
-    if (why) *why = "too many rows for 32-bit TMA coordinates";
+  if ((long long)z.nH * nVpad >= (1ll << 31) || z.nC >= 65536 || nVpad / TT >= 65536) {
+    if (why) *why = "too many rows for the 32-bit TMA coordinates";
     return false;
   }
   return true;
 }
 
-static bool make_map(CUtensorMap* m, void* ptr, bool bf16, int rows, int Qpad, int kb_elems) {
+bool split_make_map(CUtensorMap* m, void* ptr, bool bf16, long long rows, int Qld, int kb_elems) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int elt = bf16 ? 2 : 4;
-  cuuint64_t dims[2] = {(cuuint64_t)Qpad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)Qpad * elt};
+  cuuint64_t dims[2] = {(cuuint64_t)Qld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Qld * elt};
   cuuint32_t box[2] = {(cuuint32_t)kb_elems, (cuuint32_t)TT};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
@@ -500,7 +564,49 @@ int split_ccvv_blocks(const dsrg_plan* p) {
   return p->n_pairs * (nT * (nT + 1) / 2);
 }
 
-bool split_alloc(dsrg_plan* p) {
+int split_plane_rows(const Sizes& z) { return z.nH * ((z.nV + TT - 1) / TT * TT); }
+int split_plane_qpad(const Sizes& z) { return (z.Q + 63) / 64 * 64; }
+
+// Static schedule: items in their global order (molecule, pair, tile pair) are
+// dealt to the CTA with the least accumulated cost (ties: lowest index), which
+// is round-robin for uniform costs (operand tiles of one pair stay close in
+// time, so they are re-read from L2) and balances uneven molecules. Cost of an
+// item: its K blocks times its GEMM count, plus a fixed epilogue share.
+void split_schedule(const std::vector<int4>& items, const std::vector<double>& cost, int ncta,
+                    std::vector<int4>& out, std::vector<int>& begin) {
+  std::vector<double> load(ncta, 0.0);
+  std::vector<std::vector<int>> lists(ncta);
+  for (size_t k = 0; k < items.size(); ++k) {
+    int best = 0;
+    for (int c = 1; c < ncta; ++c)
+      if (load[c] < load[best]) best = c;
+    load[best] += cost[k];
+    lists[best].push_back((int)k);
+  }
+  out.clear();
+  begin.assign(ncta + 1, 0);
+  for (int c = 0; c < ncta; ++c) {
+    begin[c] = (int)out.size();
+    for (int k : lists[c]) out.push_back(items[k]);
+  }
+  begin[ncta] = (int)out.size();
+}
+
+void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
+                     std::vector<double>& cost) {
+  const int nT = (z.nV + TT - 1) / TT;
+  int slot = 0;
+  for (int i = 0; i < z.nC; ++i)
+    for (int j = i; j < z.nC; ++j)
+      for (int A = 0; A < nT; ++A)
+        for (int B = A; B < nT; ++B) {
+          items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, slot++));
+          cost.push_back((double)kblocks * (i == j ? 1.0 : 2.0) + 24.0);
+        }
+}
+
+bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
+                    const CUtensorMap* shared_hi, const CUtensorMap* shared_lo) {
   const Sizes& z = p->z;
   SplitWs* w = new SplitWs();
   p->split = w;
@@ -509,31 +615,70 @@ bool split_alloc(dsrg_plan* p) {
   w->kb_elems = KB_BYTES / w->elt;
   w->nT = (z.nV + TT - 1) / TT;
   w->nVpad = w->nT * TT;
-  w->Qpad = (z.Q + 63) / 64 * 64;
+  w->Qpad = split_plane_qpad(z);
   w->rows = z.nH * w->nVpad;
   w->n_tp = w->nT * (w->nT + 1) / 2;
   w->n_items = p->n_pairs * w->n_tp;
+  w->Qld = Qld;
+  w->row_base = row_base;
+  const size_t plane = (size_t)w->rows * Qld * w->elt;
+  bool ok = true;
+  if (hi) {
+    w->hi = hi;
+    w->lo = lo;
+  } else {
+    ok = plan_alloc(p, &w->hi, plane) && plan_alloc(p, &w->lo, plane);
+  }
+  ok = ok && plan_alloc(p, (void**)&w->alpha, (size_t)p->n_pairs * w->nVpad * 8) &&
+       plan_alloc(p, (void**)&w->pinfo, (size_t)p->n_pairs * 4 * 8) &&
+       plan_alloc(p, (void**)&w->tau, (size_t)w->nVpad * w->nVpad * 8) &&
+       plan_alloc(p, (void**)&w->trange, (size_t)w->nT * 2 * 8) &&
+       plan_alloc(p, (void**)&w->d_mol, sizeof(MolDesc));
+  if (!ok) return false;
+  if (!hi && (cudaMemset(w->hi, 0, plane) != cudaSuccess || cudaMemset(w->lo, 0, plane) != cudaSuccess))
+    return false;
+  // this molecule's own maps (CAVV kernel, single-molecule CCVV)
+  if (!split_make_map(&w->map_hi, w->hi, bf16, w->rows, Qld, w->kb_elems)) return false;
+  if (!split_make_map(&w->map_lo, w->lo, bf16, w->rows, Qld, w->kb_elems)) return false;
+  (void)shared_hi;
+  (void)shared_lo;
+  // descriptor (eps and s are filled per call)
+  MolDesc md;
+  md.eps = nullptr;
+  md.s = 0.0;
+  md.nC = z.nC;
+  md.nA = z.nA;
+  md.nV = z.nV;
+  md.nVpad = w->nVpad;
+  md.row0 = 0;
+  md.kblocks = w->Qpad / w->kb_elems;
+  md.n_tp = w->n_tp;
+  md.alpha = w->alpha;
+  md.pinfo = w->pinfo;
+  md.tau = w->tau;
+  md.trange = w->trange;
+  md.partials = p->d_partials + p->segs[p->seg_ccvv].begin;
+  if (cudaMemcpy(w->d_mol, &md, sizeof(MolDesc), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+  // single-molecule schedule
+  std::vector<int4> items, sched;
+  std::vector<double> cost;
+  std::vector<int> begin;
+  split_item_list(z, 0, md.kblocks, items, cost);
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
-  w->grid = w->n_items < nsm ? w->n_items : nsm;
-  const size_t plane = (size_t)w->rows * w->Qpad * w->elt;
-  bool ok = plan_alloc(p, &w->hi, plane) && plan_alloc(p, &w->lo, plane) &&
-            plan_alloc(p, (void**)&w->alpha, (size_t)p->n_pairs * w->nVpad * 8) &&
-            plan_alloc(p, (void**)&w->pinfo, (size_t)p->n_pairs * 4 * 8) &&
-            plan_alloc(p, (void**)&w->tau, (size_t)w->nVpad * w->nVpad * 8) &&
-            plan_alloc(p, (void**)&w->d_tp, (size_t)w->n_tp * sizeof(int2));
+  w->grid = (int)items.size() < nsm ? (int)items.size() : nsm;
+  split_schedule(items, cost, w->grid, sched, begin);
+  ok = plan_alloc(p, (void**)&w->d_items, sched.size() * sizeof(int4)) &&
+       plan_alloc(p, (void**)&w->d_begin, begin.size() * sizeof(int));
   if (!ok) return false;
-  std::vector<int2> tp;
-  for (int A = 0; A < w->nT; ++A)
-    for (int B = A; B < w->nT; ++B) tp.push_back(make_int2(A, B));
-  if (cudaMemcpy(w->d_tp, tp.data(), tp.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
-    return false;
-  // zero the planes once: padding rows/columns stay zero
-  if (cudaMemset(w->hi, 0, plane) != cudaSuccess || cudaMemset(w->lo, 0, plane) != cudaSuccess)
-    return false;
-  if (!make_map(&w->map_hi, w->hi, bf16, w->rows, w->Qpad, w->kb_elems)) return false;
-  if (!make_map(&w->map_lo, w->lo, bf16, w->rows, w->Qpad, w->kb_elems)) return false;
-  return true;
+  return cudaMemcpy(w->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemcpy(w->d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
+}
+
+bool split_alloc(dsrg_plan* p) {
+  return split_alloc_at(p, nullptr, nullptr, split_plane_qpad(p->z), 0, nullptr, nullptr);
 }
 
 int split_qpad(const dsrg_plan* p) { return p->split->Qpad; }
@@ -547,51 +692,100 @@ void split_free(dsrg_plan* p) {
   p->split = nullptr;
 }
 
-static size_t split_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024 + 256 + 3 * TT * 8 + 64; }
+static size_t split_smem_bytes() {
+  return (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (2 * TT + EPI_WARPS) * 8 + TT * 4 + 64;
+}
 
-cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, double s) {
+// Stage this molecule's planes and pair tables (no CCVV launch).
+cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double s) {
   SplitWs* w = p->split;
   const Sizes& z = p->z;
   const bool bf16 = p->prec == DSRG_PREC_BF16X3;
   {
     dim3 grid(w->Qpad / 32, w->nVpad / 32, z.nH), block(32, 8);
     if (bf16)
-      split_planes_kernel<true><<<grid, block, 0, p->stream>>>(B, z, w->nVpad, w->Qpad, w->hi, w->lo);
+      split_planes_kernel<true><<<grid, block, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
     else
-      split_planes_kernel<false><<<grid, block, 0, p->stream>>>(B, z, w->nVpad, w->Qpad, w->hi, w->lo);
+      split_planes_kernel<false><<<grid, block, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
     DSRG_LAUNCH_CHECK(p);
   }
   {
-    const size_t n = (size_t)p->n_pairs * w->nVpad + (size_t)w->nVpad * w->nVpad;
+    const size_t n = (size_t)p->n_pairs * w->nVpad + (size_t)w->nVpad * w->nVpad + w->nT;
     split_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
-        eps, s, z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau);
+        eps, s, z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange);
     DSRG_LAUNCH_CHECK(p);
   }
+  return cudaSuccess;
+}
+
+size_t split_mol_desc_bytes() { return sizeof(MolDesc); }
+int split_kb_elems(bool bf16) { return KB_BYTES / (bf16 ? 2 : 4); }
+
+// Descriptor of plan p's molecule for a launch over a shared plane buffer in
+// which its rows start at row0.
+void split_fill_mol_desc(const dsrg_plan* p, long long row0, void* out) {
+  const SplitWs* w = p->split;
+  MolDesc md;
+  md.eps = nullptr;
+  md.s = 0.0;
+  md.nC = p->z.nC;
+  md.nA = p->z.nA;
+  md.nV = p->z.nV;
+  md.nVpad = w->nVpad;
+  md.row0 = (int)row0;
+  md.kblocks = w->Qpad / w->kb_elems;
+  md.n_tp = w->n_tp;
+  md.alpha = w->alpha;
+  md.pinfo = w->pinfo;
+  md.tau = w->tau;
+  md.trange = w->trange;
+  md.partials = p->d_partials + p->segs[p->seg_ccvv].begin;
+  memcpy(out, &md, sizeof(MolDesc));
+}
+
+cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols_v, int first, int n,
+                             const double* const* eps, const double* s) {
+  MolDesc* d_mols = (MolDesc*)d_mols_v;
+  for (int b = 0; b < n; b += MOL_PER_UPDATE) {
+    MolInputs in;
+    const int m = (n - b) < MOL_PER_UPDATE ? (n - b) : MOL_PER_UPDATE;
+    for (int k = 0; k < m; ++k) {
+      in.eps[k] = eps[b + k];
+      in.s[k] = s[b + k];
+    }
+    mol_inputs_kernel<<<1, MOL_PER_UPDATE, 0, p->stream>>>(d_mols, first + b, m, in);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,
+                              const void* d_mols, const int4* d_items, const int* d_begin,
+                              int grid, bool bf16) {
   SplitArgs a;
-  a.eps = eps;
-  a.s = s;
-  a.z = z;
-  a.nVpad = w->nVpad;
-  a.kblocks = w->Qpad / w->kb_elems;
-  a.n_tp = w->n_tp;
-  a.n_items = w->n_items;
-  a.pairs = p->d_pairs;
-  a.tps = w->d_tp;
-  a.alpha = w->alpha;
-  a.pinfo = w->pinfo;
-  a.tau = w->tau;
-  a.partials = p->d_partials + p->segs[p->seg_ccvv].begin;
+  a.mols = (const MolDesc*)d_mols;
+  a.items = d_items;
+  a.cta_begin = d_begin;
   a.status = p->d_status;
   const size_t sm = split_smem_bytes();
   if (bf16) {
     cudaFuncSetAttribute(ccvv_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    ccvv_split_kernel<true><<<w->grid, SPLIT_THREADS, sm, p->stream>>>(w->map_hi, w->map_lo, a);
+    ccvv_split_kernel<true><<<grid, SPLIT_THREADS, sm, p->stream>>>(mh, ml, a);
   } else {
     cudaFuncSetAttribute(ccvv_split_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    ccvv_split_kernel<false><<<w->grid, SPLIT_THREADS, sm, p->stream>>>(w->map_hi, w->map_lo, a);
+    ccvv_split_kernel<false><<<grid, SPLIT_THREADS, sm, p->stream>>>(mh, ml, a);
   }
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
+}
+
+cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, double s) {
+  SplitWs* w = p->split;
+  cudaError_t e = split_stage(p, B, eps, s);
+  if (e != cudaSuccess) return e;
+  if ((e = split_set_inputs(p, w->d_mol, 0, 1, &eps, &s)) != cudaSuccess) return e;
+  return split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, w->d_items,
+                           w->d_begin, w->grid, p->prec == DSRG_PREC_BF16X3);
 }
 
 }  // namespace dsrg

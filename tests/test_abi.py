@@ -17,7 +17,7 @@ def _declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1603_00561_gb300.build import build
+    from paper_1603_00561_gb300._buildlib import build
     path = build()
     return ctypes.CDLL(path)
 

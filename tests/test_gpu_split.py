@@ -8,7 +8,9 @@ instruction. With 3 instructions per K step of 8 (TF32) or 16 (BF16)
 auxiliary functions, the relative error of E_CCVV is bounded by
     2 * (3 * ceil(naux / K)) * 2^-24        (the factor 2: E is quadratic in v)
 which is the tolerance used here; the measured errors sit well inside it.
-All other blocks run the FP64 kernels and keep the FP64 bar (1e-10).
+CAVV (for nA <= 2) and the (A,A|V,V) integrals of the active block come from
+the same planes and carry the same bound; CCAV runs on FP32 CUDA cores with
+the same hi/lo split (round-to-nearest accumulation), well inside the bound.
 """
 import math
 
@@ -66,7 +68,7 @@ def test_split_blocks_small(pk, prec, nC, nA, nV, Q, s, seed):
     for k in BLOCKS:
         rel = abs(gpu[k] - ref[k]) / max(abs(ref[k]), 1e-300)
         print(f"{prec} {nC}/{nA}/{nV}/{Q} {k:7s} gpu={gpu[k]:+.12e} oracle={ref[k]:+.12e} rel={rel:.2e}")
-        bar = tol if k in ("ccvv", "total") else 1e-10
+        bar = tol
         if ref[k] == 0.0:
             assert gpu[k] == 0.0
         else:
@@ -84,8 +86,8 @@ def test_split_vtz_against_fp64_path(pk, prec):
     rel = abs(gs["ccvv"] - g64["ccvv"]) / abs(g64["ccvv"])
     print(prec, "vtz ccvv rel vs fp64", rel)
     assert rel <= split_tol(prec, p.naux)
-    for k in ("cavv", "ccav", "active"):
-        assert gs[k] == g64[k]
+    for k in ("cavv", "ccav", "active", "total"):
+        assert abs(gs[k] - g64[k]) / abs(g64[k]) <= split_tol(prec, p.naux), k
 
 
 @pytest.mark.parametrize("s", [0.1, 0.5, 1.0])
@@ -101,7 +103,7 @@ def test_split_v5z_s_sweep(pk, s):
     for k in BLOCKS:
         rel = abs(gs[k] - g64[k]) / abs(g64[k])
         print(f"v5z s={s} {k:7s} split={gs[k]:+.12e} fp64={g64[k]:+.12e} rel={rel:.2e}")
-        assert rel <= (tol if k in ("ccvv", "total") else 1e-14)
+        assert rel <= tol
     sample = [(0, 0), (3, 19), (23, 23)]
     ref = odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample).numpy()
     for (m, n) in sample:
