@@ -178,6 +178,25 @@ dsrg_status_t dsrg_batch_sync(dsrg_batch_t *batch);
 int32_t dsrg_batch_launch_count(const dsrg_batch_t *batch);
 const char *dsrg_batch_last_error(const dsrg_batch_t *batch);
 
+/* E_CCVV without any device allocation (the paper has no counterpart; this is a
+ * service to callers that cannot call cudaMalloc, e.g. code running inside a
+ * memory pool it does not own or a host that forbids allocation on its hot
+ * path). Same value as out[0] of dsrg_mrpt2_energy with a DSRG_PREC_FP64 plan
+ * (same FP64 kernel; the final sum may differ in the last bits). B and eps are
+ * device arrays as above, out_dev one device double, work queued on
+ * cuda_stream. Scratch (work lists and per-item partial sums) lives in a fixed
+ * device array of 147456 doubles (1.125 MiB) inside the library, held on every
+ * GPU that loads it until the process exits; sizes that do not fit (more than
+ * 8192 core pairs, more than 8192 pairs of 64-wide virtual tiles, or more than
+ * 131072 items in total) return DSRG_ERR_UNSUPPORTED. Every scratch slot a
+ * call reads is written earlier in the same call, so nothing needs clearing.
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller. The
+ * first call on a device looks up the array's device address; make it before
+ * any stream capture. */
+dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t *sz, const double *B, const double *eps,
+                                       double s, double *out_dev, void *cuda_stream);
+
 /* Wait for the plan's stream and report any device-side condition recorded
  * since the last call (DSRG_ERR_TIMEOUT), then clear it. */
 dsrg_status_t dsrg_plan_sync(dsrg_plan_t *plan);

@@ -23,7 +23,7 @@ EXPORTS = [
     "dsrg_plan_sync", "dsrg_plan_last_launch_count", "dsrg_plan_workspace_bytes",
     "dsrg_status_string", "dsrg_plan_last_error",
     "dsrg_batch_plan", "dsrg_batch_destroy", "dsrg_mrpt2_energy_batched", "dsrg_batch_sync",
-    "dsrg_batch_launch_count", "dsrg_batch_last_error",
+    "dsrg_batch_launch_count", "dsrg_batch_last_error", "dsrg_ccvv_energy_noalloc",
 ]
 
 
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_batch_launch_count.restype = C.c_int32
     lib.dsrg_batch_last_error.argtypes = [vp]
     lib.dsrg_batch_last_error.restype = C.c_char_p
+    lib.dsrg_ccvv_energy_noalloc.argtypes = [C.POINTER(Sizes), vp, vp, C.c_double, vp, vp]
+    lib.dsrg_ccvv_energy_noalloc.restype = st
     _ = dp
     _lib = lib
     return lib
