@@ -186,6 +186,75 @@ def cpu_baseline(workload, seconds=12.0):
                       f"{dt:.1f} s"}
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_gradient(pk, torch):
+    """E + dE/dB + dE/deps + dE/ds at the cc-pVTZ size, per molecule, FP64 and BF16x3 plans."""
+    from dsrg_synth import make_problem
+    cfg = WORKLOADS["naphthyne-vtz-398"]
+    p = make_problem(seed=0, **cfg)
+    dev = pk.to_device(p)
+    res = {"workload": "naphthyne-vtz-398"}
+    for prec in ("fp64", "bf16x3"):
+        plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, grad=True)
+        plan.energy_grad(*dev, p.s)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(3):
+            plan.energy_grad(*dev, p.s)
+        e1.record()
+        torch.cuda.synchronize()
+        res[f"{prec}_ms_per_gradient"] = e0.elapsed_time(e1) / 3
+        plan.close()
+    return res
+
+
+def time_batch(pk, torch, nmol, prec):
+    """A batch of nmol molecules of the uneven recipe (seeds 0..nmol-1) in one call,
+    against one-by-one FP64 plans."""
+    from dsrg_synth import batch_sizes, make_problem
+    mols = [make_problem(seed=k, s=0.5, **batch_sizes(k)) for k in range(nmol)]
+    dev = [pk.to_device(m) for m in mols]
+    flops = sum(ccvv_flops(m.ncore, m.nvirt, m.naux) for m in mols)
+    b = pk.Batch([(m.ncore, m.nactive, m.nvirt, m.naux) for m in mols], precision=prec)
+    svals = [m.s for m in mols]
+    out = b.energy(dev, svals)          # captures the graph
+    b.energy(dev, svals, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(3):
+        b.energy(dev, svals, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 3 / 1e3
+    b.sync()
+    # one-by-one FP64 plans (each molecule its own plan and launches)
+    plans = [pk.Plan(m.ncore, m.nactive, m.nvirt, m.naux, precision="fp64") for m in mols]
+    o64 = [pl.energy(*d, m.s) for pl, d, m in zip(plans, dev, mols)]
+    torch.cuda.synchronize()
+    e0.record()
+    for pl, d, m, o in zip(plans, dev, mols, o64):
+        pl.energy(*d, m.s, out=o)
+    e1.record()
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    ob = out.cpu().numpy()
+    err = max(abs(ob[k][4] - float(o64[k][4])) / abs(float(o64[k][4])) for k in range(nmol))
+    res = {"n_mol": nmol, "precision": prec, "ms_per_batch": tb * 1e3,
+           "molecules_per_s": nmol / tb, "aggregate_ccvv_tflops": flops / tb / 1e12,
+           "graph_kernel_launches": b.launch_count(),
+           "fp64_one_by_one_ms": t64 * 1e3, "fp64_one_by_one_molecules_per_s": nmol / t64,
+           "max_rel_err_total_vs_fp64": err}
+    b.close()
+    for pl in plans:
+        pl.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,6 +266,10 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--with-grad", action="store_true",
+                    help="also time the gradient at the cc-pVTZ size (FP64 and split)")
+    ap.add_argument("--with-batch", type=int, default=0, metavar="NMOL",
+                    help="also time a batch of NMOL uneven molecules vs one-by-one FP64 plans")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -331,6 +404,12 @@ def main():
                     "abs_err_vs_fp64_eh": {k: abs(a - b) for k, a, b in zip(pk.BLOCKS, energies, r64)}}
         p64.close()
 
+    extra = {}
+    if args.with_grad:
+        extra["gradient"] = time_gradient(pk, torch)
+    if args.with_batch:
+        extra["batch"] = time_batch(pk, torch, args.with_batch, prec)
+
     if rank == 0:
         cb = None
         if not args.no_cpu_baseline and world == 1:
@@ -355,6 +434,7 @@ def main():
         }
         if fp64_cmp:
             line.update(fp64_cmp)
+        line.update(extra)
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
