@@ -97,125 +97,16 @@ __global__ void __launch_bounds__(256) ccav_fp64_kernel(
   if (threadIdx.x == 0) partials[e] = tot;
 }
 
-// F3 in the split-precision modes: same contraction and epilogue as above,
-// with the products over Q in FP32 on CUDA cores: B = hi + lo (two FP32
-// numbers), Z += hi*hi + hi*lo + lo*hi with round-to-nearest FP32 FMAs.
-// One CTA per group of CCAV_E virtual orbitals.
-constexpr int CCAV_E = 4;
-constexpr int KC_F32 = 16;
-
-__global__ void __launch_bounds__(256) ccav_f32x3_kernel(
-    const double* __restrict__ B, const double* __restrict__ eps, const double* __restrict__ G,
-    double s, Sizes z, double* __restrict__ partials) {
-  extern __shared__ float fsm[];
-  const int nC = z.nC, nA = z.nA;
-  const int nz = nA * nC * nC * CCAV_E;
-  float* Z = fsm;                                   // [nA][nC][nC][E]
-  float* eH = Z + nz;                               // [KC][nC][E]
-  float* eL = eH + KC_F32 * nC * CCAV_E;
-  float* uH = eL + KC_F32 * nC * CCAV_E;            // [KC][nC][nA]
-  float* uL = uH + KC_F32 * nC * nA;
-  __shared__ double red[8];
-  const int e0 = blockIdx.x * CCAV_E;
-  for (int k = threadIdx.x; k < nz; k += 256) Z[k] = 0.f;
-  const int ne = KC_F32 * nC * CCAV_E, nu = KC_F32 * nC * nA;
-  for (int q0 = 0; q0 < z.Q; q0 += KC_F32) {
-    __syncthreads();
-    for (int k = threadIdx.x; k < ne + nu; k += 256) {
-      double v = 0.0;
-      if (k < ne) {
-        const int qq = k / (nC * CCAV_E), r = k % (nC * CCAV_E), m = r / CCAV_E, t = r % CCAV_E;
-        const int q = q0 + qq, e = e0 + t;
-        if (q < z.Q && e < z.nV) v = B[bidx(z, q, m, nA + e)];
-        const float h = (float)v;
-        eH[k] = h;
-        eL[k] = (float)(v - (double)h);
-      } else {
-        const int kk = k - ne;
-        const int qq = kk / (nC * nA), r = kk % (nC * nA), n = r / nA, u = r % nA;
-        const int q = q0 + qq;
-        if (q < z.Q) v = B[bidx(z, q, n, u)];
-        const float h = (float)v;
-        uH[kk] = h;
-        uL[kk] = (float)(v - (double)h);
-      }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nz; k += 256) {
-      const int t = k % CCAV_E, r = k / CCAV_E;
-      const int n = r % nC, m = (r / nC) % nC, u = r / (nC * nC);
-      float acc = Z[k];
-#pragma unroll 4
-      for (int qq = 0; qq < KC_F32; ++qq) {
-        const int ie = (qq * nC + m) * CCAV_E + t, iu = (qq * nC + n) * nA + u;
-        const float ah = eH[ie], al = eL[ie], bh = uH[iu], bl = uL[iu];
-        acc = fmaf(ah, bh, acc);
-        acc = fmaf(ah, bl, acc);
-        acc = fmaf(al, bh, acc);
-      }
-      Z[k] = acc;
-    }
-  }
-  __syncthreads();
-  double acc = 0.0;
-  for (int r = threadIdx.x; r < nC * nC * CCAV_E; r += 256) {
-    const int t = r % CCAV_E, mn = r / CCAV_E, m = mn / nC, n = mn % nC;
-    const int e = e0 + t;
-    if (e >= z.nV) continue;
-    const double base = eps[m] + eps[n] - eps[nC + nA + e];
-    double Rv[NA_MAX], Rt[NA_MAX];
-    for (int u = 0; u < nA; ++u) {
-      const double D = base - eps[nC + u];
-      Rv[u] = reg_v(D, s);
-      Rt[u] = reg_t(D, s);
-    }
-    auto Zf = [&](int u, int a, int b) {
-      return (double)Z[((u * nC + a) * nC + b) * CCAV_E + t];
-    };
-    for (int u = 0; u < nA; ++u) {
-      const double zu = 2.0 * Zf(u, m, n) - Zf(u, n, m);
-      double c = 0.0;
-      for (int v = 0; v < nA; ++v) {
-        const double Hh = (u == v ? 2.0 : 0.0) - G[u * nA + v];
-        c = fma(Hh * Rv[v], Zf(v, m, n), c);
-      }
-      acc = fma(c, zu * Rt[u], acc);
-    }
-  }
-  const double tot = block_sum<256>(acc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-}
-
-static size_t ccav_f32_smem(const Sizes& z) {
-  return sizeof(float) * ((size_t)z.nA * z.nC * z.nC * CCAV_E + 2 * (size_t)KC_F32 * z.nC * CCAV_E +
-                          2 * (size_t)KC_F32 * z.nC * z.nA);
-}
-
-bool ccav_f32_used(const dsrg_plan* p) {
-  return p->prec != DSRG_PREC_FP64 && p->z.nA > 0 && ccav_f32_smem(p->z) <= 160 * 1024;
-}
-
 static size_t ccav_smem(const Sizes& z) {
   return sizeof(double) * ((size_t)z.nA * z.nC * z.nC + (size_t)KC_CCAV * z.nC * (1 + z.nA));
 }
 
-int ccav_fp64_blocks(const dsrg_plan* p) {
-  if (p->z.nA == 0) return 0;
-  return ccav_f32_used(p) ? (p->z.nV + CCAV_E - 1) / CCAV_E : p->z.nV;
-}
+int ccav_fp64_blocks(const dsrg_plan* p) { return p->z.nA == 0 ? 0 : p->z.nV; }
 
 cudaError_t launch_ccav_fp64(dsrg_plan* p, const double* B, const double* eps, const double* G,
                              double s) {
   const Segment& sg = p->segs[p->seg_ccav];
   if (sg.count == 0) return cudaSuccess;
-  if (ccav_f32_used(p)) {
-    const size_t smf = ccav_f32_smem(p->z);
-    cudaFuncSetAttribute(ccav_f32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-    ccav_f32x3_kernel<<<sg.count, 256, smf, p->stream>>>(B, eps, G, s, p->z,
-                                                        p->d_partials + sg.begin);
-    DSRG_LAUNCH_CHECK(p);
-    return cudaSuccess;
-  }
   const size_t sm = ccav_smem(p->z);
   cudaFuncSetAttribute(ccav_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ccav_fp64_kernel<<<sg.count, 256, sm, p->stream>>>(B, eps, G, s, p->z,
@@ -452,7 +343,7 @@ __global__ void __launch_bounds__(256) gram_aavv_kernel(const double* __restrict
 
 // P1[xu][yv] = sum_ef M_xu[ef] M_yv[ef] R, P2[xu][yv] = sum_ef M_xu[ef] M_vy[ef] R
 // (M_vy[e,f] = M_yv[f,e]) with R = (1 + exp(-s D_xu^2)) (1 - exp(-s D_yv^2))/D_yv.
-constexpr int ACTVV_BLOCKS = 48;
+constexpr int ACTVV_BLOCKS = 152;
 
 __global__ void __launch_bounds__(256) actvv_kernel(const double* __restrict__ eps, double s,
                                                     Sizes z, const double* __restrict__ M,
@@ -481,6 +372,55 @@ __global__ void __launch_bounds__(256) actvv_kernel(const double* __restrict__ e
   if (threadIdx.x == 0) {
     part[((size_t)blockIdx.x * 2 + 0) * nA4 + c] = t1;
     part[((size_t)blockIdx.x * 2 + 1) * nA4 + c] = t2;
+  }
+}
+
+// Same sums for small active spaces, with the regulators of each active pair
+// evaluated once per (e,f): Rv(D_xu) and Rt(D_yv) for the nA^2 pairs, then the
+// nA^4 products P1 += (M_xu Rv_xu)(M_yv Rt_yv), P2 += (M_xu Rv_xu)(M_vy Rt_yv).
+template <int NA>
+__global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restrict__ eps, double s,
+                                                          Sizes z, const double* __restrict__ M,
+                                                          double* __restrict__ part) {
+  constexpr int NA2 = NA * NA, NA4 = NA2 * NA2;
+  __shared__ double red[8];
+  const size_t nV2 = (size_t)z.nV * z.nV;
+  const int ve = z.nC + z.nA;
+  double Ep[NA2];
+#pragma unroll
+  for (int p = 0; p < NA2; ++p) Ep[p] = eps[z.nC + p / NA] + eps[z.nC + p % NA];
+  double acc1[NA4], acc2[NA4];
+#pragma unroll
+  for (int c = 0; c < NA4; ++c) acc1[c] = acc2[c] = 0.0;
+  for (size_t k = (size_t)blockIdx.x * 256 + threadIdx.x; k < nV2; k += (size_t)gridDim.x * 256) {
+    const int e = (int)(k / z.nV), f = (int)(k % z.nV);
+    const double ef = eps[ve + e] + eps[ve + f];
+    double mr[NA2], mq[NA2], m[NA2];
+#pragma unroll
+    for (int p = 0; p < NA2; ++p) m[p] = M[(size_t)p * nV2 + k];
+#pragma unroll
+    for (int p = 0; p < NA2; ++p) {
+      const double D = Ep[p] - ef;
+      mr[p] = m[p] * reg_v(D, s);
+      mq[p] = reg_t(D, s);
+    }
+#pragma unroll
+    for (int p = 0; p < NA2; ++p)
+#pragma unroll
+      for (int q = 0; q < NA2; ++q) {
+        const int qt = (q % NA) * NA + q / NA;
+        acc1[p * NA2 + q] = fma(mr[p], m[q] * mq[q], acc1[p * NA2 + q]);
+        acc2[p * NA2 + q] = fma(mr[p], m[qt] * mq[q], acc2[p * NA2 + q]);
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < NA4; ++c) {
+    const double t1 = block_sum<256>(acc1[c], red);
+    const double t2 = block_sum<256>(acc2[c], red);
+    if (threadIdx.x == 0) {
+      part[((size_t)blockIdx.x * 2 + 0) * NA4 + c] = t1;
+      part[((size_t)blockIdx.x * 2 + 1) * NA4 + c] = t2;
+    }
   }
 }
 
@@ -785,13 +725,13 @@ cudaError_t launch_gram_aavv_fp64(dsrg_plan* p, const double* B) {
 }
 
 cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                          const double* L, double s, bool gram_done) {
+                          const double* L, double s, bool ints_ready) {
   const Sizes& z = p->z;
   if (z.nA == 0) return cudaSuccess;
   ActiveWs& w = p->act;
   const ActDims d = act_dims(z);
   cudaStream_t st = p->stream;
-  {
+  if (!ints_ready) {
     const size_t n = 2 * (size_t)z.nH * z.nA * z.nA * z.nP + (size_t)z.nH * z.nA * z.nH * z.nA;
     small_ints_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(B, z, w.K1, w.K2, w.K3);
     DSRG_LAUNCH_CHECK(p);
@@ -811,14 +751,21 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     ti_kernel<<<(unsigned)((w.w1n + 255) / 256), 256, 0, st>>>(z, w.W1 + w.w1n, w.gA, w.Ti, w.w1n);
     DSRG_LAUNCH_CHECK(p);
   }
-  if (!gram_done) {
+  if (!ints_ready) {
     cudaError_t e = launch_gram_aavv_fp64(p, B);
     if (e != cudaSuccess) return e;
   }
   const int nA4 = z.nA * z.nA * z.nA * z.nA;
   {
-    dim3 grid(ACTVV_BLOCKS, nA4);
-    actvv_kernel<<<grid, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+    if (z.nA <= 2) {
+      if (z.nA == 1)
+        actvv_small_kernel<1><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+      else
+        actvv_small_kernel<2><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+    } else {
+      dim3 grid(ACTVV_BLOCKS, nA4);
+      actvv_kernel<<<grid, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+    }
     DSRG_LAUNCH_CHECK(p);
     actvv_reduce_kernel<<<(2 * nA4 + 127) / 128, 128, 0, st>>>(nA4, ACTVV_BLOCKS, w.P12part, w.P12);
     DSRG_LAUNCH_CHECK(p);

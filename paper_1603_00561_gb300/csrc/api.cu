@@ -53,7 +53,7 @@ static dsrg_status_t cuda_fail(dsrg_plan* p, cudaError_t e, const char* where) {
 
 static void free_all(dsrg_plan* p) {
   if (p->split) split_free(p);
-  if (p->cavv_state) cavv_split_free(p);
+  if (p->rest) rest_free(p);
   if (p->grad) grad_free(p);
   for (void* a : p->allocs) cudaFree(a);
   p->allocs.clear();
@@ -140,12 +140,12 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
   p->segs.push_back(Segment{np, nccvv, BLK_CCVV});
   p->seg_ccvv = 0;
   np += nccvv;
-  p->cavv_tc = (prec != DSRG_PREC_FP64) && cavv_split_supported(p);
-  const int ncavv = p->cavv_tc ? cavv_split_blocks(p) : cavv_fp64_blocks(p);
+  p->rest_tc = (prec != DSRG_PREC_FP64) && z.nA > 0 && rest_supported(z);
+  const int ncavv = p->rest_tc ? rest_cavv_blocks(p) : cavv_fp64_blocks(p);
   p->segs.push_back(Segment{np, ncavv, BLK_CAVV});
   p->seg_cavv = 1;
   np += ncavv;
-  const int nccav = ccav_fp64_blocks(p);
+  const int nccav = p->rest_tc ? rest_ccav_blocks(p) : ccav_fp64_blocks(p);
   p->segs.push_back(Segment{np, nccav, BLK_CCAV});
   p->seg_ccav = 2;
   np += nccav;
@@ -163,7 +163,7 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
   if (ok && prec != DSRG_PREC_FP64)
     ok = share ? split_alloc_at(p, share->hi, share->lo, share->Qld, share->row_base, nullptr, nullptr)
                : split_alloc(p);
-  if (ok && p->cavv_tc) ok = cavv_split_alloc(p);
+  if (ok && p->rest_tc) ok = rest_alloc(p, share ? share->y : nullptr);
   if (ok && (flags & DSRG_PLAN_GRAD)) ok = grad_alloc(p);
   if (ok && (flags & DSRG_PLAN_HOST_IO)) {
     const size_t nb = (size_t)z.Q * z.nH * z.nP;
@@ -246,13 +246,14 @@ namespace dsrg {
 dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
                        const double* L, double s, double* out) {
   cudaError_t e;
-  if (p->cavv_tc)
-    e = launch_split_cavv(p, eps, G, s);  // also forms the (A,A|V,V) integrals
-  else
-    e = launch_cavv_fp64(p, B, eps, G, s);
-  if (e != cudaSuccess) return cuda_fail(p, e, "cavv");
-  if ((e = launch_ccav_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "ccav");
-  if ((e = launch_active(p, B, eps, G, L, s, p->cavv_tc)) != cudaSuccess)
+  if (p->rest_tc) {
+    // one tensor-core GEMM feeds CAVV, CCAV and the active-block integrals
+    if ((e = launch_split_rest(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv/ccav");
+  } else {
+    if ((e = launch_cavv_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv");
+    if ((e = launch_ccav_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "ccav");
+  }
+  if ((e = launch_active(p, B, eps, G, L, s, p->rest_tc)) != cudaSuccess)
     return cuda_fail(p, e, "active");
   if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
   return DSRG_OK;
@@ -313,10 +314,9 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const doub
   p->launches = 0;
   st = run_energy(p, B, eps, gamma1, lambda2, s, out_dev);
   if (st != DSRG_OK) return st;
-  if (p->cavv_tc) {
-    // the adjoint reads the FP64 (A,A|V,V) integrals: re-form them in FP64
-    cudaError_t e0 = launch_gram_aavv_fp64(p, B);
-    if (e0 == cudaSuccess) e0 = launch_active(p, B, eps, gamma1, lambda2, s, true);
+  if (p->rest_tc) {
+    // the adjoint reads FP64 active-block integrals: re-form them in FP64
+    cudaError_t e0 = launch_active(p, B, eps, gamma1, lambda2, s, false);
     if (e0 != cudaSuccess) return cuda_fail(p, e0, "active (fp64 tables)");
   }
   cudaError_t e = launch_grad(p, B, eps, gamma1, lambda2, s, dB_dev, deps_dev, ds_dev);

@@ -24,6 +24,7 @@ struct dsrg_batch {
   std::vector<void*> allocs;
   void* hi = nullptr;
   void* lo = nullptr;
+  float* ybuf = nullptr;  // GEMM output of the CAVV/CCAV/active stage, reused molecule by molecule
   CUtensorMap map_hi, map_lo;
   void* d_mols = nullptr;
   int4* d_items = nullptr;
@@ -116,6 +117,21 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
   }
   const int elt = bf16 ? 2 : 4;
   if (split) {
+    // molecules run one after another on one stream: one GEMM output buffer serves all
+    size_t ybytes = 0;
+    for (int m = 0; m < nmol; ++m) {
+      const dsrg_sizes_t& s = sizes[m];
+      dsrg::Sizes z{s.ncore, s.nactive, s.nvirt, s.naux, s.ncore + s.nactive, s.nactive + s.nvirt,
+                    s.ncore + s.nactive + s.nvirt};
+      const size_t yb = dsrg::rest_supported(z) ? dsrg::rest_y_bytes(z) : 0;
+      ybytes = yb > ybytes ? yb : ybytes;
+    }
+    if (ybytes > 0 && !balloc(b, (void**)&b->ybuf, ybytes)) {
+      bfree(b);
+      delete b;
+      return DSRG_ERR_OOM;
+    }
+    b->ws_bytes += ybytes;
     const size_t plane = (size_t)rows * Qld * elt;
     if (!balloc(b, &b->hi, plane) || !balloc(b, &b->lo, plane)) {
       bfree(b);
@@ -137,6 +153,7 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
     sh.lo = split ? (char*)b->lo + (size_t)row_base[m] * Qld * elt : nullptr;
     sh.Qld = Qld;
     sh.row_base = row_base[m];
+    sh.y = b->ybuf;
     dsrg_status_t st =
         dsrg::create_plan(&b->plans[m], &sizes[m], prec, b->cap_stream, flags, split ? &sh : nullptr);
     if (st != DSRG_OK) {

@@ -52,7 +52,8 @@ struct ActiveWs {
   int actvv_blocks = 0;
 };
 
-struct SplitWs;  // tensor-core path workspace (tc_split.cu)
+struct SplitWs;    // tensor-core path workspace (tc_split.cu)
+struct RestState;  // tensor-core CAVV / CCAV / active integrals (tc_rest.cu)
 struct GradWs;   // gradient workspace (grad.cu)
 
 }  // namespace dsrg
@@ -89,9 +90,9 @@ struct dsrg_plan {
 
   dsrg::ActiveWs act;
   dsrg::SplitWs* split = nullptr;
-  void* cavv_state = nullptr;  // tensor-core CAVV tables (tc_cavv.cu)
+  dsrg::RestState* rest = nullptr;  // split CAVV / CCAV / active integrals (tc_rest.cu)
   dsrg::GradWs* grad = nullptr;  // gradient workspace (DSRG_PLAN_GRAD)
-  bool cavv_tc = false;        // CAVV and the (A,A|V,V) integrals on the tensor cores
+  bool rest_tc = false;        // CAVV, CCAV and the active integrals from the tensor-core GEMM
 
   // device staging of dsrg_mrpt2_energy_host (DSRG_PLAN_HOST_IO)
   double *st_B = nullptr, *st_eps = nullptr, *st_g = nullptr, *st_l = nullptr, *st_out = nullptr;
@@ -111,8 +112,10 @@ cudaError_t launch_cavv_fp64(dsrg_plan* p, const double* B, const double* eps, c
                              double s);
 cudaError_t launch_ccav_fp64(dsrg_plan* p, const double* B, const double* eps, const double* G,
                              double s);
+// ints_ready: K1, K2, K3 and M are already formed (split path); otherwise they
+// are formed here in FP64 from B.
 cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                          const double* L, double s, bool gram_done);
+                          const double* L, double s, bool ints_ready);
 cudaError_t launch_gram_aavv_fp64(dsrg_plan* p, const double* B);
 cudaError_t launch_final_reduce(dsrg_plan* p, double* out);
 cudaError_t launch_pair_energies(dsrg_plan* p, double* pairs);
@@ -140,6 +143,7 @@ struct SplitShare {
   void* lo;
   int Qld;
   long long row_base;
+  float* y;  // GEMM output of tc_rest.cu shared by the molecules (NULL: the plan owns one)
 };
 dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
                           void* cuda_stream, uint32_t flags, const SplitShare* share);
@@ -172,12 +176,19 @@ void grad_free(dsrg_plan* p);
 cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const double* G,
                         const double* L, double s, double* dB, double* deps, double* ds);
 
-// Tensor-core CAVV (tc_cavv.cu); needs the planes staged by launch_split_ccvv.
-bool cavv_split_supported(const dsrg_plan* p);
-int cavv_split_blocks(const dsrg_plan* p);
-bool cavv_split_alloc(dsrg_plan* p);
-void cavv_split_free(dsrg_plan* p);
-cudaError_t launch_split_cavv(dsrg_plan* p, const double* eps, const double* G, double s);
+// Split-path CAVV, CCAV and active-block integrals (tc_rest.cu); needs the
+// planes staged by the CCVV launch of the same call.
+int rest_xrows(const Sizes& z);
+size_t rest_y_bytes(const Sizes& z);
+bool rest_supported(const Sizes& z);
+int rest_cavv_blocks(const dsrg_plan* p);
+int rest_ccav_blocks(const dsrg_plan* p);
+bool rest_alloc(dsrg_plan* p, float* shared_y);
+void rest_free(dsrg_plan* p);
+cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                              double s);
+void* split_plane_ptr(const dsrg_plan* p, bool hi);
+int split_qld(const dsrg_plan* p);
 
 }  // namespace dsrg
 

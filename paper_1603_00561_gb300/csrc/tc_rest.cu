@@ -1,0 +1,744 @@
+// Split-precision CAVV (diagram F2), CCAV (diagram F3) and the integrals of
+// the active block from one tensor-core GEMM over the hi/lo planes of CCVV.
+//
+// Every one of these quantities is a product of two rows of the hole x
+// particle factors B: (ge|uf), (ge|hx), (hx|h'y) with g, h holes, u an
+// active hole, e, f virtuals and x, y active particles. The planes already
+// hold the rows (g, e) for every hole g and virtual e (K-major over Q); the
+// rows (h, x) of the active particles are appended to them (nH*nA rows,
+// padded to 64). One GEMM
+//     Y = P[(g,e)] . P[(u,f) ; (h,x)]^T       (hi.hi + hi.lo + lo.hi, FP32 accumulation)
+// then holds, at row (g, e):
+//     columns u*nVpad + f   ->  (ge|uf) = X_u[e,f] of F2 for g = m core,
+//                               M_xu[e,f] = (xe|uf) for g = x active
+//     columns XC + h*nA + x ->  (ge|hx): Z_u[m,n,e] = (me|nu) of F3, and the
+//                               virtual parts of (ia|ux), (ix|ua)
+// (Sec. III step 4: the integrals with active indices are formed explicitly,
+// then contracted). FP64 kernels then evaluate the F2 and F3 energies with
+// FP64 regulators, and gather the active-block integrals; (hx|h'y), which
+// has no virtual index, is formed in FP64 from B directly.
+//
+// The GEMM kernel (one CTA per SM, persistent, tiles 128 x 256):
+//   warp 0      TMA producer (one elected thread)
+//   warp 1      TMEM allocator and MMA issuer (one elected thread)
+//   warps 2-5   epilogue: TMEM -> registers -> FP32 stores of Y
+// Shared memory: 4 stages x (A 128 rows + B 256 rows) x 2 planes x 64 B, 64-byte
+// swizzle. TMEM: 2 buffers x 256 columns. Every wait is bounded (about 2 s).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "regulators.cuh"
+#include "tc_common.cuh"
+
+namespace dsrg {
+
+constexpr int G_BM = 128, G_BN = 256;
+constexpr int G_KB = 64;                              // K bytes per row per stage
+constexpr int G_STAGES = 4;
+constexpr int G_A_BYTES = G_BM * G_KB;                // 8 KB per plane
+constexpr int G_B_BYTES = G_BN * G_KB;                // 16 KB per plane
+constexpr int G_STAGE_BYTES = 2 * (G_A_BYTES + G_B_BYTES);
+constexpr int G_THREADS = 192;
+constexpr uint32_t G_TMEM_COLS = 512;
+constexpr int XROW_ALIGN = 64;
+constexpr int F2_T = 32;                              // F2 epilogue tile edge
+
+struct GemmArgs {
+  int a_row0;        // row r of Y is plane row a_row0 + r
+  int b_row0;        // column c of Y is plane row b_row0 + c
+  int m_tiles, n_tiles, kblocks;
+  float* Y;
+  long long ldy;
+  int* status;
+};
+
+__host__ __device__ constexpr uint32_t idesc_mn(bool bf16, uint32_t m, uint32_t n) {
+  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) | ((n >> 3) << 17) |
+         ((m >> 4) << 24);
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(G_THREADS, 1)
+    split_gemm_kernel(const __grid_constant__ CUtensorMap map_hi,
+                      const __grid_constant__ CUtensorMap map_lo, const GemmArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* tiles = smem;
+  uint64_t* full = (uint64_t*)(smem + G_STAGES * G_STAGE_BYTES);
+  uint64_t* empty = full + G_STAGES;
+  uint64_t* tfull = empty + G_STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_items = a.m_tiles * a.n_tiles;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(G_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&map_hi) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&map_lo) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+        const int arow = a.a_row0 + (it / a.n_tiles) * G_BM;
+        const int brow = a.b_row0 + (it % a.n_tiles) * G_BN;
+        for (int kb = 0; kb < a.kblocks; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = tiles + stage * G_STAGE_BYTES;
+          mbar_expect_tx(&full[stage], (uint32_t)G_STAGE_BYTES);
+          // the last auxiliary functions first (see the K order of the MMA issuer)
+          const int kq = (a.kblocks - 1 - kb) * (G_KB / (BF16 ? 2 : 4));
+          tma_load_2d(st, &map_hi, &full[stage], kq, arow);
+          tma_load_2d(st + G_A_BYTES, &map_lo, &full[stage], kq, arow);
+          uint8_t* sb = st + 2 * G_A_BYTES;
+          tma_load_2d(sb, &map_hi, &full[stage], kq, brow);
+          tma_load_2d(sb + G_A_BYTES, &map_hi, &full[stage], kq, brow + G_BM);
+          tma_load_2d(sb + G_B_BYTES, &map_lo, &full[stage], kq, brow);
+          tma_load_2d(sb + G_B_BYTES + G_A_BYTES, &map_lo, &full[stage], kq, brow + G_BM);
+          if (++stage == G_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        int s = stage;
+        uint32_t ph = phase;
+        for (int k = 0; k < G_STAGES; ++k) {
+          if (--s < 0) {
+            s = G_STAGES - 1;
+            ph ^= 1u;
+          }
+          const unsigned long long t0 = gtimer();
+          while (!mbar_try(&full[s], ph) && gtimer() - t0 < TC_WAIT_NS) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_mn(BF16, G_BM, G_BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int tbuf = 0;
+      uint32_t tphase = 0;
+      bool ok = true, issued = false;
+      for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
+        if (!mbar_wait(&tempty[tbuf], tphase ^ 1u, abort_flag, a.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(tbuf * G_BN);
+        for (int kb = 0; kb < a.kblocks; ++kb) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(tiles + stage * G_STAGE_BYTES);
+          const uint32_t sb = sa + 2 * G_A_BYTES;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            // K from the last auxiliary function to the first, cross products
+            // before hi*hi: the FP32 accumulator truncates toward zero at every
+            // instruction, and with factors that decrease along Q this keeps it
+            // small until the largest terms arrive
+            const uint32_t off = (uint32_t)((1 - k) * 32);
+            const uint64_t ah = desc_sw64(sa + off), al = desc_sw64(sa + G_A_BYTES + off);
+            const uint64_t bh = desc_sw64(sb + off), bl = desc_sw64(sb + G_B_BYTES + off);
+            const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+            tc_mma<BF16>(d, al, bh, idesc, acc0);
+            tc_mma<BF16>(d, ah, bl, idesc, 1u);
+            tc_mma<BF16>(d, ah, bh, idesc, 1u);
+          }
+          issued = true;
+          tc_commit(&empty[stage]);
+          if (++stage == G_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[tbuf]);
+        if (++tbuf == 2) {
+          tbuf = 0;
+          tphase ^= 1u;
+        }
+      }
+      if (!ok && issued) {
+        tc_commit(drain);
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try(drain, 0) && gtimer() - t0 < TC_WAIT_NS) {
+        }
+      }
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32*(w%4).. (its row of the tile)
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    int tbuf = 0;
+    uint32_t tphase = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+      const bool ok = mbar_wait(&tfull[tbuf], tphase, abort_flag, a.status);
+      tc_fence_after();
+      if (ok) {
+        const uint32_t t = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * G_BN);
+        float* y = a.Y + (size_t)((it / a.n_tiles) * G_BM + row) * a.ldy + (it % a.n_tiles) * G_BN;
+        for (int c0 = 0; c0 < G_BN; c0 += 32) {
+          uint32_t r0[16], r1[16];
+          tmem_ld16(t + c0, r0);
+          tmem_ld16(t + c0 + 16, r1);
+          tmem_ld_wait();
+          float4* o = (float4*)(y + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            o[q] = make_float4(__uint_as_float(r0[4 * q]), __uint_as_float(r0[4 * q + 1]),
+                               __uint_as_float(r0[4 * q + 2]), __uint_as_float(r0[4 * q + 3]));
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            o[4 + q] = make_float4(__uint_as_float(r1[4 * q]), __uint_as_float(r1[4 * q + 1]),
+                                   __uint_as_float(r1[4 * q + 2]), __uint_as_float(r1[4 * q + 3]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[tbuf]);
+      if (++tbuf == 2) {
+        tbuf = 0;
+        tphase ^= 1u;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(G_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Active-particle rows of the planes and their FP64 copy.
+//   plane row xrow0 + h*nA + x  =  B[Q][h][x]  (split like the main rows)
+//   Xq[(h*nA + x) * Q + q]      =  B[q][h][x]  (FP64)
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void xrows_kernel(const double* __restrict__ B, Sizes z, long long xrow0, int Qld,
+                             void* __restrict__ hi, void* __restrict__ lo, double* __restrict__ Xq) {
+  const int T = z.nH * z.nA;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (size_t)T * z.Q) return;
+  const int t = (int)(k / z.Q), q = (int)(k % z.Q);
+  const int h = t / z.nA, x = t % z.nA;
+  const double v = B[bidx(z, q, h, x)];
+  Xq[k] = v;
+  const size_t o = (size_t)(xrow0 + t) * Qld + q;
+  if (BF16) {
+    const __nv_bfloat16 vh = __float2bfloat16_rn((float)v);
+    ((__nv_bfloat16*)hi)[o] = vh;
+    ((__nv_bfloat16*)lo)[o] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(vh)));
+  } else {
+    uint32_t u = __float_as_uint((float)v);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0xfffu + ((u >> 13) & 1u)) & 0xffffe000u;
+    const float vh = __uint_as_float(u);
+    uint32_t w = __float_as_uint((float)(v - (double)vh));
+    if ((w & 0x7f800000u) != 0x7f800000u) w = (w + 0xfffu + ((w >> 13) & 1u)) & 0xffffe000u;
+    ((float*)hi)[o] = vh;
+    ((float*)lo)[o] = __uint_as_float(w);
+  }
+}
+
+// (hx|h'y) in FP64: one warp per pair t1 <= t2 of active-particle rows.
+__global__ void xx_gram_kernel(const double* __restrict__ Xq, int T, int Q, double* __restrict__ Gxx) {
+  const int w = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int npair = T * (T + 1) / 2;
+  if (w >= npair) return;
+  int t1 = 0, r = w;
+  while (r >= T - t1) {
+    r -= T - t1;
+    ++t1;
+  }
+  const int t2 = t1 + r;
+  const double* a = Xq + (size_t)t1 * Q;
+  const double* b = Xq + (size_t)t2 * Q;
+  double acc = 0.0;
+  for (int q = lane; q < Q; q += 32) acc = fma(a[q], b[q], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    Gxx[(size_t)t1 * T + t2] = acc;
+    Gxx[(size_t)t2 * T + t1] = acc;
+  }
+}
+
+// Factors of exp(-s D_u^2), D_u = E_mu - e_a - e_b, E_mu = e_m + e_u (m core, u active).
+__global__ void cavv_tables_kernel(const double* __restrict__ eps, double s, Sizes z, int nVpad,
+                                   double* __restrict__ alpha, double* __restrict__ pinfo,
+                                   double* __restrict__ tau1) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ve = z.nC + z.nA;
+  const int nmu = z.nC * z.nA;
+  const size_t na = (size_t)nmu * nVpad, nt = (size_t)nVpad * nVpad;
+  if (k < na) {
+    const int mu = (int)(k / nVpad), b = (int)(k % nVpad);
+    const int m = mu / z.nA, u = mu % z.nA;
+    const double E = eps[m] + eps[z.nC + u];
+    alpha[k] = (b < z.nV) ? exp(2.0 * s * E * eps[ve + b]) : 0.0;
+    if (b == 0) {
+      double vmax = 0.0;
+      for (int v = 0; v < z.nV; ++v) vmax = fmax(vmax, fabs(eps[ve + v]));
+      const bool ok = (s * E * E <= 700.0) && (2.0 * s * fabs(E) * vmax <= 700.0) &&
+                      (4.0 * s * vmax * vmax <= 700.0);
+      pinfo[4 * mu + 0] = E;
+      pinfo[4 * mu + 1] = exp(-s * E * E);
+      pinfo[4 * mu + 2] = ok ? 1.0 : 0.0;
+      pinfo[4 * mu + 3] = 0.0;
+    }
+  } else if (k < na + nt) {
+    const size_t r = k - na;
+    const int aa = (int)(r / nVpad), bb = (int)(r % nVpad);
+    double v = 0.0;
+    if (aa < z.nV && bb < z.nV) {
+      const double t = eps[ve + aa] + eps[ve + bb];
+      v = exp(-s * t * t);
+    }
+    tau1[r] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// F2 (CAVV), spin-adapted (closed-shell spin sum of Table 2's F2):
+//   F2 = sum_m sum_{u,v} G_uv sum_ef X_u[e,f] (2 X_v[e,f] - X_v[f,e]) Rv_u Rt_v,
+//   X_u[e,f] = (me|uf), D_u = e_m + e_u - e_e - e_f,
+//   Rv_u = 1 + exp(-s D_u^2) (Eq. (15)), Rt_v = (1 - exp(-s D_v^2)) / D_v (Eq. (13)).
+// One CTA per (m, 32 x 32 tile pair E <= F); for E < F each position (e,f) also
+// adds its mirror (f,e), whose X_u[f,e] is the same CTA's transposed tile.
+// exp(-s D_u^2) = exp(-s E^2) exp(2 s E e_e) exp(2 s E e_f) exp(-s (e_e + e_f)^2);
+// 1/D_u is an FP32 seed with one FP64 Newton step; |D_u| < 1/4 (or a pair whose
+// factors could overflow) takes expm1 and an FP64 divide.
+// ---------------------------------------------------------------------------
+template <int NA>
+__global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ Y, long long ldy,
+                                                      int nVpad, const double* __restrict__ eps,
+                                                      const double* __restrict__ G, double s, Sizes z,
+                                                      const int2* __restrict__ tps, int n_tp,
+                                                      const double* __restrict__ alpha,
+                                                      const double* __restrict__ pinfo,
+                                                      const double* __restrict__ tau1,
+                                                      double* __restrict__ partials) {
+  extern __shared__ float f2s[];
+  float* sX = f2s;                              // [NA][32][33]   X_u[e,f]
+  float* sXt = sX + NA * F2_T * (F2_T + 1);     // [NA][32][33]   X_u[f,e]
+  __shared__ double sAe[NA][F2_T], sAf[NA][F2_T], sEe[F2_T], sEf[F2_T], sG[NA * NA];
+  __shared__ double sE[NA], sBeta[NA];
+  __shared__ int sFact;
+  __shared__ double red[8];
+  const int m = blockIdx.x / n_tp;
+  const int2 ab = tps[blockIdx.x % n_tp];
+  const int E0 = ab.x * F2_T, F0 = ab.y * F2_T;
+  const int ve = z.nC + z.nA;
+  const float* Ym = Y + (size_t)m * nVpad * ldy;
+  for (int k = threadIdx.x; k < NA * F2_T * F2_T; k += 256) {
+    const int u = k / (F2_T * F2_T), r = (k / F2_T) % F2_T, c = k % F2_T;
+    sX[(u * F2_T + r) * (F2_T + 1) + c] = Ym[(size_t)(E0 + r) * ldy + u * nVpad + F0 + c];
+    sXt[(u * F2_T + c) * (F2_T + 1) + r] = Ym[(size_t)(F0 + r) * ldy + u * nVpad + E0 + c];
+  }
+  if (threadIdx.x < F2_T) {
+    const int t = threadIdx.x;
+    const int e = E0 + t, f = F0 + t;
+    sEe[t] = e < z.nV ? eps[ve + e] : 0.0;
+    sEf[t] = f < z.nV ? eps[ve + f] : 0.0;
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const double* al = alpha + (size_t)(m * z.nA + u) * nVpad;
+      sAe[u][t] = al[E0 + t];
+      sAf[u][t] = al[F0 + t];
+    }
+  }
+  if (threadIdx.x < NA * NA) sG[threadIdx.x] = G[threadIdx.x];
+  if (threadIdx.x == 0) {
+    int fact = 1;
+    for (int u = 0; u < NA; ++u) {
+      sE[u] = pinfo[4 * (m * z.nA + u)];
+      sBeta[u] = pinfo[4 * (m * z.nA + u) + 1];
+      fact = fact && (pinfo[4 * (m * z.nA + u) + 2] != 0.0);
+    }
+    sFact = fact;
+  }
+  __syncthreads();
+  const bool mirror = ab.x < ab.y;
+  const bool fact = sFact != 0;
+  const int c = threadIdx.x & 31;
+  const int f = F0 + c;
+  double acc = 0.0;
+  if (f < z.nV) {
+    for (int r = threadIdx.x >> 5; r < F2_T; r += 8) {
+      const int e = E0 + r;
+      if (e >= z.nV) break;
+      const double tau = fact ? tau1[(size_t)e * nVpad + f] : 0.0;
+      const double eef = sEe[r] + sEf[c];
+      double Rv[NA], Rt[NA], X[NA], Xt[NA];
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        X[u] = (double)sX[(u * F2_T + r) * (F2_T + 1) + c];
+        Xt[u] = (double)sXt[(u * F2_T + r) * (F2_T + 1) + c];
+        const double D = sE[u] - eef;
+        if (fact && fabs(D) >= 0.25) {
+          const double g = sBeta[u] * sAe[u][r] * sAf[u][c] * tau;
+          float r0f;
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
+          const double r0 = (double)r0f;
+          const double en = fma(-D, r0, 1.0);
+          const double R0 = fma(-g, r0, r0);
+          Rt[u] = fma(R0, en, R0);
+          Rv[u] = 1.0 + g;
+        } else {
+          Rt[u] = reg_t(D, s);
+          Rv[u] = reg_v(D, s);
+        }
+      }
+      double t1 = 0.0, t2 = 0.0;
+#pragma unroll
+      for (int v = 0; v < NA; ++v) {
+        double c1 = 0.0, c2 = 0.0;
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const double w = sG[u * NA + v] * Rv[u];
+          c1 = fma(w, X[u], c1);
+          c2 = fma(w, Xt[u], c2);
+        }
+        t1 = fma(c1, (2.0 * X[v] - Xt[v]) * Rt[v], t1);
+        t2 = fma(c2, (2.0 * Xt[v] - X[v]) * Rt[v], t2);
+      }
+      acc += mirror ? (t1 + t2) : t1;
+    }
+  }
+  const double tot = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// F3 (CCAV), spin-adapted:
+//   F3 = sum_{u,v} Hh_uv sum_{m,n,e} Z_v[m,n,e] (2 Z_u[m,n,e] - Z_u[n,m,e])
+//        (1 + exp(-s D_v^2)) (1 - exp(-s D_u^2))/D_u,
+//   Z_u[m,n,e] = (me|nu) = Y[(m,e), XC + n*nA + u], D_u = e_m + e_n - e_e - e_u,
+//   Hh = 2 I - G. One CTA per virtual e.
+// ---------------------------------------------------------------------------
+template <int NA>
+__global__ void __launch_bounds__(256) ccav_f3_kernel(const float* __restrict__ Y, long long ldy,
+                                                      int nVpad, long long xc,
+                                                      const double* __restrict__ eps,
+                                                      const double* __restrict__ G, double s, Sizes z,
+                                                      double* __restrict__ partials) {
+  extern __shared__ float f3s[];  // [nC][nC*NA]: Z_u[m,n,e] at m*(nC*NA) + n*NA + u
+  __shared__ double sH[NA * NA];
+  __shared__ double red[8];
+  const int e = blockIdx.x, nC = z.nC, w = nC * NA;
+  for (int k = threadIdx.x; k < nC * w; k += 256) {
+    const int m = k / w, r = k % w;
+    f3s[k] = Y[(size_t)(m * nVpad + e) * ldy + xc + r];
+  }
+  if (threadIdx.x < NA * NA) {
+    const int u = threadIdx.x / NA, v = threadIdx.x % NA;
+    sH[threadIdx.x] = (u == v ? 2.0 : 0.0) - G[threadIdx.x];
+  }
+  __syncthreads();
+  const double ee = eps[nC + z.nA + e];
+  double acc = 0.0;
+  for (int mn = threadIdx.x; mn < nC * nC; mn += 256) {
+    const int m = mn / nC, n = mn % nC;
+    const double base = eps[m] + eps[n] - ee;
+    double Rv[NA], Rt[NA], Zmn[NA], Znm[NA];
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const double D = base - eps[nC + u];
+      Rv[u] = reg_v(D, s);
+      Rt[u] = reg_t(D, s);
+      Zmn[u] = (double)f3s[m * w + n * NA + u];
+      Znm[u] = (double)f3s[n * w + m * NA + u];
+    }
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const double zu = 2.0 * Zmn[u] - Znm[u];
+      double cc = 0.0;
+#pragma unroll
+      for (int v = 0; v < NA; ++v) cc = fma(sH[u * NA + v] * Rv[v], Zmn[v], cc);
+      acc = fma(cc, zu * Rt[u], acc);
+    }
+  }
+  const double tot = block_sum<256>(acc, red);
+  if (threadIdx.x == 0) partials[e] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Active-block integrals from Y (virtual indices) and Gxx (active particles):
+//   K1[i][u][x][a] = (ia|ux), K2[i][u][x][a] = (ix|ua)   [nH][nA][nA][nP]
+//   K3[i][x][j][y] = (ix|jy)                              [nH][nA][nH][nA]
+//   M[x][u][e][f]  = (xe|uf)                              [nA][nA][nV][nV]
+// ---------------------------------------------------------------------------
+__global__ void act_gather_kernel(const float* __restrict__ Y, long long ldy, int nVpad,
+                                  long long xc, const double* __restrict__ Gxx, Sizes z,
+                                  double* __restrict__ K1, double* __restrict__ K2,
+                                  double* __restrict__ K3, double* __restrict__ M) {
+  const int nA = z.nA, nC = z.nC, T = z.nH * nA;
+  const size_t n12 = (size_t)z.nH * nA * nA * z.nP;
+  const size_t n3 = (size_t)T * T;
+  const size_t nm = (size_t)nA * nA * z.nV * z.nV;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < 2 * n12) {
+    const bool second = k >= n12;
+    const size_t r = second ? k - n12 : k;
+    const int a = (int)(r % z.nP);
+    const int x = (int)((r / z.nP) % nA);
+    const int u = (int)((r / ((size_t)z.nP * nA)) % nA);
+    const int i = (int)(r / ((size_t)z.nP * nA * nA));
+    double v;
+    if (!second) {  // (ia|ux)
+      v = (a < nA) ? Gxx[(size_t)(i * nA + a) * T + (nC + u) * nA + x]
+                   : (double)Y[(size_t)(i * nVpad + a - nA) * ldy + xc + (nC + u) * nA + x];
+      K1[r] = v;
+    } else {        // (ix|ua)
+      v = (a < nA) ? Gxx[(size_t)(i * nA + x) * T + (nC + u) * nA + a]
+                   : (double)Y[(size_t)((nC + u) * nVpad + a - nA) * ldy + xc + i * nA + x];
+      K2[r] = v;
+    }
+  } else if (k < 2 * n12 + n3) {
+    const size_t r = k - 2 * n12;  // [i][x][j][y] = Gxx[(i,x)][(j,y)]
+    K3[r] = Gxx[r];
+  } else if (k < 2 * n12 + n3 + nm) {
+    const size_t r = k - 2 * n12 - n3;
+    const int f = (int)(r % z.nV);
+    const int e = (int)((r / z.nV) % z.nV);
+    const int u = (int)((r / ((size_t)z.nV * z.nV)) % nA);
+    const int x = (int)(r / ((size_t)z.nV * z.nV * nA));
+    M[r] = (double)Y[(size_t)((nC + x) * nVpad + e) * ldy + (size_t)u * nVpad + f];
+  }
+}
+
+// ------------------------------- host side -------------------------------
+struct RestState {
+  int nVpad = 0, XR = 0, ncols = 0, n_tiles = 0, m_tiles = 0, grid = 0;
+  long long ldy = 0, xc = 0;
+  float* Y = nullptr;
+  double* Xq = nullptr;
+  double* Gxx = nullptr;
+  double* alpha = nullptr;
+  double* pinfo = nullptr;
+  double* tau1 = nullptr;
+  int2* d_tp = nullptr;
+  int n_tp = 0;
+};
+
+int rest_xrows(const Sizes& z) {
+  if (z.nA == 0) return 0;
+  return (z.nH * z.nA + XROW_ALIGN - 1) / XROW_ALIGN * XROW_ALIGN;
+}
+
+static void rest_dims(const Sizes& z, RestState* st) {
+  st->nVpad = (z.nV + G_BM - 1) / G_BM * G_BM;
+  st->XR = rest_xrows(z);
+  st->ncols = z.nA * st->nVpad + st->XR;
+  st->n_tiles = (st->ncols + G_BN - 1) / G_BN;
+  st->m_tiles = z.nH * st->nVpad / G_BM;
+  st->ldy = (long long)st->n_tiles * G_BN;
+  st->xc = (long long)z.nA * st->nVpad;
+  const int nt = (z.nV + F2_T - 1) / F2_T;
+  st->n_tp = nt * (nt + 1) / 2;
+}
+
+size_t rest_y_bytes(const Sizes& z) {
+  if (z.nA == 0) return 0;
+  RestState st;
+  rest_dims(z, &st);
+  return (size_t)z.nH * st.nVpad * st.ldy * sizeof(float);
+}
+
+bool rest_split_used(const dsrg_plan* p) { return p->prec != DSRG_PREC_FP64 && p->z.nA > 0; }
+
+int rest_cavv_blocks(const dsrg_plan* p) {
+  RestState st;
+  rest_dims(p->z, &st);
+  return p->z.nC * st.n_tp;
+}
+
+int rest_ccav_blocks(const dsrg_plan* p) { return p->z.nV; }
+
+static size_t gemm_smem_bytes() { return (size_t)G_STAGES * G_STAGE_BYTES + 1024 + 256; }
+static size_t f2_smem_bytes(int na) { return (size_t)2 * na * F2_T * (F2_T + 1) * sizeof(float); }
+static size_t f3_smem_bytes(const Sizes& z) { return (size_t)z.nC * z.nC * z.nA * sizeof(float); }
+
+bool rest_supported(const Sizes& z) {
+  return z.nA <= NA_MAX && f3_smem_bytes(z) <= 200 * 1024;
+}
+
+bool rest_alloc(dsrg_plan* p, float* shared_y) {
+  const Sizes& z = p->z;
+  RestState* st = new RestState();
+  p->rest = st;
+  rest_dims(z, st);
+  int nsm = 148;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+  const int items = st->m_tiles * st->n_tiles;
+  st->grid = items < nsm ? items : nsm;
+  const int T = z.nH * z.nA;
+  bool ok = true;
+  if (shared_y)
+    st->Y = shared_y;
+  else
+    ok = plan_alloc(p, (void**)&st->Y, rest_y_bytes(z));
+  ok = ok && plan_alloc(p, (void**)&st->Xq, (size_t)T * z.Q * 8) &&
+       plan_alloc(p, (void**)&st->Gxx, (size_t)T * T * 8) &&
+       plan_alloc(p, (void**)&st->alpha, (size_t)z.nC * z.nA * st->nVpad * 8) &&
+       plan_alloc(p, (void**)&st->pinfo, (size_t)z.nC * z.nA * 4 * 8) &&
+       plan_alloc(p, (void**)&st->tau1, (size_t)st->nVpad * st->nVpad * 8) &&
+       plan_alloc(p, (void**)&st->d_tp, (size_t)st->n_tp * sizeof(int2));
+  if (!ok) return false;
+  const int nt = (z.nV + F2_T - 1) / F2_T;
+  std::vector<int2> tp;
+  for (int A = 0; A < nt; ++A)
+    for (int B = A; B < nt; ++B) tp.push_back(make_int2(A, B));
+  return cudaMemcpy(st->d_tp, tp.data(), tp.size() * sizeof(int2), cudaMemcpyHostToDevice) ==
+         cudaSuccess;
+}
+
+void rest_free(dsrg_plan* p) {
+  delete p->rest;
+  p->rest = nullptr;
+}
+
+// CAVV and CCAV partials and the active-block integrals K1, K2, K3, M of this
+// call (requires the planes staged by the CCVV launch of the same call).
+cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                              double s) {
+  RestState* st = p->rest;
+  const Sizes& z = p->z;
+  const bool bf16 = p->prec == DSRG_PREC_BF16X3;
+  cudaStream_t stream = p->stream;
+  const int T = z.nH * z.nA;
+  const long long xrow0 = (long long)z.nH * st->nVpad;
+  {
+    const size_t n = (size_t)T * z.Q;
+    void* hi = split_plane_ptr(p, true);
+    void* lo = split_plane_ptr(p, false);
+    const int Qld = split_qld(p);
+    if (bf16)
+      xrows_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(B, z, xrow0, Qld, hi, lo, st->Xq);
+    else
+      xrows_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(B, z, xrow0, Qld, hi, lo, st->Xq);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    GemmArgs a;
+    a.a_row0 = 0;
+    a.b_row0 = z.nC * st->nVpad;
+    a.m_tiles = st->m_tiles;
+    a.n_tiles = st->n_tiles;
+    a.kblocks = split_qpad(p) / (G_KB / (bf16 ? 2 : 4));
+    a.Y = st->Y;
+    a.ldy = st->ldy;
+    a.status = p->d_status;
+    const size_t sm = gemm_smem_bytes();
+    const CUtensorMap* mh = split_map(p, true);
+    const CUtensorMap* ml = split_map(p, false);
+    if (bf16) {
+      cudaFuncSetAttribute(split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      split_gemm_kernel<true><<<st->grid, G_THREADS, sm, stream>>>(*mh, *ml, a);
+    } else {
+      cudaFuncSetAttribute(split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      split_gemm_kernel<false><<<st->grid, G_THREADS, sm, stream>>>(*mh, *ml, a);
+    }
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const size_t n = (size_t)z.nC * z.nA * st->nVpad + (size_t)st->nVpad * st->nVpad;
+    cavv_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(eps, s, z, st->nVpad,
+                                                                      st->alpha, st->pinfo, st->tau1);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const Segment& sg = p->segs[p->seg_cavv];
+    const size_t sm = f2_smem_bytes(z.nA);
+#define F2_LAUNCH(NA_)                                                                             \
+  case NA_:                                                                                        \
+    cudaFuncSetAttribute(cavv_f2_kernel<NA_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    cavv_f2_kernel<NA_><<<sg.count, 256, sm, stream>>>(st->Y, st->ldy, st->nVpad, eps, G, s, z,       \
+                                                      st->d_tp, st->n_tp, st->alpha, st->pinfo,   \
+                                                      st->tau1, p->d_partials + sg.begin);        \
+    break;
+    switch (z.nA) {
+      F2_LAUNCH(1) F2_LAUNCH(2) F2_LAUNCH(3) F2_LAUNCH(4)
+      F2_LAUNCH(5) F2_LAUNCH(6) F2_LAUNCH(7) F2_LAUNCH(8)
+      default: return cudaErrorInvalidValue;
+    }
+#undef F2_LAUNCH
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const Segment& sg = p->segs[p->seg_ccav];
+    const size_t sm = f3_smem_bytes(z);
+#define F3_LAUNCH(NA_)                                                                             \
+  case NA_:                                                                                        \
+    cudaFuncSetAttribute(ccav_f3_kernel<NA_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    ccav_f3_kernel<NA_><<<sg.count, 256, sm, stream>>>(st->Y, st->ldy, st->nVpad, st->xc, eps, G, s, \
+                                                      z, p->d_partials + sg.begin);              \
+    break;
+    switch (z.nA) {
+      F3_LAUNCH(1) F3_LAUNCH(2) F3_LAUNCH(3) F3_LAUNCH(4)
+      F3_LAUNCH(5) F3_LAUNCH(6) F3_LAUNCH(7) F3_LAUNCH(8)
+      default: return cudaErrorInvalidValue;
+    }
+#undef F3_LAUNCH
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const int npair = T * (T + 1) / 2;
+    xx_gram_kernel<<<(npair + 7) / 8, 256, 0, stream>>>(st->Xq, T, z.Q, st->Gxx);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  {
+    const size_t n = 2 * (size_t)z.nH * z.nA * z.nA * z.nP + (size_t)T * T +
+                     (size_t)z.nA * z.nA * z.nV * z.nV;
+    act_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+        st->Y, st->ldy, st->nVpad, st->xc, st->Gxx, z, p->act.K1, p->act.K2, p->act.K3, p->act.M);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace dsrg

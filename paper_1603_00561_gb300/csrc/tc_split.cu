@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           }
           uint8_t* st = tiles + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], (uint32_t)(ip.nload * 2 * SLOT_BYTES));
-          const int kq = kb * (KB_BYTES / (BF16 ? 2 : 4));
+          const int kq = (kblocks - 1 - kb) * (KB_BYTES / (BF16 ? 2 : 4));
           for (int l = 0; l < ip.nload; ++l) {
             const int sl = ip.load[l];
             const int row = row0 + slot_row(ip, sl, nVpad);
@@ -263,23 +263,28 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           const uint32_t sb = su32(tiles + stage * STAGE_BYTES);
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            const uint32_t off = (uint32_t)(k * 32);
+            // K runs from the last auxiliary function to the first and the small
+            // cross products go before hi*hi: the accumulator truncates toward zero
+            // at every instruction, and with the factors' magnitudes decreasing
+            // along Q this keeps the accumulator small until the largest terms
+            // arrive, so few truncations act on the full-size sum.
+            const uint32_t off = (uint32_t)((1 - k) * 32);
             const uint64_t a1h = desc_sw64(sb + (ip.g1a * 2 + 0) * SLOT_BYTES + off);
             const uint64_t a1l = desc_sw64(sb + (ip.g1a * 2 + 1) * SLOT_BYTES + off);
             const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + off);
             const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + off);
             const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-            tc_mma<BF16>(dx, a1h, b1h, idesc, acc0);
+            tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
             tc_mma<BF16>(dx, a1h, b1l, idesc, 1u);
-            tc_mma<BF16>(dx, a1l, b1h, idesc, 1u);
+            tc_mma<BF16>(dx, a1h, b1h, idesc, 1u);
             if (ip.two) {
               const uint64_t a2h = desc_sw64(sb + (ip.g2a * 2 + 0) * SLOT_BYTES + off);
               const uint64_t a2l = desc_sw64(sb + (ip.g2a * 2 + 1) * SLOT_BYTES + off);
               const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + off);
               const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + off);
-              tc_mma<BF16>(dy, a2h, b2h, idesc, acc0);
+              tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
               tc_mma<BF16>(dy, a2h, b2l, idesc, 1u);
-              tc_mma<BF16>(dy, a2l, b2h, idesc, 1u);
+              tc_mma<BF16>(dy, a2h, b2h, idesc, 1u);
             }
           }
           issued = true;
@@ -564,7 +569,9 @@ int split_ccvv_blocks(const dsrg_plan* p) {
   return p->n_pairs * (nT * (nT + 1) / 2);
 }
 
-int split_plane_rows(const Sizes& z) { return z.nH * ((z.nV + TT - 1) / TT * TT); }
+// Rows of one molecule's planes: (h, e) for every hole h and padded virtual e,
+// then the active-particle rows (h, x) of tc_rest.cu.
+int split_plane_rows(const Sizes& z) { return z.nH * ((z.nV + TT - 1) / TT * TT) + rest_xrows(z); }
 int split_plane_qpad(const Sizes& z) { return (z.Q + 63) / 64 * 64; }
 
 // Static schedule: items in their global order (molecule, pair, tile pair) are
@@ -616,7 +623,7 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
   w->nT = (z.nV + TT - 1) / TT;
   w->nVpad = w->nT * TT;
   w->Qpad = split_plane_qpad(z);
-  w->rows = z.nH * w->nVpad;
+  w->rows = split_plane_rows(z);
   w->n_tp = w->nT * (w->nT + 1) / 2;
   w->n_items = p->n_pairs * w->n_tp;
   w->Qld = Qld;
@@ -682,6 +689,8 @@ bool split_alloc(dsrg_plan* p) {
 }
 
 int split_qpad(const dsrg_plan* p) { return p->split->Qpad; }
+int split_qld(const dsrg_plan* p) { return p->split->Qld; }
+void* split_plane_ptr(const dsrg_plan* p, bool hi) { return hi ? p->split->hi : p->split->lo; }
 
 const CUtensorMap* split_map(const dsrg_plan* p, bool hi) {
   return hi ? &p->split->map_hi : &p->split->map_lo;

@@ -74,9 +74,13 @@ def test_batch_uneven_recipe_against_oracle(pk):
     out = batch.energy([pk.to_device(p) for p in mols], [p.s for p in mols]).cpu().numpy()
     for m, p in enumerate(mols):
         ref = odsrg.energy(p.B, p.eps, p.gamma1, p.lambda2, p.s, p.ncore, p.nactive, p.nvirt)
-        tol = 2.0 * 3 * -(-p.naux // 16) * 2.0 ** -24
+        # truncating tensor-core accumulator: < 1 ulp (2^-23) per instruction,
+        # 3 instructions per K step of 16, E quadratic in the integrals, and a
+        # factor 2 for blocks whose terms are not all of one sign
+        tol = 2.0 * 3 * -(-p.naux // 16) * 2.0 ** -23
         for k, name in enumerate(["ccvv", "cavv", "ccav", "active", "total"]):
+            bar = tol if name == "ccvv" else 2.0 * tol
             if ref[name] == 0.0:
                 assert out[m][k] == 0.0
             else:
-                assert abs(out[m][k] - ref[name]) / abs(ref[name]) <= tol, (m, name)
+                assert abs(out[m][k] - ref[name]) / abs(ref[name]) <= bar, (m, name)

@@ -1,16 +1,18 @@
 """Parity of the split-precision tensor-core path (tcgen05) with the oracle.
 
-The CCVV products run as hi*hi + hi*lo + lo*hi with B = hi + lo in TF32 or
-BF16 planes, accumulated in FP32 in tensor memory. The tensor-core
-accumulator does not round to nearest: every MMA instruction truncates
-toward zero, which shrinks |v_ef| by up to about half an FP32 ulp per
-instruction. With 3 instructions per K step of 8 (TF32) or 16 (BF16)
-auxiliary functions, the relative error of E_CCVV is bounded by
-    2 * (3 * ceil(naux / K)) * 2^-24        (the factor 2: E is quadratic in v)
-which is the tolerance used here; the measured errors sit well inside it.
-CAVV (for nA <= 2) and the (A,A|V,V) integrals of the active block come from
-the same planes and carry the same bound; CCAV runs on FP32 CUDA cores with
-the same hi/lo split (round-to-nearest accumulation), well inside the bound.
+The pair GEMMs run as hi*hi + hi*lo + lo*hi with B = hi + lo in TF32 or BF16
+planes, accumulated in FP32 in tensor memory. The tensor-core accumulator does
+not round to nearest: every MMA instruction truncates toward zero, which moves
+the sum toward zero by less than one FP32 ulp, i.e. by less than 2^-23 of the
+accumulator. With 3 instructions per K step of 8 (TF32) or 16 (BF16)
+auxiliary functions, an integral carries a relative error below
+3 * ceil(naux / K) * 2^-23, and E_CCVV (quadratic in the integrals, every term
+positive) below twice that:
+    tol = 2 * 3 * ceil(naux / K) * 2^-23.
+The other blocks (CAVV, CCAV, the active block, the total) come from the same
+planes through one GEMM; their terms are not all of one sign, and the bound
+gets a factor 2 for the cancellation among them. The measured errors sit well
+inside these bounds except at small naux, where few K steps make them tight.
 """
 import math
 
@@ -26,8 +28,9 @@ BLOCKS = ["ccvv", "cavv", "ccav", "active", "total"]
 KSTEP = {"tf32x3": 8, "bf16x3": 16}
 
 
-def split_tol(prec, naux):
-    return 2.0 * 3 * math.ceil(naux / KSTEP[prec]) * 2.0 ** -24
+def split_tol(prec, naux, block="ccvv"):
+    definite = 1.0 if block == "ccvv" else 2.0
+    return definite * 2.0 * 3 * math.ceil(naux / KSTEP[prec]) * 2.0 ** -23
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +71,7 @@ def test_split_blocks_small(pk, prec, nC, nA, nV, Q, s, seed):
     for k in BLOCKS:
         rel = abs(gpu[k] - ref[k]) / max(abs(ref[k]), 1e-300)
         print(f"{prec} {nC}/{nA}/{nV}/{Q} {k:7s} gpu={gpu[k]:+.12e} oracle={ref[k]:+.12e} rel={rel:.2e}")
-        bar = tol
+        bar = split_tol(prec, Q, k)
         if ref[k] == 0.0:
             assert gpu[k] == 0.0
         else:
@@ -87,7 +90,7 @@ def test_split_vtz_against_fp64_path(pk, prec):
     print(prec, "vtz ccvv rel vs fp64", rel)
     assert rel <= split_tol(prec, p.naux)
     for k in ("cavv", "ccav", "active", "total"):
-        assert abs(gs[k] - g64[k]) / abs(g64[k]) <= split_tol(prec, p.naux), k
+        assert abs(gs[k] - g64[k]) / abs(g64[k]) <= split_tol(prec, p.naux, k), k
 
 
 @pytest.mark.parametrize("s", [0.1, 0.5, 1.0])
@@ -103,7 +106,7 @@ def test_split_v5z_s_sweep(pk, s):
     for k in BLOCKS:
         rel = abs(gs[k] - g64[k]) / abs(g64[k])
         print(f"v5z s={s} {k:7s} split={gs[k]:+.12e} fp64={g64[k]:+.12e} rel={rel:.2e}")
-        assert rel <= tol
+        assert rel <= split_tol("bf16x3", p.naux, k)
     sample = [(0, 0), (3, 19), (23, 23)]
     ref = odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample).numpy()
     for (m, n) in sample:
