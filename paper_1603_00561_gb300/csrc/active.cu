@@ -108,7 +108,7 @@ cudaError_t launch_ccav_fp64(dsrg_plan* p, const double* B, const double* eps, c
   const Segment& sg = p->segs[p->seg_ccav];
   if (sg.count == 0) return cudaSuccess;
   const size_t sm = ccav_smem(p->z);
-  cudaFuncSetAttribute(ccav_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  raise_smem_limit((const void*)ccav_fp64_kernel, sm);
   ccav_fp64_kernel<<<sg.count, 256, sm, p->stream>>>(B, eps, G, s, p->z,
                                                      p->d_partials + sg.begin);
   DSRG_LAUNCH_CHECK(p);
@@ -171,7 +171,9 @@ __global__ void small_ints_kernel(const double* __restrict__ B, Sizes z, double*
   }
 }
 
-// Spin-orbital W1, W2 (V, T, Vt), cumulant and active gamma.
+// Spin-orbital W1, W2 (V, T, Vt), cumulant and active gamma. One thread per
+// spatial quadruple of W1 / W2: the regulators depend on the spatial orbitals
+// only, so they are evaluated once and the 16 spin combinations written.
 __global__ void build_tables_kernel(const double* __restrict__ eps, const double* __restrict__ G,
                                     const double* __restrict__ L, double s, Sizes z,
                                     const double* __restrict__ K1, const double* __restrict__ K2,
@@ -179,43 +181,54 @@ __global__ void build_tables_kernel(const double* __restrict__ eps, const double
                                     double* __restrict__ W2, double* __restrict__ lam,
                                     double* __restrict__ gA, size_t w1n, size_t w2n) {
   const ActDims d = act_dims(z);
+  const size_t n1 = (size_t)z.nH * z.nA * z.nP * z.nA;   // spatial (i, u, a, x)
+  const size_t n2 = (size_t)z.nH * z.nH * z.nA * z.nA;   // spatial (i, j, x, y)
   const size_t nl = (size_t)d.nA2 * d.nA2 * d.nA2 * d.nA2;
   const size_t ng = (size_t)d.nA2 * d.nA2;
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < w1n) {
-    const int X = (int)(k % d.nA2);
-    const int A = (int)((k / d.nA2) % d.nP2);
-    const int U = (int)((k / ((size_t)d.nA2 * d.nP2)) % d.nA2);
-    const int I = (int)(k / ((size_t)d.nA2 * d.nP2 * d.nA2));
-    const int i = I >> 1, u = U >> 1, a = A >> 1, x = X >> 1;
-    const int si = I & 1, su = U & 1, sa = A & 1, sx = X & 1;
+  if (k < n1) {
+    const int x = (int)(k % z.nA);
+    const int a = (int)((k / z.nA) % z.nP);
+    const int u = (int)((k / ((size_t)z.nA * z.nP)) % z.nA);
+    const int i = (int)(k / ((size_t)z.nA * z.nP * z.nA));
     const size_t kk = (((size_t)i * z.nA + u) * z.nA + x) * z.nP + a;
-    double V = 0.0;
-    if (si == sa && su == sx) V += K1[kk];
-    if (si == sx && su == sa) V -= K2[kk];
+    const double k1 = K1[kk], k2 = K2[kk];
     const double D = eps[i] + eps[z.nC + u] - eps[z.nC + a] - eps[z.nC + x];
-    const bool internal = (I >= d.nC2) && (A < d.nA2);
-    W1[k] = V;
-    W1[w1n + k] = internal ? 0.0 : V * reg_t(D, s);
-    W1[2 * w1n + k] = V * reg_v(D, s);
-  } else if (k < w1n + w2n) {
-    const size_t r = k - w1n;
-    const int Y = (int)(r % d.nA2);
-    const int X = (int)((r / d.nA2) % d.nA2);
-    const int J = (int)((r / ((size_t)d.nA2 * d.nA2)) % d.nH2);
-    const int I = (int)(r / ((size_t)d.nA2 * d.nA2 * d.nH2));
-    const int i = I >> 1, j = J >> 1, x = X >> 1, y = Y >> 1;
-    const int si = I & 1, sj = J & 1, sx = X & 1, sy = Y & 1;
-    double V = 0.0;
-    if (si == sx && sj == sy) V += K3[(((size_t)i * z.nA + x) * z.nH + j) * z.nA + y];
-    if (si == sy && sj == sx) V -= K3[(((size_t)i * z.nA + y) * z.nH + j) * z.nA + x];
+    const double rt = reg_t(D, s), rv = reg_v(D, s);
+    const bool internal = (i >= z.nC) && (a < z.nA);
+    for (int sp = 0; sp < 16; ++sp) {
+      const int si = sp >> 3, su = (sp >> 2) & 1, sa = (sp >> 1) & 1, sx = sp & 1;
+      double V = 0.0;
+      if (si == sa && su == sx) V += k1;
+      if (si == sx && su == sa) V -= k2;
+      const size_t o = w1i(d, 2 * i + si, 2 * u + su, 2 * a + sa, 2 * x + sx);
+      W1[o] = V;
+      W1[w1n + o] = internal ? 0.0 : V * rt;
+      W1[2 * w1n + o] = V * rv;
+    }
+  } else if (k < n1 + n2) {
+    const size_t r = k - n1;
+    const int y = (int)(r % z.nA);
+    const int x = (int)((r / z.nA) % z.nA);
+    const int j = (int)((r / ((size_t)z.nA * z.nA)) % z.nH);
+    const int i = (int)(r / ((size_t)z.nA * z.nA * z.nH));
+    const double kxy = K3[(((size_t)i * z.nA + x) * z.nH + j) * z.nA + y];
+    const double kyx = K3[(((size_t)i * z.nA + y) * z.nH + j) * z.nA + x];
     const double D = eps[i] + eps[j] - eps[z.nC + x] - eps[z.nC + y];
-    const bool internal = (I >= d.nC2) && (J >= d.nC2);
-    W2[r] = V;
-    W2[w2n + r] = internal ? 0.0 : V * reg_t(D, s);
-    W2[2 * w2n + r] = V * reg_v(D, s);
-  } else if (k < w1n + w2n + nl) {
-    const int r = (int)(k - w1n - w2n);
+    const double rt = reg_t(D, s), rv = reg_v(D, s);
+    const bool internal = (i >= z.nC) && (j >= z.nC);
+    for (int sp = 0; sp < 16; ++sp) {
+      const int si = sp >> 3, sj = (sp >> 2) & 1, sx = (sp >> 1) & 1, sy = sp & 1;
+      double V = 0.0;
+      if (si == sx && sj == sy) V += kxy;
+      if (si == sy && sj == sx) V -= kyx;
+      const size_t o = w2i(d, 2 * i + si, 2 * j + sj, 2 * x + sx, 2 * y + sy);
+      W2[o] = V;
+      W2[w2n + o] = internal ? 0.0 : V * rt;
+      W2[2 * w2n + o] = V * rv;
+    }
+  } else if (k < n1 + n2 + nl) {
+    const int r = (int)(k - n1 - n2);
     const int Y = r % d.nA2, X = (r / d.nA2) % d.nA2, V = (r / (d.nA2 * d.nA2)) % d.nA2,
               U = r / (d.nA2 * d.nA2 * d.nA2);
     const int u = U >> 1, v = V >> 1, x = X >> 1, y = Y >> 1;
@@ -231,8 +244,8 @@ __global__ void build_tables_kernel(const double* __restrict__ eps, const double
       val = (su == 0) ? -Lf(u, v, y, x) : -Lf(v, u, x, y);
     }
     lam[r] = val;
-  } else if (k < w1n + w2n + nl + ng) {
-    const int r = (int)(k - w1n - w2n - nl);
+  } else if (k < n1 + n2 + nl + ng) {
+    const int r = (int)(k - n1 - n2 - nl);
     const int U = r / d.nA2, V = r % d.nA2;
     gA[r] = ((U & 1) == (V & 1)) ? 0.5 * G[(U >> 1) * z.nA + (V >> 1)] : 0.0;
   }
@@ -424,6 +437,84 @@ __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restri
   }
 }
 
+// The same sums for any active space: per chunk of ACTVV_CH positions (e,f)
+// the CTA first forms, for every active pair p = (x,u) and its transpose
+// p' = (u,x), a_p = M_p Rv_p, b_p = M_p Rt_p and c_p = M_p' Rt_p in shared memory
+// (nA^2 regulator pairs per position; D_p' = D_p), then accumulates
+// P1[p][q] += a_p b_q and P2[p][q] += a_p c_q (M_vy = M_(yv)') over the chunk,
+// each thread holding a fixed set of (p, q).
+constexpr int ACTVV_CH = 64;
+
+template <int NA>
+__global__ void __launch_bounds__(256) actvv_gen_kernel(const double* __restrict__ eps, double s,
+                                                        Sizes z, const double* __restrict__ M,
+                                                        double* __restrict__ part) {
+  constexpr int NA2 = NA * NA, NA4 = NA2 * NA2;
+  constexpr int PER = (NA4 + 255) / 256;  // (p,q) outputs per thread
+  extern __shared__ double avs[];
+  double* sa = avs;                        // [NA2][CH]
+  double* sb = sa + NA2 * ACTVV_CH;        // [NA2][CH]
+  double* sc = sb + NA2 * ACTVV_CH;        // [NA2][CH]
+  __shared__ double red[8];
+  const size_t nV2 = (size_t)z.nV * z.nV;
+  const int ve = z.nC + z.nA;
+  double acc1[PER], acc2[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) acc1[r] = acc2[r] = 0.0;
+  const size_t nchunks = (nV2 + ACTVV_CH - 1) / ACTVV_CH;
+  for (size_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const size_t k0 = ch * ACTVV_CH;
+    __syncthreads();
+    for (int it = threadIdx.x; it < NA2 * ACTVV_CH; it += 256) {
+      const int pidx = it / ACTVV_CH, kk = it % ACTVV_CH;
+      const size_t k = k0 + kk;
+      double a = 0.0, b = 0.0, c = 0.0;
+      if (k < nV2) {
+        const int x = pidx / NA, u = pidx % NA;
+        const int e = (int)(k / z.nV), f = (int)(k % z.nV);
+        const double D = eps[z.nC + x] + eps[z.nC + u] - eps[ve + e] - eps[ve + f];
+        const double m = M[(size_t)pidx * nV2 + k];
+        const double mt = M[(size_t)(u * NA + x) * nV2 + k];
+        const double rt = reg_t(D, s);
+        a = m * reg_v(D, s);
+        b = m * rt;
+        c = mt * rt;
+      }
+      sa[it] = a;
+      sb[it] = b;
+      sc[it] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int o = threadIdx.x + 256 * r;
+      if (o < NA4) {
+        const double* ap = sa + (o / NA2) * ACTVV_CH;
+        const double* bq = sb + (o % NA2) * ACTVV_CH;
+        const double* cq = sc + (o % NA2) * ACTVV_CH;
+        double t1 = acc1[r], t2 = acc2[r];
+#pragma unroll 8
+        for (int kk = 0; kk < ACTVV_CH; ++kk) {
+          t1 = fma(ap[kk], bq[kk], t1);
+          t2 = fma(ap[kk], cq[kk], t2);
+        }
+        acc1[r] = t1;
+        acc2[r] = t2;
+      }
+    }
+  }
+  // per-CTA partials: thread-owned outputs need no block reduction
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int o = threadIdx.x + 256 * r;
+    if (o < NA4) {
+      part[((size_t)blockIdx.x * 2 + 0) * NA4 + o] = acc1[r];
+      part[((size_t)blockIdx.x * 2 + 1) * NA4 + o] = acc2[r];
+    }
+  }
+  (void)red;
+}
+
 __global__ void actvv_reduce_kernel(int nA4, int nblk, const double* __restrict__ part,
                                     double* __restrict__ P12) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,222 +553,268 @@ __device__ __forceinline__ double s_vv(const ActDims& d, int nA, const double* P
   return r;
 }
 
+// Every term is a full sum over its spin-orbital indices; a thread takes one
+// value of the leading indices (the "outer" index o of that term) and loops
+// over the rest. gamma and eta are spin-diagonal, the cumulant is non-zero
+// only for {s_u, s_v} = {s_x, s_y} and t1, ft conserve spin, so the inner loops
+// run over spatial orbitals of the one spin that can give a non-zero product.
+__device__ __forceinline__ long term_count(int term, const ActDims& d) {
+  const long a2 = (long)d.nA2 * d.nA2;
+  switch (term) {
+    case T_A: return (long)d.nH2 * d.nP2;
+    case T_B: return (long)d.nV2 * a2;
+    case T_C: return (long)d.nC2 * a2;
+    case T_D: return (long)d.nV2 * a2;
+    case T_E: return (long)d.nC2 * a2;
+    case T_GVA: return (long)d.nV2 * a2;
+    case T_GVV: return a2 * a2;
+    case T_H: return (long)d.nH2 * d.nH2 * a2;
+    case T_I: return (long)d.nH2 * d.nP2 * a2;
+    case T_F4: return a2 * a2;
+    case T_F5: return (long)d.nC2 * d.nC2 * a2;
+    case T_F6: return (long)d.nC2 * d.nV2 * a2;
+    case T_F7: return (long)d.nV2 * a2 * d.nA2;
+    case T_F8: return (long)d.nC2 * a2 * d.nA2;
+  }
+  return 0;
+}
+
 __device__ double term_value(int term, long o, const Sizes& z, const ActDims& d,
                              const TermArgs& t) {
-  const int nA2 = d.nA2;
+  const int nA2 = d.nA2, nA = z.nA;
+  const int C2 = d.nC2;  // first active hole spin orbital
   double acc = 0.0;
   switch (term) {
     case T_A: {  // ft_j^b t_a^i gamma_i^j eta_b^a, outer (J, Bp)
-      if (o >= (long)d.nH2 * d.nP2) return 0.0;
       const int J = (int)(o / d.nP2), Bp = (int)(o % d.nP2);
       double gf = 0.0, te = 0.0;
-      const int k0 = (J < d.nC2) ? J : d.nC2, k1 = (J < d.nC2) ? J + 1 : d.nH2;
+      const int k0 = (J < C2) ? J : C2, k1 = (J < C2) ? J + 1 : d.nH2;
       for (int K = k0; K < k1; ++K) gf = fma(gam_h(d, t.gA, J, K), t.ft[(size_t)K * d.nP2 + Bp], gf);
       const int a0 = (Bp < nA2) ? 0 : Bp, a1 = (Bp < nA2) ? nA2 : Bp + 1;
       for (int A = a0; A < a1; ++A) te = fma(eta_p(d, t.gA, A, Bp), t.t1[(size_t)J * d.nP2 + A], te);
       return gf * te;
     }
-    case T_B: {  // 1/2 vt_{xy}^{ev} t_e^u lambda_{uv}^{xy}, outer E (virtual)
-      if (o >= d.nV2) return 0.0;
-      const int Ap = nA2 + (int)o;
-      for (int X = 0; X < nA2; ++X)
-        for (int Y = 0; Y < nA2; ++Y)
-          for (int V = 0; V < nA2; ++V) {
-            const double vt = t.W1Vt[w1i(d, d.nC2 + X, Y, Ap, V)];
-            if (vt == 0.0) continue;
-            for (int U = 0; U < nA2; ++U)
-              acc = fma(vt * t.t1[(size_t)(d.nC2 + U) * d.nP2 + Ap], t.lam[lami(d, U, V, X, Y)], acc);
-          }
+    case T_B: {  // 1/2 vt_{xy}^{ev} t_e^u lambda_{uv}^{xy}, outer (E, X, Y)
+      const int Y = (int)(o % nA2), X = (int)((o / nA2) % nA2);
+      const int Ap = nA2 + (int)(o / ((long)nA2 * nA2));
+      const int su = Ap & 1;  // t_e^u conserves spin
+      for (int V = 0; V < nA2; ++V) {
+        const double vt = t.W1Vt[w1i(d, C2 + X, Y, Ap, V)];
+        if (vt == 0.0) continue;
+        for (int u = 0; u < nA; ++u) {
+          const int U = 2 * u + su;
+          acc = fma(vt * t.t1[(size_t)(C2 + U) * d.nP2 + Ap], t.lam[lami(d, U, V, X, Y)], acc);
+        }
+      }
       return 0.5 * acc;
     }
-    case T_C: {  // -1/2 vt_{my}^{uv} t_x^m lambda_{uv}^{xy}, outer M (core)
-      if (o >= d.nC2) return 0.0;
-      const int M = (int)o;
-      for (int Y = 0; Y < nA2; ++Y)
-        for (int U = 0; U < nA2; ++U)
-          for (int V = 0; V < nA2; ++V) {
-            const double vt = t.W1Vt[w1i(d, M, Y, U, V)];
-            if (vt == 0.0) continue;
-            for (int X = 0; X < nA2; ++X)
-              acc = fma(vt * t.t1[(size_t)M * d.nP2 + X], t.lam[lami(d, U, V, X, Y)], acc);
-          }
+    case T_C: {  // -1/2 vt_{my}^{uv} t_x^m lambda_{uv}^{xy}, outer (M, Y, U)
+      const int U = (int)(o % nA2), Y = (int)((o / nA2) % nA2), M = (int)(o / ((long)nA2 * nA2));
+      const int sx = M & 1;
+      for (int V = 0; V < nA2; ++V) {
+        const double vt = t.W1Vt[w1i(d, M, Y, U, V)];
+        if (vt == 0.0) continue;
+        for (int x = 0; x < nA; ++x) {
+          const int X = 2 * x + sx;
+          acc = fma(vt * t.t1[(size_t)M * d.nP2 + X], t.lam[lami(d, U, V, X, Y)], acc);
+        }
+      }
       return -0.5 * acc;
     }
-    case T_D: {  // 1/2 ft_x^e t_{ey}^{uv} lambda_{uv}^{xy}, outer E
-      if (o >= d.nV2) return 0.0;
-      const int Ap = nA2 + (int)o;
-      for (int U = 0; U < nA2; ++U)
-        for (int V = 0; V < nA2; ++V)
-          for (int Y = 0; Y < nA2; ++Y) {
-            const double tt = t.W1T[w1i(d, d.nC2 + U, V, Ap, Y)];
-            if (tt == 0.0) continue;
-            for (int X = 0; X < nA2; ++X)
-              acc = fma(tt * t.ft[(size_t)(d.nC2 + X) * d.nP2 + Ap], t.lam[lami(d, U, V, X, Y)], acc);
-          }
+    case T_D: {  // 1/2 ft_x^e t_{ey}^{uv} lambda_{uv}^{xy}, outer (E, U, V)
+      const int V = (int)(o % nA2), U = (int)((o / nA2) % nA2);
+      const int Ap = nA2 + (int)(o / ((long)nA2 * nA2));
+      const int sx = Ap & 1;
+      for (int Y = 0; Y < nA2; ++Y) {
+        const double tt = t.W1T[w1i(d, C2 + U, V, Ap, Y)];
+        if (tt == 0.0) continue;
+        for (int x = 0; x < nA; ++x) {
+          const int X = 2 * x + sx;
+          acc = fma(tt * t.ft[(size_t)(C2 + X) * d.nP2 + Ap], t.lam[lami(d, U, V, X, Y)], acc);
+        }
+      }
       return 0.5 * acc;
     }
-    case T_E: {  // -1/2 ft_m^v t_{xy}^{um} lambda_{uv}^{xy}, outer M
-      if (o >= d.nC2) return 0.0;
-      const int M = (int)o;
-      for (int U = 0; U < nA2; ++U)
-        for (int X = 0; X < nA2; ++X)
-          for (int Y = 0; Y < nA2; ++Y) {
-            const double tt = t.W2T[w2i(d, d.nC2 + U, M, X, Y)];
-            if (tt == 0.0) continue;
-            for (int V = 0; V < nA2; ++V)
-              acc = fma(tt * t.ft[(size_t)M * d.nP2 + V], t.lam[lami(d, U, V, X, Y)], acc);
-          }
+    case T_E: {  // -1/2 ft_m^v t_{xy}^{um} lambda_{uv}^{xy}, outer (M, U, X)
+      const int X = (int)(o % nA2), U = (int)((o / nA2) % nA2), M = (int)(o / ((long)nA2 * nA2));
+      const int sv = M & 1;
+      for (int Y = 0; Y < nA2; ++Y) {
+        const double tt = t.W2T[w2i(d, C2 + U, M, X, Y)];
+        if (tt == 0.0) continue;
+        for (int v = 0; v < nA; ++v) {
+          const int V = 2 * v + sv;
+          acc = fma(tt * t.ft[(size_t)M * d.nP2 + V], t.lam[lami(d, U, V, X, Y)], acc);
+        }
+      }
       return -0.5 * acc;
     }
-    case T_GVA: {  // G with one virtual and one active particle, outer E
-      if (o >= d.nV2) return 0.0;
-      const int Ap = nA2 + (int)o;
-      for (int U = 0; U < nA2; ++U)
-        for (int V = 0; V < nA2; ++V)
-          for (int C = 0; C < nA2; ++C) {
-            double tg = 0.0;  // sum_a eta_c^a t_{a e}^{uv}, with the particle pair reversed
-            for (int A = 0; A < nA2; ++A)
-              tg = fma(ea(d, t.gA, C, A), t.W1T[w1i(d, d.nC2 + U, V, Ap, A)], tg);
-            if (tg == 0.0) continue;
-            for (int X = 0; X < nA2; ++X)
-              for (int Y = 0; Y < nA2; ++Y)
-                acc = fma(t.W1Vt[w1i(d, d.nC2 + X, Y, Ap, C)] * tg, t.lam[lami(d, U, V, X, Y)], acc);
+    case T_GVA: {  // G with one virtual and one active particle, outer (E, U, V)
+      const int V = (int)(o % nA2), U = (int)((o / nA2) % nA2);
+      const int Ap = nA2 + (int)(o / ((long)nA2 * nA2));
+      for (int Cc = 0; Cc < nA2; ++Cc) {
+        double tg = 0.0;  // sum_a eta_c^a t_{a e}^{uv}, with the particle pair reversed
+        for (int a = 0; a < nA; ++a) {
+          const int A = 2 * a + (Cc & 1);
+          tg = fma(ea(d, t.gA, Cc, A), t.W1T[w1i(d, C2 + U, V, Ap, A)], tg);
+        }
+        if (tg == 0.0) continue;
+        for (int X = 0; X < nA2; ++X) {
+          const int sy = (U & 1) + (V & 1) - (X & 1);  // cumulant spin rule
+          if (sy < 0 || sy > 1) continue;
+          for (int y = 0; y < nA; ++y) {
+            const int Y = 2 * y + sy;
+            acc = fma(t.W1Vt[w1i(d, C2 + X, Y, Ap, Cc)] * tg, t.lam[lami(d, U, V, X, Y)], acc);
           }
+        }
+      }
       return 0.25 * acc;
     }
     case T_GVV: {  // G with two virtual particles, outer (X, Y, U, V)
-      if (o >= (long)nA2 * nA2 * nA2 * nA2) return 0.0;
       const int V = (int)(o % nA2), U = (int)((o / nA2) % nA2), Y = (int)((o / (nA2 * nA2)) % nA2),
                 X = (int)(o / (nA2 * nA2 * nA2));
       return 0.125 * t.lam[lami(d, U, V, X, Y)] * s_vv(d, z.nA, t.P12, X, Y, U, V);
     }
-    case T_H: {  // 1/8 vt_{kl}^{uv} t_{xy}^{ij} gamma_i^k gamma_j^l lambda_{uv}^{xy}, outer (K, L)
-      if (o >= (long)d.nH2 * d.nH2) return 0.0;
-      const int K = (int)(o / d.nH2), L = (int)(o % d.nH2);
-      const int i0 = (K < d.nC2) ? K : d.nC2, i1 = (K < d.nC2) ? K + 1 : d.nH2;
-      const int j0 = (L < d.nC2) ? L : d.nC2, j1 = (L < d.nC2) ? L + 1 : d.nH2;
-      for (int X = 0; X < nA2; ++X)
-        for (int Y = 0; Y < nA2; ++Y) {
-          double th = 0.0;
-          for (int I = i0; I < i1; ++I)
-            for (int J = j0; J < j1; ++J)
-              th = fma(gam_h(d, t.gA, K, I) * gam_h(d, t.gA, L, J), t.W2T[w2i(d, I, J, X, Y)], th);
-          if (th == 0.0) continue;
-          for (int U = 0; U < nA2; ++U)
-            for (int V = 0; V < nA2; ++V)
-              acc = fma(t.W2Vt[w2i(d, K, L, U, V)] * th, t.lam[lami(d, U, V, X, Y)], acc);
+    case T_H: {  // 1/8 vt_{kl}^{uv} t_{xy}^{ij} gamma_i^k gamma_j^l lambda_{uv}^{xy}, outer (K, L, X, Y)
+      const int Y = (int)(o % nA2), X = (int)((o / nA2) % nA2);
+      const long kl = o / ((long)nA2 * nA2);
+      const int K = (int)(kl / d.nH2), L = (int)(kl % d.nH2);
+      double th = 0.0;
+      const int ni = (K < C2) ? 1 : nA, nj = (L < C2) ? 1 : nA;
+      for (int ii = 0; ii < ni; ++ii) {
+        const int I = (K < C2) ? K : C2 + 2 * ii + (K & 1);
+        const double gk = gam_h(d, t.gA, K, I);
+        if (gk == 0.0) continue;
+        for (int jj = 0; jj < nj; ++jj) {
+          const int J = (L < C2) ? L : C2 + 2 * jj + (L & 1);
+          th = fma(gk * gam_h(d, t.gA, L, J), t.W2T[w2i(d, I, J, X, Y)], th);
         }
+      }
+      if (th == 0.0) return 0.0;
+      for (int U = 0; U < nA2; ++U) {
+        const int sv = (X & 1) + (Y & 1) - (U & 1);
+        if (sv < 0 || sv > 1) continue;
+        for (int v = 0; v < nA; ++v) {
+          const int V = 2 * v + sv;
+          acc = fma(t.W2Vt[w2i(d, K, L, U, V)] * th, t.lam[lami(d, U, V, X, Y)], acc);
+        }
+      }
       return 0.125 * acc;
     }
-    case T_I: {  // vt_{jx}^{bu} t_{ay}^{iv} gamma_i^j eta_b^a lambda_{uv}^{xy}, outer (J, Bp)
-      if (o >= (long)d.nH2 * d.nP2) return 0.0;
-      const int J = (int)(o / d.nP2), Bp = (int)(o % d.nP2);
-      for (int U = 0; U < nA2; ++U)
-        for (int X = 0; X < nA2; ++X) {
-          const double vt = t.W1Vt[w1i(d, J, X, Bp, U)];
-          if (vt == 0.0) continue;
-          double c = 0.0;
-          for (int V = 0; V < nA2; ++V)
-            for (int Y = 0; Y < nA2; ++Y) c = fma(t.Ti[w1i(d, J, V, Bp, Y)], t.lam[lami(d, U, V, X, Y)], c);
-          acc = fma(vt, c, acc);
+    case T_I: {  // vt_{jx}^{bu} t_{ay}^{iv} gamma_i^j eta_b^a lambda_{uv}^{xy}, outer (J, Bp, U, X)
+      const int X = (int)(o % nA2), U = (int)((o / nA2) % nA2);
+      const long jb = o / ((long)nA2 * nA2);
+      const int J = (int)(jb / d.nP2), Bp = (int)(jb % d.nP2);
+      const double vt = t.W1Vt[w1i(d, J, X, Bp, U)];
+      if (vt == 0.0) return 0.0;
+      double c = 0.0;
+      for (int V = 0; V < nA2; ++V) {
+        const int sy = (U & 1) + (V & 1) - (X & 1);
+        if (sy < 0 || sy > 1) continue;
+        for (int y = 0; y < nA; ++y) {
+          const int Y = 2 * y + sy;
+          c = fma(t.Ti[w1i(d, J, V, Bp, Y)], t.lam[lami(d, U, V, X, Y)], c);
         }
-      return acc;
+      }
+      return vt * c;
     }
     case T_F4: {  // 1/4 vt_{xu}^{ef} t_{ef}^{yv} gamma_y^x gamma_v^u, outer (X, U, Y, V)
-      if (o >= (long)nA2 * nA2 * nA2 * nA2) return 0.0;
       const int V = (int)(o % nA2), Y = (int)((o / nA2) % nA2), U = (int)((o / (nA2 * nA2)) % nA2),
                 X = (int)(o / (nA2 * nA2 * nA2));
       return 0.25 * ga(d, t.gA, X, Y) * ga(d, t.gA, U, V) * s_vv(d, z.nA, t.P12, X, U, Y, V);
     }
-    case T_F5: {  // 1/4 vt_{mn}^{vy} t_{ux}^{mn} eta_v^u eta_y^x, outer (M, N)
-      if (o >= (long)d.nC2 * d.nC2) return 0.0;
-      const int M = (int)(o / d.nC2), N = (int)(o % d.nC2);
-      for (int V = 0; V < nA2; ++V)
-        for (int Y = 0; Y < nA2; ++Y) {
-          const double vt = t.W2Vt[w2i(d, M, N, V, Y)];
-          if (vt == 0.0) continue;
-          for (int U = 0; U < nA2; ++U)
-            for (int X = 0; X < nA2; ++X)
-              acc = fma(vt * ea(d, t.gA, U, V) * ea(d, t.gA, X, Y), t.W2T[w2i(d, M, N, U, X)], acc);
+    case T_F5: {  // 1/4 vt_{mn}^{vy} t_{ux}^{mn} eta_v^u eta_y^x, outer (M, N, V, Y)
+      const int Y = (int)(o % nA2), V = (int)((o / nA2) % nA2);
+      const long mn = o / ((long)nA2 * nA2);
+      const int M = (int)(mn / C2), N = (int)(mn % C2);
+      const double vt = t.W2Vt[w2i(d, M, N, V, Y)];
+      if (vt == 0.0) return 0.0;
+      for (int u = 0; u < nA; ++u) {
+        const int U = 2 * u + (V & 1);
+        const double eu = ea(d, t.gA, U, V);
+        for (int x = 0; x < nA; ++x) {
+          const int X = 2 * x + (Y & 1);
+          acc = fma(eu * ea(d, t.gA, X, Y), t.W2T[w2i(d, M, N, U, X)], acc);
         }
-      return 0.25 * acc;
+      }
+      return 0.25 * vt * acc;
     }
-    case T_F6: {  // vt_{mx}^{ve} t_{ue}^{my} gamma_y^x eta_v^u, outer (M, E)
-      if (o >= (long)d.nC2 * d.nV2) return 0.0;
-      const int M = (int)(o / d.nV2), Ap = nA2 + (int)(o % d.nV2);
-      for (int X = 0; X < nA2; ++X)
-        for (int V = 0; V < nA2; ++V) {
-          const double vt = t.W1Vt[w1i(d, M, X, Ap, V)];
-          if (vt == 0.0) continue;
-          for (int Y = 0; Y < nA2; ++Y)
-            for (int U = 0; U < nA2; ++U)
-              acc = fma(vt * ga(d, t.gA, X, Y) * ea(d, t.gA, U, V), t.W1T[w1i(d, M, Y, Ap, U)], acc);
+    case T_F6: {  // vt_{mx}^{ve} t_{ue}^{my} gamma_y^x eta_v^u, outer (M, E, X, V)
+      const int V = (int)(o % nA2), X = (int)((o / nA2) % nA2);
+      const long me = o / ((long)nA2 * nA2);
+      const int M = (int)(me / d.nV2), Ap = nA2 + (int)(me % d.nV2);
+      const double vt = t.W1Vt[w1i(d, M, X, Ap, V)];
+      if (vt == 0.0) return 0.0;
+      for (int y = 0; y < nA; ++y) {
+        const int Y = 2 * y + (X & 1);
+        const double gy = ga(d, t.gA, X, Y);
+        for (int u = 0; u < nA; ++u) {
+          const int U = 2 * u + (V & 1);
+          acc = fma(gy * ea(d, t.gA, U, V), t.W1T[w1i(d, M, Y, Ap, U)], acc);
         }
-      return acc;
+      }
+      return vt * acc;
     }
-    case T_F7: {  // 1/2 vt_{yz}^{ve} t_{ue}^{wx} gamma_w^y gamma_x^z eta_v^u, outer E
-      if (o >= d.nV2) return 0.0;
-      const int Ap = nA2 + (int)o;
-      for (int Y = 0; Y < nA2; ++Y)
-        for (int Z = 0; Z < nA2; ++Z)
-          for (int V = 0; V < nA2; ++V) {
-            const double vt = t.W1Vt[w1i(d, d.nC2 + Y, Z, Ap, V)];
-            if (vt == 0.0) continue;
-            for (int W = 0; W < nA2; ++W)
-              for (int X = 0; X < nA2; ++X) {
-                const double gg = ga(d, t.gA, Y, W) * ga(d, t.gA, Z, X);
-                if (gg == 0.0) continue;
-                for (int U = 0; U < nA2; ++U)
-                  acc = fma(vt * gg * ea(d, t.gA, U, V), t.W1T[w1i(d, d.nC2 + W, X, Ap, U)], acc);
-              }
+    case T_F7: {  // 1/2 vt_{yz}^{ve} t_{ue}^{wx} gamma_w^y gamma_x^z eta_v^u, outer (E, Y, Z, V)
+      const int V = (int)(o % nA2), Z = (int)((o / nA2) % nA2), Y = (int)((o / (nA2 * nA2)) % nA2);
+      const int Ap = nA2 + (int)(o / ((long)nA2 * nA2 * nA2));
+      const double vt = t.W1Vt[w1i(d, C2 + Y, Z, Ap, V)];
+      if (vt == 0.0) return 0.0;
+      for (int w = 0; w < nA; ++w) {
+        const int W = 2 * w + (Y & 1);
+        const double gw = ga(d, t.gA, Y, W);
+        for (int x = 0; x < nA; ++x) {
+          const int X = 2 * x + (Z & 1);
+          const double gg = gw * ga(d, t.gA, Z, X);
+          if (gg == 0.0) continue;
+          for (int u = 0; u < nA; ++u) {
+            const int U = 2 * u + (V & 1);
+            acc = fma(gg * ea(d, t.gA, U, V), t.W1T[w1i(d, C2 + W, X, Ap, U)], acc);
           }
-      return 0.5 * acc;
+        }
+      }
+      return 0.5 * vt * acc;
     }
-    case T_F8: {  // 1/2 vt_{mw}^{vy} t_{ux}^{mz} gamma_z^w eta_v^u eta_y^x, outer M
-      if (o >= d.nC2) return 0.0;
-      const int M = (int)o;
-      for (int W = 0; W < nA2; ++W)
-        for (int V = 0; V < nA2; ++V)
-          for (int Y = 0; Y < nA2; ++Y) {
-            const double vt = t.W1Vt[w1i(d, M, W, V, Y)];
-            if (vt == 0.0) continue;
-            for (int Z = 0; Z < nA2; ++Z) {
-              const double g = ga(d, t.gA, W, Z);
-              if (g == 0.0) continue;
-              for (int U = 0; U < nA2; ++U)
-                for (int X = 0; X < nA2; ++X)
-                  acc = fma(vt * g * ea(d, t.gA, U, V) * ea(d, t.gA, X, Y), t.W1T[w1i(d, M, Z, U, X)],
-                            acc);
-            }
+    case T_F8: {  // 1/2 vt_{mw}^{vy} t_{ux}^{mz} gamma_z^w eta_v^u eta_y^x, outer (M, W, V, Y)
+      const int Y = (int)(o % nA2), V = (int)((o / nA2) % nA2), W = (int)((o / (nA2 * nA2)) % nA2);
+      const int M = (int)(o / ((long)nA2 * nA2 * nA2));
+      const double vt = t.W1Vt[w1i(d, M, W, V, Y)];
+      if (vt == 0.0) return 0.0;
+      for (int zz = 0; zz < nA; ++zz) {
+        const int Z = 2 * zz + (W & 1);
+        const double g = ga(d, t.gA, W, Z);
+        if (g == 0.0) continue;
+        for (int u = 0; u < nA; ++u) {
+          const int U = 2 * u + (V & 1);
+          const double ge = g * ea(d, t.gA, U, V);
+          for (int x = 0; x < nA; ++x) {
+            const int X = 2 * x + (Y & 1);
+            acc = fma(ge * ea(d, t.gA, X, Y), t.W1T[w1i(d, M, Z, U, X)], acc);
           }
-      return 0.5 * acc;
+        }
+      }
+      return 0.5 * vt * acc;
     }
   }
   return 0.0;
 }
 
 constexpr int TERM_NT = 128;
+constexpr int TERM_BLOCKS = 304;  // CTAs per term, grid-stride over its outer index
 
 __global__ void __launch_bounds__(TERM_NT) terms_kernel(Sizes z, TermArgs t,
                                                         double* __restrict__ partials) {
   __shared__ double red[TERM_NT / 32];
   const ActDims d = act_dims(z);
-  const long o = (long)blockIdx.x * TERM_NT + threadIdx.x;
-  const double v = term_value(blockIdx.y, o, z, d, t);
+  const int term = blockIdx.y;
+  const long n = term_count(term, d);
+  double v = 0.0;
+  for (long o = (long)blockIdx.x * TERM_NT + threadIdx.x; o < n; o += (long)gridDim.x * TERM_NT)
+    v += term_value(term, o, z, d, t);
   const double tot = block_sum<TERM_NT>(v, red);
   if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
-static long term_outer_max(const Sizes& z) {
-  const ActDims d = act_dims(z);
-  long m = (long)d.nH2 * d.nP2;
-  m = m > (long)d.nH2 * d.nH2 ? m : (long)d.nH2 * d.nH2;
-  m = m > (long)d.nC2 * d.nV2 ? m : (long)d.nC2 * d.nV2;
-  const long a4 = (long)d.nA2 * d.nA2 * d.nA2 * d.nA2;
-  return m > a4 ? m : a4;
-}
-
-static int term_blocks(const Sizes& z) { return (int)((term_outer_max(z) + TERM_NT - 1) / TERM_NT); }
+static int term_blocks(const Sizes&) { return TERM_BLOCKS; }
 
 bool active_alloc(dsrg_plan* p) {
   const Sizes& z = p->z;
@@ -737,7 +874,8 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     DSRG_LAUNCH_CHECK(p);
   }
   {
-    const size_t n = w.w1n + w.w2n + (size_t)d.nA2 * d.nA2 * d.nA2 * d.nA2 + (size_t)d.nA2 * d.nA2;
+    const size_t n = w.w1n / 16 + w.w2n / 16 + (size_t)d.nA2 * d.nA2 * d.nA2 * d.nA2 +
+                     (size_t)d.nA2 * d.nA2;
     build_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         eps, G, L, s, z, w.K1, w.K2, w.K3, w.W1, w.W2, w.lam, w.gA, w.w1n, w.w2n);
     DSRG_LAUNCH_CHECK(p);
@@ -757,15 +895,26 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
   }
   const int nA4 = z.nA * z.nA * z.nA * z.nA;
   {
-    if (z.nA <= 2) {
-      if (z.nA == 1)
+    const size_t smg = (size_t)3 * z.nA * z.nA * ACTVV_CH * sizeof(double);
+#define ACTVV_GEN(NA_)                                                                       \
+  case NA_:                                                                                  \
+    raise_smem_limit((const void*)actvv_gen_kernel<NA_>, smg);                               \
+    actvv_gen_kernel<NA_><<<ACTVV_BLOCKS, 256, smg, st>>>(eps, s, z, w.M, w.P12part);        \
+    break;
+    switch (z.nA) {
+      case 1:
         actvv_small_kernel<1><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
-      else
+        break;
+      case 2:
         actvv_small_kernel<2><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
-    } else {
-      dim3 grid(ACTVV_BLOCKS, nA4);
-      actvv_kernel<<<grid, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+        break;
+      ACTVV_GEN(3) ACTVV_GEN(4) ACTVV_GEN(5) ACTVV_GEN(6) ACTVV_GEN(7) ACTVV_GEN(8)
+      default: {
+        dim3 grid(ACTVV_BLOCKS, nA4);
+        actvv_kernel<<<grid, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+      }
     }
+#undef ACTVV_GEN
     DSRG_LAUNCH_CHECK(p);
     actvv_reduce_kernel<<<(2 * nA4 + 127) / 128, 128, 0, st>>>(nA4, ACTVV_BLOCKS, w.P12part, w.P12);
     DSRG_LAUNCH_CHECK(p);

@@ -2,6 +2,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "internal.cuh"
@@ -29,6 +31,20 @@ bool plan_alloc(dsrg_plan* p, void** ptr, size_t bytes) {
   p->allocs.push_back(*ptr);
   p->ws_bytes += bytes;
   return true;
+}
+
+cudaError_t raise_smem_limit(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> cur;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& c = cur[std::make_pair(func, dev)];
+  if (bytes <= c) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
 }
 
 static void tile_pairs(int n, int tile, std::vector<int2>& out) {
@@ -158,6 +174,12 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
   ok = ok && plan_alloc(p, (void**)&p->d_tp_cavv, tp32.size() * sizeof(int2));
   ok = ok && plan_alloc(p, (void**)&p->d_partials, (size_t)np * sizeof(double));
   ok = ok && plan_alloc(p, (void**)&p->d_segs, p->segs.size() * sizeof(Segment));
+  std::vector<int2> chunks;
+  for (int g = 0; g < (int)p->segs.size(); ++g)
+    for (int c = 0; c * RED_CHUNK < p->segs[g].count; ++c) chunks.push_back(make_int2(g, c));
+  p->n_chunks = (int)chunks.size();
+  ok = ok && plan_alloc(p, (void**)&p->d_chunks, chunks.size() * sizeof(int2)) &&
+       plan_alloc(p, (void**)&p->d_red, chunks.size() * 2 * sizeof(double));
   ok = ok && plan_alloc(p, (void**)&p->d_status, sizeof(int));
   ok = ok && active_alloc(p);
   if (ok && prec != DSRG_PREC_FP64)
@@ -192,6 +214,8 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_segs, p->segs.data(), p->segs.size() * sizeof(Segment),
                    cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !chunks.empty())
+    e = cudaMemcpy(p->d_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_partials, 0, (size_t)np * sizeof(double));
   if (e != cudaSuccess) {

@@ -1192,7 +1192,7 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   // ---- F3
   {
     const size_t sm = ccav_adj_smem(z);
-    cudaFuncSetAttribute(ccav_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)ccav_adj_kernel, sm);
     ccav_adj_kernel<<<z.nV, 256, sm, st>>>(B, eps, G, s, z, w->dZ, deps, ds);
     DSRG_LAUNCH_CHECK(p);
     const long long nCV = (long long)z.nC * nV, nCCV = (long long)z.nC * nCV;

@@ -32,6 +32,7 @@ enum Block { BLK_CCVV = 0, BLK_CAVV = 1, BLK_CCAV = 2, BLK_ACTIVE = 3 };
 struct Segment {
   int begin, count, block;
 };
+constexpr int RED_CHUNK = 4096;  // partials per CTA of the first reduction level
 
 // Active-block workspace (spin-orbital tables and spatial integrals).
 struct ActiveWs {
@@ -84,6 +85,9 @@ struct dsrg_plan {
   int n_partials = 0;
   std::vector<dsrg::Segment> segs;
   dsrg::Segment* d_segs = nullptr;
+  int n_chunks = 0;             // (segment, chunk) pairs of the first reduction level
+  int2* d_chunks = nullptr;
+  double* d_red = nullptr;      // [n_chunks][2] chunk sums and compensations
   int seg_ccvv = -1, seg_cavv = -1, seg_ccav = -1;
   std::vector<int> seg_active;
   double* d_pairbuf = nullptr;  // [nC*nC] pair energies (scratch for the pairs entry)
@@ -105,6 +109,11 @@ namespace dsrg {
 
 // Allocation helper: records the pointer in the plan; returns false on failure.
 bool plan_alloc(dsrg_plan* p, void** ptr, size_t bytes);
+
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current
+// device. A launch captured in a CUDA graph keeps its own size; lowering the
+// limit afterwards for a smaller problem would invalidate that launch.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 
 // Launchers (each returns cudaSuccess or the launch error; adds to p->launches).
 cudaError_t launch_ccvv_fp64(dsrg_plan* p, const double* B, const double* eps, double s);

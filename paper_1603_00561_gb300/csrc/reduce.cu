@@ -14,46 +14,63 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
   s = t;
 }
 
-// One CTA of 256 threads. Each thread sums a fixed strided subset of each
-// block's segments; the 256 (sum, compensation) pairs are then folded in
-// index order by thread 0. out[0..3] = blocks, out[4] = their total.
-__global__ void __launch_bounds__(256) final_reduce_kernel(const double* __restrict__ partials,
-                                                           const Segment* __restrict__ segs,
-                                                           int nseg, double* __restrict__ out) {
+// Level 1: one CTA of 256 threads per chunk of RED_CHUNK partials of one
+// segment. Each thread sums a fixed strided subset with Neumaier compensation;
+// thread 0 folds the 256 (sum, compensation) pairs in index order and stores
+// the chunk's pair.
+__global__ void __launch_bounds__(256) reduce_chunks_kernel(const double* __restrict__ partials,
+                                                            const Segment* __restrict__ segs,
+                                                            const int2* __restrict__ chunks,
+                                                            double* __restrict__ red) {
   __shared__ double sh_s[256], sh_c[256];
-  __shared__ double blk[4];
-  for (int b = 0; b < 4; ++b) {
-    double s = 0.0, c = 0.0;
-    for (int g = 0; g < nseg; ++g) {
-      if (segs[g].block != b) continue;
-      const double* p = partials + segs[g].begin;
-      for (int k = threadIdx.x; k < segs[g].count; k += 256) neumaier_add(s, c, p[k]);
-    }
-    sh_s[threadIdx.x] = s;
-    sh_c[threadIdx.x] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double S = 0.0, C = 0.0;
-      for (int k = 0; k < 256; ++k) {
-        neumaier_add(S, C, sh_s[k]);
-        C += sh_c[k];
-      }
-      blk[b] = S + C;
-    }
-    __syncthreads();
-  }
+  const int2 ch = chunks[blockIdx.x];
+  const Segment sg = segs[ch.x];
+  const int k0 = ch.y * RED_CHUNK;
+  const int k1 = min(sg.count, k0 + RED_CHUNK);
+  const double* p = partials + sg.begin;
+  double s = 0.0, c = 0.0;
+  for (int k = k0 + threadIdx.x; k < k1; k += 256) neumaier_add(s, c, p[k]);
+  sh_s[threadIdx.x] = s;
+  sh_c[threadIdx.x] = c;
+  __syncthreads();
   if (threadIdx.x == 0) {
     double S = 0.0, C = 0.0;
-    for (int b = 0; b < 4; ++b) {
-      out[b] = blk[b];
-      neumaier_add(S, C, blk[b]);
+    for (int k = 0; k < 256; ++k) {
+      neumaier_add(S, C, sh_s[k]);
+      C += sh_c[k];
     }
-    out[4] = S + C;
+    red[2 * blockIdx.x] = S;
+    red[2 * blockIdx.x + 1] = C;
   }
 }
 
+// Level 2 (one thread): the chunk pairs of each block in chunk order.
+// out[0..3] = blocks, out[4] = their total.
+__global__ void reduce_blocks_kernel(const Segment* __restrict__ segs, const int2* __restrict__ chunks,
+                                     int nchunks, const double* __restrict__ red,
+                                     double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double T = 0.0, TC = 0.0;
+  for (int b = 0; b < 4; ++b) {
+    double S = 0.0, C = 0.0;
+    for (int k = 0; k < nchunks; ++k) {
+      if (segs[chunks[k].x].block != b) continue;
+      neumaier_add(S, C, red[2 * k]);
+      C += red[2 * k + 1];
+    }
+    out[b] = S + C;
+    neumaier_add(T, TC, out[b]);
+  }
+  out[4] = T + TC;
+}
+
 cudaError_t launch_final_reduce(dsrg_plan* p, double* out) {
-  final_reduce_kernel<<<1, 256, 0, p->stream>>>(p->d_partials, p->d_segs, (int)p->segs.size(), out);
+  if (p->n_chunks > 0) {
+    reduce_chunks_kernel<<<p->n_chunks, 256, 0, p->stream>>>(p->d_partials, p->d_segs, p->d_chunks,
+                                                            p->d_red);
+    DSRG_LAUNCH_CHECK(p);
+  }
+  reduce_blocks_kernel<<<1, 32, 0, p->stream>>>(p->d_segs, p->d_chunks, p->n_chunks, p->d_red, out);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }

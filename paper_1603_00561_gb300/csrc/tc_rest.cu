@@ -677,10 +677,10 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     const CUtensorMap* mh = split_map(p, true);
     const CUtensorMap* ml = split_map(p, false);
     if (bf16) {
-      cudaFuncSetAttribute(split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_limit((const void*)split_gemm_kernel<true>, sm);
       split_gemm_kernel<true><<<st->grid, G_THREADS, sm, stream>>>(*mh, *ml, a);
     } else {
-      cudaFuncSetAttribute(split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      raise_smem_limit((const void*)split_gemm_kernel<false>, sm);
       split_gemm_kernel<false><<<st->grid, G_THREADS, sm, stream>>>(*mh, *ml, a);
     }
     DSRG_LAUNCH_CHECK(p);
@@ -696,7 +696,7 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     const size_t sm = f2_smem_bytes(z.nA);
 #define F2_LAUNCH(NA_)                                                                             \
   case NA_:                                                                                        \
-    cudaFuncSetAttribute(cavv_f2_kernel<NA_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    raise_smem_limit((const void*)cavv_f2_kernel<NA_>, sm); \
     cavv_f2_kernel<NA_><<<sg.count, 256, sm, stream>>>(st->Y, st->ldy, st->nVpad, eps, G, s, z,       \
                                                       st->d_tp, st->n_tp, st->alpha, st->pinfo,   \
                                                       st->tau1, p->d_partials + sg.begin);        \
@@ -714,7 +714,7 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     const size_t sm = f3_smem_bytes(z);
 #define F3_LAUNCH(NA_)                                                                             \
   case NA_:                                                                                        \
-    cudaFuncSetAttribute(ccav_f3_kernel<NA_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    raise_smem_limit((const void*)ccav_f3_kernel<NA_>, sm); \
     ccav_f3_kernel<NA_><<<sg.count, 256, sm, stream>>>(st->Y, st->ldy, st->nVpad, st->xc, eps, G, s, \
                                                       z, p->d_partials + sg.begin);              \
     break;

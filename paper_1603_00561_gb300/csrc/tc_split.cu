@@ -778,10 +778,10 @@ cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtenso
   a.status = p->d_status;
   const size_t sm = split_smem_bytes();
   if (bf16) {
-    cudaFuncSetAttribute(ccvv_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)ccvv_split_kernel<true>, sm);
     ccvv_split_kernel<true><<<grid, SPLIT_THREADS, sm, p->stream>>>(mh, ml, a);
   } else {
-    cudaFuncSetAttribute(ccvv_split_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_smem_limit((const void*)ccvv_split_kernel<false>, sm);
     ccvv_split_kernel<false><<<grid, SPLIT_THREADS, sm, p->stream>>>(mh, ml, a);
   }
   DSRG_LAUNCH_CHECK(p);
