@@ -35,6 +35,10 @@ WORKLOADS = {
 }
 # nominal dense rates (TFLOP/s) of the recipe, used to scale the measured BF16 peak
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+# DRAM bytes (read + write) per launch of the CCVV kernel from one ncu capture,
+# keyed by (workload, precision, item order); summaries under profiles/. Any
+# other combination, or a kernel changed since the capture, reports null.
+TRAFFIC = {}
 
 
 def ccvv_flops(nC, nV, Q):
@@ -221,6 +225,7 @@ def time_batch(pk, torch, nmol, prec):
     flops = sum(ccvv_flops(m.ncore, m.nvirt, m.naux) for m in mols)
     b = pk.Batch([(m.ncore, m.nactive, m.nvirt, m.naux) for m in mols], precision=prec)
     svals = [m.s for m in mols]
+    order = b.autotune(dev, svals, reps=1) if prec != "fp64" else None   # setup, not timed
     out = b.energy(dev, svals)          # captures the graph
     b.energy(dev, svals, out=out)
     torch.cuda.synchronize()
@@ -244,7 +249,7 @@ def time_batch(pk, torch, nmol, prec):
     t64 = e0.elapsed_time(e1) / 1e3
     ob = out.cpu().numpy()
     err = max(abs(ob[k][4] - float(o64[k][4])) / abs(float(o64[k][4])) for k in range(nmol))
-    res = {"n_mol": nmol, "precision": prec, "ms_per_batch": tb * 1e3,
+    res = {"n_mol": nmol, "precision": prec, "item_order": order, "ms_per_batch": tb * 1e3,
            "molecules_per_s": nmol / tb, "aggregate_ccvv_tflops": flops / tb / 1e12,
            "graph_kernel_launches": b.launch_count(),
            "fp64_one_by_one_ms": t64 * 1e3, "fp64_one_by_one_molecules_per_s": nmol / t64,
@@ -302,6 +307,8 @@ def main():
     B, eps, g, l = pk.to_device(p)
     out = torch.empty(5, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
+    # schedule autotuning of the CCVV launch (setup, not timed): item orders timed on these inputs
+    item_order = plan.autotune(B, eps, p.s, reps=2) if prec != "fp64" else None
 
     def step():
         plan.energy(B, eps, g, l, p.s, out=out)
@@ -336,20 +343,23 @@ def main():
     flops = ccvv_flops(p.ncore, p.nvirt, p.naux)
     value = world * flops / t_step / 1e12
 
-    # dominant kernel: the CCVV pair contraction, timed alone with events on the same stream
-    pairs_out = torch.empty((p.ncore, p.ncore), dtype=torch.float64, device="cuda")
-    for _ in range(2):
-        plan.pair_energies(B, eps, p.s, out=pairs_out)
+    # dominant kernel: the CCVV pair contraction alone, timed with CUDA events on the
+    # plan's stream inside the library (planes staged first, one untimed launch)
     nk = max(3, min(args.steps, 10))
-    k0 = torch.cuda.Event(enable_timing=True)
-    k1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    k0.record(stream)
-    for _ in range(nk):
+    if prec != "fp64":
+        t_ccvv = plan.time_ccvv(B, eps, p.s, reps=nk) / 1e3
+    else:
+        pairs_out = torch.empty((p.ncore, p.ncore), dtype=torch.float64, device="cuda")
         plan.pair_energies(B, eps, p.s, out=pairs_out)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    t_ccvv = k0.elapsed_time(k1) / 1e3 / nk
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        k0.record(stream)
+        for _ in range(nk):
+            plan.pair_energies(B, eps, p.s, out=pairs_out)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        t_ccvv = k0.elapsed_time(k1) / 1e3 / nk
     peaks, peak_kind = load_peaks()
     if prec == "fp64":
         mult, peak = 1, peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
@@ -361,8 +371,9 @@ def main():
         mult, peak = 3, peaks["bf16_tflops"]
         peak_note = f"bf16 {peak_kind} peak; achieved counts 3 MMA products"
     achieved = mult * flops / t_ccvv / 1e12
+    traffic = TRAFFIC.get((args.workload, prec, item_order))
     roofline = {"bound": "tensor" if prec != "fp64" else "fp64", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "kernel": "ccvv pair contraction", "ccvv_ms": t_ccvv * 1e3,
                 "algorithmic_tflops": flops / t_ccvv / 1e12, "peak_source": peak_note}
 
@@ -373,12 +384,14 @@ def main():
     lh = torch.from_numpy(np.ascontiguousarray(p.lambda2)).pin_memory()
     oh = torch.zeros(5, dtype=torch.float64).pin_memory()
     plan.energy_host(Bh, eh, gh, lh, p.s, out=oh)
-    ne2e = max(2, min(args.steps, 5))
+    ne2e = max(3, min(args.steps, 7))
     barrier()
-    t0 = time.perf_counter()
+    te2e = []
     for _ in range(ne2e):
-        plan.energy_host(Bh, eh, gh, lh, p.s, out=oh)
-    t_e2e = (time.perf_counter() - t0) / ne2e
+        t0 = time.perf_counter()
+        plan.energy_host(Bh, eh, gh, lh, p.s, out=oh)   # synchronises (host out)
+        te2e.append(time.perf_counter() - t0)
+    t_e2e = float(np.median(te2e))
     te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
@@ -420,6 +433,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, **cfg, "precision": prec,
+                       "item_order": item_order,
                        "l2": ("inputs larger than L2 (B is %.2f GB, L2 129 MB)" % (p.B.nbytes / 1e9))
                        if p.B.nbytes > 129e6 else "inputs smaller than L2"},
             "e2_ms_per_molecule": t_step * 1e3,

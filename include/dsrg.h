@@ -178,6 +178,43 @@ dsrg_status_t dsrg_batch_sync(dsrg_batch_t *batch);
 int32_t dsrg_batch_launch_count(const dsrg_batch_t *batch);
 const char *dsrg_batch_last_error(const dsrg_batch_t *batch);
 
+/* Schedule tuning of the split-precision CCVV launch (build-side; the paper has
+ * no counterpart). Work items (core pair x virtual tile pair) are dealt to the
+ * SMs in a static order, and items that run at the same time share operand
+ * tiles in L2 according to that order. A schedule code holds the order in its
+ * low 16 bits: pair-major (0), or core orbitals grouped in blocks of G (2G:
+ * tile pairs outer; 2G+1: pairs outer); and in bits 16 and up the number of K
+ * stages (0..64) ahead that the producer prefetches into L2. The autotuner tries
+ * the orders {0, 2G and 2G+1 for a few G} with prefetch distances {0, 4, 12},
+ * stages the given inputs, times `reps` launches of the CCVV kernel under every
+ * candidate with CUDA events on the plan's (or batch's) stream, keeps the
+ * fastest and returns its code in *chosen (may be NULL). Energies do not depend
+ * on the schedule: every item writes its own partial sum, reduced in a fixed order.
+ * Synchronous; do not call while the stream is being captured. FP64 plans and
+ * batches: no-op, *chosen = -1. B, eps: device arrays as for dsrg_mrpt2_energy
+ * (for the batch: host arrays of device pointers, s a host array). */
+dsrg_status_t dsrg_plan_autotune(dsrg_plan_t *plan, const double *B, const double *eps, double s,
+                                 int32_t reps, int32_t *chosen);
+dsrg_status_t dsrg_batch_autotune(dsrg_batch_t *batch, const double *const *B,
+                                  const double *const *eps, const double *s, int32_t reps,
+                                  int32_t *chosen);
+/* Schedule code in use (-1 for FP64), and setting one directly (a code found
+ * earlier; prefetch distance <= 64; no-op for FP64). The batch
+ * setter waits for the batch's stream first; neither may run while a launch
+ * that uses the schedule is being captured. */
+int32_t dsrg_plan_item_order(const dsrg_plan_t *plan);
+int32_t dsrg_batch_item_order(const dsrg_batch_t *batch);
+dsrg_status_t dsrg_plan_set_item_order(dsrg_plan_t *plan, int32_t order);
+dsrg_status_t dsrg_batch_set_item_order(dsrg_batch_t *batch, int32_t order);
+
+/* Device time of the split-precision CCVV kernel alone (Eq. (23) pair GEMMs
+ * with the fused regulator epilogue): stages the inputs, makes one untimed
+ * launch, then times `reps` launches between two CUDA events recorded on the
+ * plan's stream; *ms = average per launch. Synchronous. FP64 plans:
+ * DSRG_ERR_UNSUPPORTED. */
+dsrg_status_t dsrg_plan_time_ccvv(dsrg_plan_t *plan, const double *B, const double *eps, double s,
+                                  int32_t reps, float *ms);
+
 /* E_CCVV without any device allocation (the paper has no counterpart; this is a
  * service to callers that cannot call cudaMalloc, e.g. code running inside a
  * memory pool it does not own or a host that forbids allocation on its hot

@@ -138,6 +138,31 @@ class Plan:
         self._check(st, "dsrg_mrpt2_energy_host")
         return out
 
+    def autotune(self, B, eps, s: float, reps: int = 3) -> int:
+        """Time the candidate work-item orders of the CCVV launch on these inputs
+        and keep the fastest (``dsrg_plan_autotune``); returns its code."""
+        chosen = C.c_int32(-1)
+        self._stream()
+        st = self.lib.dsrg_plan_autotune(self.h, _ptr(B), _ptr(eps), float(s), int(reps), C.byref(chosen))
+        self._check(st, "dsrg_plan_autotune")
+        return int(chosen.value)
+
+    @property
+    def item_order(self) -> int:
+        return int(self.lib.dsrg_plan_item_order(self.h))
+
+    @item_order.setter
+    def item_order(self, order: int):
+        self._check(self.lib.dsrg_plan_set_item_order(self.h, int(order)), "dsrg_plan_set_item_order")
+
+    def time_ccvv(self, B, eps, s: float, reps: int = 5) -> float:
+        """Average device milliseconds of the CCVV kernel alone (``dsrg_plan_time_ccvv``)."""
+        ms = C.c_float(0.0)
+        self._stream()
+        st = self.lib.dsrg_plan_time_ccvv(self.h, _ptr(B), _ptr(eps), float(s), int(reps), C.byref(ms))
+        self._check(st, "dsrg_plan_time_ccvv")
+        return float(ms.value)
+
     def sync(self):
         self._check(self.lib.dsrg_plan_sync(self.h), "dsrg_plan_sync")
 
@@ -187,6 +212,29 @@ class Batch:
         if st != _native.OK:
             raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
         return out
+
+    def autotune(self, inputs, s, reps: int = 2) -> int:
+        """Time the candidate work-item orders of the batched CCVV launch and keep
+        the fastest (``dsrg_batch_autotune``); returns its code."""
+        P = C.c_void_p * self.n
+        Bs = P(*[_ptr(t[0]) for t in inputs])
+        es = P(*[_ptr(t[1]) for t in inputs])
+        svals = (C.c_double * self.n)(*[float(x) for x in s])
+        chosen = C.c_int32(-1)
+        st = self.lib.dsrg_batch_autotune(self.h, Bs, es, svals, int(reps), C.byref(chosen))
+        if st != _native.OK:
+            raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
+        return int(chosen.value)
+
+    @property
+    def item_order(self) -> int:
+        return int(self.lib.dsrg_batch_item_order(self.h))
+
+    @item_order.setter
+    def item_order(self, order: int):
+        st = self.lib.dsrg_batch_set_item_order(self.h, int(order))
+        if st != _native.OK:
+            raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
 
     def sync(self):
         st = self.lib.dsrg_batch_sync(self.h)

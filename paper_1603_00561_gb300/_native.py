@@ -24,6 +24,8 @@ EXPORTS = [
     "dsrg_status_string", "dsrg_plan_last_error",
     "dsrg_batch_plan", "dsrg_batch_destroy", "dsrg_mrpt2_energy_batched", "dsrg_batch_sync",
     "dsrg_batch_launch_count", "dsrg_batch_last_error", "dsrg_ccvv_energy_noalloc",
+    "dsrg_plan_autotune", "dsrg_batch_autotune", "dsrg_plan_item_order", "dsrg_batch_item_order",
+    "dsrg_plan_time_ccvv", "dsrg_plan_set_item_order", "dsrg_batch_set_item_order",
 ]
 
 
@@ -83,6 +85,21 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_batch_last_error.restype = C.c_char_p
     lib.dsrg_ccvv_energy_noalloc.argtypes = [C.POINTER(Sizes), vp, vp, C.c_double, vp, vp]
     lib.dsrg_ccvv_energy_noalloc.restype = st
+    lib.dsrg_plan_autotune.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.POINTER(C.c_int32)]
+    lib.dsrg_plan_autotune.restype = st
+    lib.dsrg_batch_autotune.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_double),
+                                        C.c_int32, C.POINTER(C.c_int32)]
+    lib.dsrg_batch_autotune.restype = st
+    lib.dsrg_plan_item_order.argtypes = [vp]
+    lib.dsrg_plan_item_order.restype = C.c_int32
+    lib.dsrg_batch_item_order.argtypes = [vp]
+    lib.dsrg_batch_item_order.restype = C.c_int32
+    lib.dsrg_plan_time_ccvv.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.POINTER(C.c_float)]
+    lib.dsrg_plan_time_ccvv.restype = st
+    lib.dsrg_plan_set_item_order.argtypes = [vp, C.c_int32]
+    lib.dsrg_plan_set_item_order.restype = st
+    lib.dsrg_batch_set_item_order.argtypes = [vp, C.c_int32]
+    lib.dsrg_batch_set_item_order.restype = st
     _ = dp
     _lib = lib
     return lib

@@ -358,6 +358,35 @@ __global__ void __launch_bounds__(256) gram_aavv_kernel(const double* __restrict
 // (M_vy[e,f] = M_yv[f,e]) with R = (1 + exp(-s D_xu^2)) (1 - exp(-s D_yv^2))/D_yv.
 constexpr int ACTVV_BLOCKS = 152;
 
+// Factor tables of exp(-s D_p^2), D_p = E_p - e_e - e_f for the active pairs
+// p = (x, u), E_p = e_x + e_u: exp(-s E_p^2) exp(2 s E_p e_e) exp(2 s E_p e_f)
+// exp(-s (e_e + e_f)^2). alpha == nullptr: evaluate exp directly.
+struct ActFact {
+  const double* alpha;  // [nA^2][ld]  exp(2 s E_p e_e)
+  const double* pinfo;  // [nA^2][4]   E_p, exp(-s E_p^2), factorisable flag
+  const double* tau;    // [ld][ld]    exp(-s (e_e + e_f)^2)
+  int ld;
+};
+
+// Rv = 1 + exp(-s D^2), Rt = (1 - exp(-s D^2)) / D in FP64; g = exp(-s D^2)
+// from the factor tables when fact, 1/D as an FP32 seed and one Newton step;
+// |D| < 1/4 takes expm1 and an FP64 divide.
+__device__ __forceinline__ void reg_pair(double D, double s, bool fact, double g, double& rv,
+                                         double& rt) {
+  if (fact && fabs(D) >= 0.25) {
+    float r0f;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
+    const double r0 = (double)r0f;
+    const double en = fma(-D, r0, 1.0);
+    const double R0 = fma(-g, r0, r0);
+    rt = fma(R0, en, R0);
+    rv = 1.0 + g;
+  } else {
+    rt = reg_t(D, s);
+    rv = reg_v(D, s);
+  }
+}
+
 __global__ void __launch_bounds__(256) actvv_kernel(const double* __restrict__ eps, double s,
                                                     Sizes z, const double* __restrict__ M,
                                                     double* __restrict__ part) {
@@ -394,28 +423,37 @@ __global__ void __launch_bounds__(256) actvv_kernel(const double* __restrict__ e
 template <int NA>
 __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restrict__ eps, double s,
                                                           Sizes z, const double* __restrict__ M,
-                                                          double* __restrict__ part) {
+                                                          ActFact F, double* __restrict__ part) {
   constexpr int NA2 = NA * NA, NA4 = NA2 * NA2;
   __shared__ double red[8];
   const size_t nV2 = (size_t)z.nV * z.nV;
   const int ve = z.nC + z.nA;
-  double Ep[NA2];
+  double Ep[NA2], Bp[NA2];
+  bool fact = F.alpha != nullptr;
 #pragma unroll
-  for (int p = 0; p < NA2; ++p) Ep[p] = eps[z.nC + p / NA] + eps[z.nC + p % NA];
+  for (int p = 0; p < NA2; ++p) {
+    Ep[p] = eps[z.nC + p / NA] + eps[z.nC + p % NA];
+    Bp[p] = fact ? F.pinfo[4 * p + 1] : 0.0;
+    fact = fact && F.pinfo[4 * p + 2] != 0.0;
+  }
   double acc1[NA4], acc2[NA4];
 #pragma unroll
   for (int c = 0; c < NA4; ++c) acc1[c] = acc2[c] = 0.0;
   for (size_t k = (size_t)blockIdx.x * 256 + threadIdx.x; k < nV2; k += (size_t)gridDim.x * 256) {
     const int e = (int)(k / z.nV), f = (int)(k % z.nV);
     const double ef = eps[ve + e] + eps[ve + f];
+    const double tau = fact ? F.tau[(size_t)e * F.ld + f] : 0.0;
     double mr[NA2], mq[NA2], m[NA2];
 #pragma unroll
     for (int p = 0; p < NA2; ++p) m[p] = M[(size_t)p * nV2 + k];
 #pragma unroll
     for (int p = 0; p < NA2; ++p) {
       const double D = Ep[p] - ef;
-      mr[p] = m[p] * reg_v(D, s);
-      mq[p] = reg_t(D, s);
+      const double g = fact ? Bp[p] * F.alpha[(size_t)p * F.ld + e] * F.alpha[(size_t)p * F.ld + f] * tau : 0.0;
+      double rv, rt;
+      reg_pair(D, s, fact, g, rv, rt);
+      mr[p] = m[p] * rv;
+      mq[p] = rt;
     }
 #pragma unroll
     for (int p = 0; p < NA2; ++p)
@@ -448,7 +486,7 @@ constexpr int ACTVV_CH = 64;
 template <int NA>
 __global__ void __launch_bounds__(256) actvv_gen_kernel(const double* __restrict__ eps, double s,
                                                         Sizes z, const double* __restrict__ M,
-                                                        double* __restrict__ part) {
+                                                        ActFact F, double* __restrict__ part) {
   constexpr int NA2 = NA * NA, NA4 = NA2 * NA2;
   constexpr int PER = (NA4 + 255) / 256;  // (p,q) outputs per thread
   extern __shared__ double avs[];
@@ -458,6 +496,8 @@ __global__ void __launch_bounds__(256) actvv_gen_kernel(const double* __restrict
   __shared__ double red[8];
   const size_t nV2 = (size_t)z.nV * z.nV;
   const int ve = z.nC + z.nA;
+  bool fact = F.alpha != nullptr;
+  for (int p = 0; fact && p < NA2; ++p) fact = F.pinfo[4 * p + 2] != 0.0;
   double acc1[PER], acc2[PER];
 #pragma unroll
   for (int r = 0; r < PER; ++r) acc1[r] = acc2[r] = 0.0;
@@ -475,8 +515,12 @@ __global__ void __launch_bounds__(256) actvv_gen_kernel(const double* __restrict
         const double D = eps[z.nC + x] + eps[z.nC + u] - eps[ve + e] - eps[ve + f];
         const double m = M[(size_t)pidx * nV2 + k];
         const double mt = M[(size_t)(u * NA + x) * nV2 + k];
-        const double rt = reg_t(D, s);
-        a = m * reg_v(D, s);
+        const double g = fact ? F.pinfo[4 * pidx + 1] * F.alpha[(size_t)pidx * F.ld + e] *
+                                    F.alpha[(size_t)pidx * F.ld + f] * F.tau[(size_t)e * F.ld + f]
+                              : 0.0;
+        double rv, rt;
+        reg_pair(D, s, fact, g, rv, rt);
+        a = m * rv;
         b = m * rt;
         c = mt * rt;
       }
@@ -896,17 +940,20 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
   const int nA4 = z.nA * z.nA * z.nA * z.nA;
   {
     const size_t smg = (size_t)3 * z.nA * z.nA * ACTVV_CH * sizeof(double);
+    // factor tables of the split path (tc_rest.cu) when this call formed them
+    ActFact F{nullptr, nullptr, nullptr, 0};
+    if (ints_ready) rest_act_tables(p, &F.alpha, &F.pinfo, &F.tau, &F.ld);
 #define ACTVV_GEN(NA_)                                                                       \
   case NA_:                                                                                  \
     raise_smem_limit((const void*)actvv_gen_kernel<NA_>, smg);                               \
-    actvv_gen_kernel<NA_><<<ACTVV_BLOCKS, 256, smg, st>>>(eps, s, z, w.M, w.P12part);        \
+    actvv_gen_kernel<NA_><<<ACTVV_BLOCKS, 256, smg, st>>>(eps, s, z, w.M, F, w.P12part);     \
     break;
     switch (z.nA) {
       case 1:
-        actvv_small_kernel<1><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+        actvv_small_kernel<1><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
         break;
       case 2:
-        actvv_small_kernel<2><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, w.P12part);
+        actvv_small_kernel<2><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
         break;
       ACTVV_GEN(3) ACTVV_GEN(4) ACTVV_GEN(5) ACTVV_GEN(6) ACTVV_GEN(7) ACTVV_GEN(8)
       default: {

@@ -348,6 +348,59 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const doub
   return DSRG_OK;
 }
 
+dsrg_status_t dsrg_plan_time_ccvv(dsrg_plan_t* p, const double* B, const double* eps, double s,
+                                  int32_t reps, float* ms) {
+  dsrg_status_t st = check_common(p, B, eps, nullptr, nullptr, s, false);
+  if (st != DSRG_OK) return st;
+  if (!ms || reps < 1) return fail(p, DSRG_ERR_INVALID_ARG, "ms must not be NULL and reps >= 1");
+  if (p->prec == DSRG_PREC_FP64) return fail(p, DSRG_ERR_UNSUPPORTED, "FP64 plans have no split kernel");
+  cudaError_t e = split_stage(p, B, eps, s);
+  if (e == cudaSuccess) e = split_prepare_single(p, eps, s);
+  float warm = 0.f;
+  if (e == cudaSuccess) e = split_time_ccvv(p, 1, &warm);
+  if (e == cudaSuccess) e = split_time_ccvv(p, reps, ms);
+  if (e != cudaSuccess) return cuda_fail(p, e, "ccvv timing");
+  return dsrg_plan_sync(p);
+}
+
+dsrg_status_t dsrg_plan_autotune(dsrg_plan_t* p, const double* B, const double* eps, double s,
+                                 int32_t reps, int32_t* chosen) {
+  dsrg_status_t st = check_common(p, B, eps, nullptr, nullptr, s, false);
+  if (st != DSRG_OK) return st;
+  if (reps < 1) return fail(p, DSRG_ERR_INVALID_ARG, "reps must be >= 1");
+  if (chosen) *chosen = -1;
+  if (p->prec == DSRG_PREC_FP64) return DSRG_OK;
+  cudaError_t e = split_stage(p, B, eps, s);
+  if (e == cudaSuccess) e = split_prepare_single(p, eps, s);
+  float best_ms = 0.f;
+  int best = 0;
+  for (int c = 0; c < N_SPLIT_ORDERS && e == cudaSuccess; ++c) {
+    float warm = 0.f, ms = 0.f;
+    e = split_set_order(p, SPLIT_ORDERS[c]);
+    if (e == cudaSuccess) e = split_time_ccvv(p, 1, &warm);
+    if (e == cudaSuccess) e = split_time_ccvv(p, reps, &ms);
+    if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = SPLIT_ORDERS[c];
+    }
+  }
+  if (e == cudaSuccess) e = split_set_order(p, best);
+  if (e != cudaSuccess) return cuda_fail(p, e, "autotune");
+  st = dsrg_plan_sync(p);
+  if (st != DSRG_OK) return st;
+  if (chosen) *chosen = best;
+  return DSRG_OK;
+}
+
+int32_t dsrg_plan_item_order(const dsrg_plan_t* p) { return p ? split_order(p) : -1; }
+
+dsrg_status_t dsrg_plan_set_item_order(dsrg_plan_t* p, int32_t order) {
+  if (!p || order < 0 || (order >> 16) > 64) return DSRG_ERR_INVALID_ARG;
+  if (p->prec == DSRG_PREC_FP64) return DSRG_OK;
+  cudaError_t e = split_set_order(p, order);
+  return e == cudaSuccess ? DSRG_OK : cuda_fail(p, e, "item order");
+}
+
 dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const double* eps_host,
                                      const double* gamma1_host, const double* lambda2_host,
                                      double s, double* out_host) {

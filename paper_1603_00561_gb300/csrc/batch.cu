@@ -30,6 +30,7 @@ struct dsrg_batch {
   int4* d_items = nullptr;
   int* d_begin = nullptr;
   int grid = 0;
+  int order = 0;  // item order of the batched CCVV schedule
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;
@@ -172,7 +173,7 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
     for (int m = 0; m < nmol; ++m) {
       dsrg::split_fill_mol_desc(b->plans[m], row_base[m], mols.data() + m * mdb);
       const int kblocks = dsrg::split_plane_qpad(b->plans[m]->z) / dsrg::split_kb_elems(bf16);
-      dsrg::split_item_list(b->plans[m]->z, m, kblocks, items, cost);
+      dsrg::split_item_list(b->plans[m]->z, m, kblocks, items, cost, 0);
     }
     int nsm = 148, dev = 0;
     cudaGetDevice(&dev);
@@ -194,6 +195,98 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
   }
   *out = b;
   return DSRG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Rebuild the batched CCVV schedule for item order `order` (same item count).
+cudaError_t batch_set_order(dsrg_batch* b, int order) {
+  const bool bf16 = b->prec == DSRG_PREC_BF16X3;
+  std::vector<int4> items, sched;
+  std::vector<double> cost;
+  std::vector<int> begin;
+  for (int m = 0; m < b->nmol; ++m) {
+    const int kblocks = dsrg::split_plane_qpad(b->plans[m]->z) / dsrg::split_kb_elems(bf16);
+    dsrg::split_item_list(b->plans[m]->z, m, kblocks, items, cost, order & 0xffff);
+  }
+  dsrg::split_schedule(items, cost, b->grid, sched, begin);
+  cudaError_t e = cudaMemcpy(b->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) b->order = order;
+  return e;
+}
+}  // namespace
+
+extern "C" {
+
+dsrg_status_t dsrg_batch_autotune(dsrg_batch_t* b, const double* const* B, const double* const* eps,
+                                  const double* s, int32_t reps, int32_t* chosen) {
+  if (!b || !B || !eps || !s || reps < 1) return DSRG_ERR_INVALID_ARG;
+  if (chosen) *chosen = -1;
+  if (b->prec == DSRG_PREC_FP64) return DSRG_OK;
+  const int n = b->nmol;
+  for (int m = 0; m < n; ++m) {
+    if (!B[m] || !eps[m]) return bfail(b, DSRG_ERR_INVALID_ARG, "B and eps must not be NULL");
+    if (std::isnan(s[m]) || std::isinf(s[m]) || s[m] < 0.0)
+      return bfail(b, DSRG_ERR_INVALID_ARG, "bad s");
+  }
+  cudaStream_t st = b->user_stream;
+  dsrg_plan* p0 = b->plans[0];
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < n && e == cudaSuccess; ++m) {
+    b->plans[m]->stream = st;
+    e = dsrg::split_stage(b->plans[m], B[m], eps[m], s[m]);
+  }
+  if (e == cudaSuccess) e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best_ms = 0.f;
+  int best = 0;
+  const bool bf16 = b->prec == DSRG_PREC_BF16X3;
+  for (int c = 0; c < dsrg::N_SPLIT_ORDERS && e == cudaSuccess; ++c) {
+    e = batch_set_order(b, dsrg::SPLIT_ORDERS[c]);
+    // one untimed launch, then `reps` timed ones
+    for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
+      if (r == 1) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess)
+        e = dsrg::split_launch_ccvv(p0, b->map_hi, b->map_lo, b->d_mols, b->d_items, b->d_begin,
+                                    b->grid, bf16, b->order >> 16);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = dsrg::SPLIT_ORDERS[c];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = batch_set_order(b, best);
+  if (e != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+  for (dsrg_plan* p : b->plans) {
+    dsrg_status_t stt = dsrg_plan_sync(p);
+    if (stt != DSRG_OK) return bfail(b, stt, "a device-side wait ran out");
+  }
+  // the schedule arrays keep their addresses: a captured graph stays valid
+  if (chosen) *chosen = best;
+  return DSRG_OK;
+}
+
+int32_t dsrg_batch_item_order(const dsrg_batch_t* b) {
+  return (b && b->prec != DSRG_PREC_FP64) ? b->order : -1;
+}
+
+dsrg_status_t dsrg_batch_set_item_order(dsrg_batch_t* b, int32_t order) {
+  if (!b || order < 0 || (order >> 16) > 64) return DSRG_ERR_INVALID_ARG;
+  if (b->prec == DSRG_PREC_FP64) return DSRG_OK;
+  if (b->user_stream) cudaStreamSynchronize(b->user_stream);
+  cudaError_t e = batch_set_order(b, order);
+  return e == cudaSuccess ? DSRG_OK : bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
 }
 
 dsrg_status_t dsrg_batch_destroy(dsrg_batch_t* b) {
@@ -262,7 +355,7 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
       e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
       if (e == cudaSuccess)
         e = dsrg::split_launch_ccvv(p0, b->map_hi, b->map_lo, b->d_mols, b->d_items, b->d_begin,
-                                    b->grid, b->prec == DSRG_PREC_BF16X3);
+                                    b->grid, b->prec == DSRG_PREC_BF16X3, b->order >> 16);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
     for (int m = 0; m < n && st == DSRG_OK; ++m) {

@@ -173,9 +173,15 @@ cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols, int first, int n,
                              const double* const* eps, const double* s);
 cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,
                               const void* d_mols, const int4* d_items, const int* d_begin,
-                              int grid, bool bf16);
+                              int grid, bool bf16, int prefetch);
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
-                     std::vector<double>& cost);
+                     std::vector<double>& cost, int order);
+extern const int SPLIT_ORDERS[];
+extern const int N_SPLIT_ORDERS;
+cudaError_t split_set_order(dsrg_plan* p, int order);
+int split_order(const dsrg_plan* p);
+cudaError_t split_time_ccvv(dsrg_plan* p, int reps, float* ms);
+cudaError_t split_prepare_single(dsrg_plan* p, const double* eps, double s);
 void split_schedule(const std::vector<int4>& items, const std::vector<double>& cost, int ncta,
                     std::vector<int4>& out, std::vector<int>& begin);
 
@@ -197,6 +203,10 @@ void rest_free(dsrg_plan* p);
 cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
                               double s);
 void* split_plane_ptr(const dsrg_plan* p, bool hi);
+// Factor tables of exp(-s D^2) for the active pairs and the pair-independent
+// table, formed by launch_split_rest of the same call.
+void rest_act_tables(const dsrg_plan* p, const double** alpha, const double** pinfo,
+                     const double** tau, int* ld);
 int split_qld(const dsrg_plan* p);
 
 }  // namespace dsrg

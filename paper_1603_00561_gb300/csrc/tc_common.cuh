@@ -61,6 +61,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"((unsigned long long)map), "r"(su32(bar)), "r"(c0), "r"(c1)
       : "memory");
 }
+// Bring a box of the tensor into L2 ahead of its load (no shared-memory write).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   (unsigned long long)map),
+               "r"(c0), "r"(c1)
+               : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }

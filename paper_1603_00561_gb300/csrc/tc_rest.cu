@@ -307,17 +307,19 @@ __global__ void xx_gram_kernel(const double* __restrict__ Xq, int T, int Q, doub
   }
 }
 
-// Factors of exp(-s D_u^2), D_u = E_mu - e_a - e_b, E_mu = e_m + e_u (m core, u active).
+// Factors of exp(-s D_u^2), D_u = E_mu - e_a - e_b, E_mu = e_m + e_u, for the
+// pairs mu = (m core, u active) and then (x active, u active) (the active VV
+// sums of the active block).
 __global__ void cavv_tables_kernel(const double* __restrict__ eps, double s, Sizes z, int nVpad,
                                    double* __restrict__ alpha, double* __restrict__ pinfo,
                                    double* __restrict__ tau1) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int ve = z.nC + z.nA;
-  const int nmu = z.nC * z.nA;
+  const int nmu = (z.nC + z.nA) * z.nA;
   const size_t na = (size_t)nmu * nVpad, nt = (size_t)nVpad * nVpad;
   if (k < na) {
     const int mu = (int)(k / nVpad), b = (int)(k % nVpad);
-    const int m = mu / z.nA, u = mu % z.nA;
+    const int m = mu / z.nA, u = mu % z.nA;  // m < nC: core; m >= nC: active x = m - nC
     const double E = eps[m] + eps[z.nC + u];
     alpha[k] = (b < z.nV) ? exp(2.0 * s * E * eps[ve + b]) : 0.0;
     if (b == 0) {
@@ -413,13 +415,22 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
       if (e >= z.nV) break;
       const double tau = fact ? tau1[(size_t)e * nVpad + f] : 0.0;
       const double eef = sEe[r] + sEf[c];
-      double Rv[NA], Rt[NA], X[NA], Xt[NA];
+      double Rv[NA], Rt[NA];
+      float X[NA], Xt[NA];
+      bool far = fact;
 #pragma unroll
       for (int u = 0; u < NA; ++u) {
-        X[u] = (double)sX[(u * F2_T + r) * (F2_T + 1) + c];
-        Xt[u] = (double)sXt[(u * F2_T + r) * (F2_T + 1) + c];
+        X[u] = sX[(u * F2_T + r) * (F2_T + 1) + c];
+        Xt[u] = sXt[(u * F2_T + r) * (F2_T + 1) + c];
         const double D = sE[u] - eef;
-        if (fact && fabs(D) >= 0.25) {
+        far = far && fabs(D) >= 0.25;
+      }
+      if (far) {
+        // every D_u away from 0: FP64 regulators from the factor tables, the
+        // exchange combination Q_uv = X_u (2 X_v - Xt_v) [+ mirror] in FP32
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const double D = sE[u] - eef;
           const double g = sBeta[u] * sAe[u][r] * sAf[u][c] * tau;
           float r0f;
           asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
@@ -428,25 +439,44 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
           const double R0 = fma(-g, r0, r0);
           Rt[u] = fma(R0, en, R0);
           Rv[u] = 1.0 + g;
-        } else {
+        }
+        double t = 0.0;
+#pragma unroll
+        for (int v = 0; v < NA; ++v) {
+          const float dv = 2.0f * X[v] - Xt[v], dtv = 2.0f * Xt[v] - X[v];
+          double cv = 0.0;
+#pragma unroll
+          for (int u = 0; u < NA; ++u) {
+            const float q = mirror ? fmaf(X[u], dv, Xt[u] * dtv) : X[u] * dv;
+            cv = fma(sG[u * NA + v] * Rv[u], (double)q, cv);
+          }
+          t = fma(cv, Rt[v], t);
+        }
+        acc += t;
+      } else {
+        // a D_u near 0 (or a pair whose factors could overflow): expm1 regulators
+        // and the exchange combination in FP64
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const double D = sE[u] - eef;
           Rt[u] = reg_t(D, s);
           Rv[u] = reg_v(D, s);
         }
-      }
-      double t1 = 0.0, t2 = 0.0;
+        double t1 = 0.0, t2 = 0.0;
 #pragma unroll
-      for (int v = 0; v < NA; ++v) {
-        double c1 = 0.0, c2 = 0.0;
+        for (int v = 0; v < NA; ++v) {
+          double c1 = 0.0, c2 = 0.0;
 #pragma unroll
-        for (int u = 0; u < NA; ++u) {
-          const double w = sG[u * NA + v] * Rv[u];
-          c1 = fma(w, X[u], c1);
-          c2 = fma(w, Xt[u], c2);
+          for (int u = 0; u < NA; ++u) {
+            const double w = sG[u * NA + v] * Rv[u];
+            c1 = fma(w, (double)X[u], c1);
+            c2 = fma(w, (double)Xt[u], c2);
+          }
+          t1 = fma(c1, (2.0 * (double)X[v] - (double)Xt[v]) * Rt[v], t1);
+          t2 = fma(c2, (2.0 * (double)Xt[v] - (double)X[v]) * Rt[v], t2);
         }
-        t1 = fma(c1, (2.0 * X[v] - Xt[v]) * Rt[v], t1);
-        t2 = fma(c2, (2.0 * Xt[v] - X[v]) * Rt[v], t2);
+        acc += mirror ? (t1 + t2) : t1;
       }
-      acc += mirror ? (t1 + t2) : t1;
     }
   }
   const double tot = block_sum<256>(acc, red);
@@ -624,8 +654,8 @@ bool rest_alloc(dsrg_plan* p, float* shared_y) {
     ok = plan_alloc(p, (void**)&st->Y, rest_y_bytes(z));
   ok = ok && plan_alloc(p, (void**)&st->Xq, (size_t)T * z.Q * 8) &&
        plan_alloc(p, (void**)&st->Gxx, (size_t)T * T * 8) &&
-       plan_alloc(p, (void**)&st->alpha, (size_t)z.nC * z.nA * st->nVpad * 8) &&
-       plan_alloc(p, (void**)&st->pinfo, (size_t)z.nC * z.nA * 4 * 8) &&
+       plan_alloc(p, (void**)&st->alpha, (size_t)z.nH * z.nA * st->nVpad * 8) &&
+       plan_alloc(p, (void**)&st->pinfo, (size_t)z.nH * z.nA * 4 * 8) &&
        plan_alloc(p, (void**)&st->tau1, (size_t)st->nVpad * st->nVpad * 8) &&
        plan_alloc(p, (void**)&st->d_tp, (size_t)st->n_tp * sizeof(int2));
   if (!ok) return false;
@@ -635,6 +665,17 @@ bool rest_alloc(dsrg_plan* p, float* shared_y) {
     for (int B = A; B < nt; ++B) tp.push_back(make_int2(A, B));
   return cudaMemcpy(st->d_tp, tp.data(), tp.size() * sizeof(int2), cudaMemcpyHostToDevice) ==
          cudaSuccess;
+}
+
+void rest_act_tables(const dsrg_plan* p, const double** alpha, const double** pinfo,
+                     const double** tau, int* ld) {
+  const RestState* st = p->rest;
+  if (!st) return;
+  const size_t off = (size_t)p->z.nC * p->z.nA;  // the (x, u) pairs follow the (m, u) pairs
+  *alpha = st->alpha + off * st->nVpad;
+  *pinfo = st->pinfo + off * 4;
+  *tau = st->tau1;
+  *ld = st->nVpad;
 }
 
 void rest_free(dsrg_plan* p) {
@@ -686,7 +727,7 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     DSRG_LAUNCH_CHECK(p);
   }
   {
-    const size_t n = (size_t)z.nC * z.nA * st->nVpad + (size_t)st->nVpad * st->nVpad;
+    const size_t n = (size_t)z.nH * z.nA * st->nVpad + (size_t)st->nVpad * st->nVpad;
     cavv_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(eps, s, z, st->nVpad,
                                                                       st->alpha, st->pinfo, st->tau1);
     DSRG_LAUNCH_CHECK(p);

@@ -61,6 +61,7 @@ struct SplitWs {
   void* d_mol = nullptr;    // device MolDesc of this molecule
   int4* d_items = nullptr;  // single-molecule schedule
   int* d_begin = nullptr;
+  int order = 0;            // item order of that schedule (split_item_list)
 };
 
 // One molecule of a (possibly batched) CCVV launch.
@@ -83,6 +84,7 @@ struct SplitArgs {
   const int4* items;
   const int* cta_begin;
   int* status;
+  int prefetch;  // K stages ahead to prefetch into L2 (0: off)
 };
 
 // Operand slots of one stage: 0 = rows (i, A), 1 = (j, B), 2 = (j, A), 3 = (i, B).
@@ -194,10 +196,16 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      constexpr int KE = KB_BYTES / (BF16 ? 2 : 4);
       for (int idx = it0; ok && idx < it1; ++idx) {
         const MolDesc* md;
         const ItemPlan ip = plan_item(a, idx, &md);
         const int kblocks = md->kblocks, row0 = md->row0, nVpad = md->nVpad;
+        // the next item of this CTA, for prefetches that run past this one
+        const MolDesc* mdn = md;
+        ItemPlan ipn = ip;
+        const bool has_next = idx + 1 < it1;
+        if (has_next) ipn = plan_item(a, idx + 1, &mdn);
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.status)) {
             ok = false;
@@ -205,12 +213,31 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           }
           uint8_t* st = tiles + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], (uint32_t)(ip.nload * 2 * SLOT_BYTES));
-          const int kq = (kblocks - 1 - kb) * (KB_BYTES / (BF16 ? 2 : 4));
+          const int kq = (kblocks - 1 - kb) * KE;
           for (int l = 0; l < ip.nload; ++l) {
             const int sl = ip.load[l];
             const int row = row0 + slot_row(ip, sl, nVpad);
             tma_load_2d(st + (sl * 2 + 0) * SLOT_BYTES, &map_hi, &full[stage], kq, row);
             tma_load_2d(st + (sl * 2 + 1) * SLOT_BYTES, &map_lo, &full[stage], kq, row);
+          }
+          if (a.prefetch > 0) {
+            // L2 prefetch of the stage `prefetch` ahead (in this item or the next)
+            const int kf = kb + a.prefetch;
+            if (kf < kblocks) {
+              const int kqf = (kblocks - 1 - kf) * KE;
+              for (int l = 0; l < ip.nload; ++l) {
+                const int row = row0 + slot_row(ip, ip.load[l], nVpad);
+                tma_prefetch_2d(&map_hi, kqf, row);
+                tma_prefetch_2d(&map_lo, kqf, row);
+              }
+            } else if (has_next && kf - kblocks < mdn->kblocks) {
+              const int kqf = (mdn->kblocks - 1 - (kf - kblocks)) * KE;
+              for (int l = 0; l < ipn.nload; ++l) {
+                const int row = mdn->row0 + slot_row(ipn, ipn.load[l], mdn->nVpad);
+                tma_prefetch_2d(&map_hi, kqf, row);
+                tma_prefetch_2d(&map_lo, kqf, row);
+              }
+            }
           }
           if (++stage == STAGES) {
             stage = 0;
@@ -436,31 +463,59 @@ __device__ __forceinline__ float tf32_rne(float x) {
   return __uint_as_float(u);
 }
 
+// 64 x 64 tiles: coalesced 8-byte reads along the particle index, then each
+// thread splits 16 consecutive Q of one row and writes them as 16-byte stores.
 template <bool BF16>
-__global__ void split_planes_kernel(const double* __restrict__ B, Sizes z, int nVpad, int Qld,
-                                    void* __restrict__ hi, void* __restrict__ lo) {
-  __shared__ double t[32][33];
-  const int q0 = blockIdx.x * 32, a0 = blockIdx.y * 32, h = blockIdx.z;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    const int q = q0 + r, a = a0 + tx;
-    t[r][tx] = (q < z.Q && a < z.nV) ? B[bidx(z, q, h, z.nA + a)] : 0.0;
+__global__ void __launch_bounds__(256) split_planes_kernel(const double* __restrict__ B, Sizes z,
+                                                           int nVpad, int Qld,
+                                                           void* __restrict__ hi,
+                                                           void* __restrict__ lo) {
+  __shared__ double t[64][65];
+  const int q0 = blockIdx.x * 64, a0 = blockIdx.y * 64, h = blockIdx.z;
+  for (int k = threadIdx.x; k < 64 * 64; k += 256) {
+    const int r = k >> 6, c = k & 63;
+    const int q = q0 + r, a = a0 + c;
+    t[r][c] = (q < z.Q && a < z.nV) ? B[bidx(z, q, h, z.nA + a)] : 0.0;
   }
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int a = a0 + r, q = q0 + tx;
-    const double x = t[tx][r];
-    const size_t o = ((size_t)h * nVpad + a) * Qld + q;
-    if (BF16) {
-      const __nv_bfloat16 xh = __float2bfloat16_rn((float)x);
-      const __nv_bfloat16 xl = __float2bfloat16_rn((float)(x - (double)__bfloat162float(xh)));
-      ((__nv_bfloat16*)hi)[o] = xh;
-      ((__nv_bfloat16*)lo)[o] = xl;
-    } else {
-      const float xh = tf32_rne((float)x);
-      const float xl = tf32_rne((float)(x - (double)xh));
-      ((float*)hi)[o] = xh;
-      ((float*)lo)[o] = xl;
+  const int ar = threadIdx.x >> 2, qq = (threadIdx.x & 3) * 16;
+  const size_t o = ((size_t)h * nVpad + a0 + ar) * Qld + q0 + qq;
+  if (BF16) {
+    uint32_t ph[8], pl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t wh = 0, wl = 0;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double x = t[qq + 2 * j + k][ar];
+        const __nv_bfloat16 xh = __float2bfloat16_rn((float)x);
+        const __nv_bfloat16 xl = __float2bfloat16_rn((float)(x - (double)__bfloat162float(xh)));
+        wh |= (uint32_t)__bfloat16_as_ushort(xh) << (16 * k);
+        wl |= (uint32_t)__bfloat16_as_ushort(xl) << (16 * k);
+      }
+      ph[j] = wh;
+      pl[j] = wl;
+    }
+    uint4* dh = (uint4*)((__nv_bfloat16*)hi + o);
+    uint4* dl = (uint4*)((__nv_bfloat16*)lo + o);
+    dh[0] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    dh[1] = make_uint4(ph[4], ph[5], ph[6], ph[7]);
+    dl[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    dl[1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
+  } else {
+    float4* dh = (float4*)((float*)hi + o);
+    float4* dl = (float4*)((float*)lo + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float vh[4], vl[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double x = t[qq + 4 * j + k][ar];
+        vh[k] = tf32_rne((float)x);
+        vl[k] = tf32_rne((float)(x - (double)vh[k]));
+      }
+      dh[j] = make_float4(vh[0], vh[1], vh[2], vh[3]);
+      dl[j] = make_float4(vl[0], vl[1], vl[2], vl[3]);
     }
   }
 }
@@ -599,18 +654,57 @@ void split_schedule(const std::vector<int4>& items, const std::vector<double>& c
   begin[ncta] = (int)out.size();
 }
 
+// Work items of one molecule in the order given by `order` (the item's slot,
+// which indexes its partial sum, is the same in every order):
+//   0           pair-major: (i, j) then tile pairs (A, B)
+//   2G + 0      core orbitals in blocks of G; per block pair (I <= J): tile
+//               pairs outer, the pairs of the block inner
+//   2G + 1      the same blocks; pairs outer, tile pairs inner
+// Consecutive items run at the same time on different SMs, so the order sets
+// which operand tiles share the L2 at any moment.
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
-                     std::vector<double>& cost) {
-  const int nT = (z.nV + TT - 1) / TT;
-  int slot = 0;
-  for (int i = 0; i < z.nC; ++i)
-    for (int j = i; j < z.nC; ++j)
-      for (int A = 0; A < nT; ++A)
-        for (int B = A; B < nT; ++B) {
-          items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, slot++));
-          cost.push_back((double)kblocks * (i == j ? 1.0 : 2.0) + 24.0);
-        }
+                     std::vector<double>& cost, int order) {
+  const int nT = (z.nV + TT - 1) / TT, nC = z.nC;
+  const int n_tp = nT * (nT + 1) / 2;
+  auto pair_index = [&](int i, int j) { return i * nC - i * (i - 1) / 2 + (j - i); };
+  auto tp_index = [&](int A, int B) { return A * nT - A * (A - 1) / 2 + (B - A); };
+  auto push = [&](int i, int j, int A, int B) {
+    items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, pair_index(i, j) * n_tp + tp_index(A, B)));
+    cost.push_back((double)kblocks * (i == j ? 1.0 : 2.0) + 24.0);
+  };
+  const int G = order >> 1;
+  if (G <= 0) {
+    for (int i = 0; i < nC; ++i)
+      for (int j = i; j < nC; ++j)
+        for (int A = 0; A < nT; ++A)
+          for (int B = A; B < nT; ++B) push(i, j, A, B);
+    return;
+  }
+  const bool pairs_outer = (order & 1) != 0;
+  for (int I0 = 0; I0 < nC; I0 += G)
+    for (int J0 = I0; J0 < nC; J0 += G) {
+      std::vector<int2> pr;
+      for (int i = I0; i < I0 + G && i < nC; ++i)
+        for (int j = (J0 > i ? J0 : i); j < J0 + G && j < nC; ++j) pr.push_back(make_int2(i, j));
+      if (pairs_outer) {
+        for (const int2& ij : pr)
+          for (int A = 0; A < nT; ++A)
+            for (int B = A; B < nT; ++B) push(ij.x, ij.y, A, B);
+      } else {
+        for (int A = 0; A < nT; ++A)
+          for (int B = A; B < nT; ++B)
+            for (const int2& ij : pr) push(ij.x, ij.y, A, B);
+      }
+    }
 }
+
+// Schedule codes the autotuner tries: item order (low 16 bits, pair-major
+// first) and L2 prefetch distance in K stages (bits 16 and up).
+#define DSRG_ORDERS(PF) (PF << 16), (PF << 16) | (2 << 1), (PF << 16) | (4 << 1), (PF << 16) | (8 << 1), \
+    (PF << 16) | (4 << 1) | 1, (PF << 16) | (8 << 1) | 1, (PF << 16) | (64 << 1)
+const int SPLIT_ORDERS[] = {DSRG_ORDERS(0), DSRG_ORDERS(4), DSRG_ORDERS(12)};
+#undef DSRG_ORDERS
+const int N_SPLIT_ORDERS = sizeof(SPLIT_ORDERS) / sizeof(SPLIT_ORDERS[0]);
 
 bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
                     const CUtensorMap* shared_hi, const CUtensorMap* shared_lo) {
@@ -670,18 +764,59 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
   std::vector<int4> items, sched;
   std::vector<double> cost;
   std::vector<int> begin;
-  split_item_list(z, 0, md.kblocks, items, cost);
+  split_item_list(z, 0, md.kblocks, items, cost, 0);
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
   w->grid = (int)items.size() < nsm ? (int)items.size() : nsm;
-  split_schedule(items, cost, w->grid, sched, begin);
-  ok = plan_alloc(p, (void**)&w->d_items, sched.size() * sizeof(int4)) &&
-       plan_alloc(p, (void**)&w->d_begin, begin.size() * sizeof(int));
+  ok = plan_alloc(p, (void**)&w->d_items, items.size() * sizeof(int4)) &&
+       plan_alloc(p, (void**)&w->d_begin, (w->grid + 1) * sizeof(int));
   if (!ok) return false;
-  return cudaMemcpy(w->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice) ==
-             cudaSuccess &&
-         cudaMemcpy(w->d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice) ==
-             cudaSuccess;
+  return split_set_order(p, 0) == cudaSuccess;
+}
+
+// Rebuild the single-molecule schedule for item order `order`.
+cudaError_t split_set_order(dsrg_plan* p, int order) {
+  SplitWs* w = p->split;
+  std::vector<int4> items, sched;
+  std::vector<double> cost;
+  std::vector<int> begin;
+  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, order & 0xffff);
+  split_schedule(items, cost, w->grid, sched, begin);
+  cudaError_t e = cudaMemcpy(w->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(w->d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) w->order = order;
+  return e;
+}
+
+int split_order(const dsrg_plan* p) { return p->split ? p->split->order : -1; }
+
+// Average duration of the CCVV kernel alone (planes and tables staged by the
+// caller), `reps` launches between two events on the plan's stream.
+cudaError_t split_time_ccvv(dsrg_plan* p, int reps, float* ms) {
+  SplitWs* w = p->split;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  const bool bf16 = p->prec == DSRG_PREC_BF16X3;
+  e = cudaEventRecord(e0, p->stream);
+  for (int r = 0; e == cudaSuccess && r < reps; ++r)
+    e = split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, w->d_items, w->d_begin, w->grid, bf16,
+                          w->order >> 16);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / (float)(reps > 0 ? reps : 1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
 }
 
 bool split_alloc(dsrg_plan* p) {
@@ -711,11 +846,11 @@ cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double
   const Sizes& z = p->z;
   const bool bf16 = p->prec == DSRG_PREC_BF16X3;
   {
-    dim3 grid(w->Qpad / 32, w->nVpad / 32, z.nH), block(32, 8);
+    dim3 grid(w->Qpad / 64, w->nVpad / 64, z.nH);
     if (bf16)
-      split_planes_kernel<true><<<grid, block, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
+      split_planes_kernel<true><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
     else
-      split_planes_kernel<false><<<grid, block, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
+      split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
     DSRG_LAUNCH_CHECK(p);
   }
   {
@@ -770,12 +905,13 @@ cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols_v, int first, int n,
 
 cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,
                               const void* d_mols, const int4* d_items, const int* d_begin,
-                              int grid, bool bf16) {
+                              int grid, bool bf16, int prefetch) {
   SplitArgs a;
   a.mols = (const MolDesc*)d_mols;
   a.items = d_items;
   a.cta_begin = d_begin;
   a.status = p->d_status;
+  a.prefetch = prefetch;
   const size_t sm = split_smem_bytes();
   if (bf16) {
     raise_smem_limit((const void*)ccvv_split_kernel<true>, sm);
@@ -788,13 +924,18 @@ cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtenso
   return cudaSuccess;
 }
 
+// Per-call inputs (eps, s) of the single-molecule descriptor.
+cudaError_t split_prepare_single(dsrg_plan* p, const double* eps, double s) {
+  return split_set_inputs(p, p->split->d_mol, 0, 1, &eps, &s);
+}
+
 cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, double s) {
   SplitWs* w = p->split;
   cudaError_t e = split_stage(p, B, eps, s);
   if (e != cudaSuccess) return e;
-  if ((e = split_set_inputs(p, w->d_mol, 0, 1, &eps, &s)) != cudaSuccess) return e;
+  if ((e = split_prepare_single(p, eps, s)) != cudaSuccess) return e;
   return split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, w->d_items,
-                           w->d_begin, w->grid, p->prec == DSRG_PREC_BF16X3);
+                           w->d_begin, w->grid, p->prec == DSRG_PREC_BF16X3, w->order >> 16);
 }
 
 }  // namespace dsrg
