@@ -38,7 +38,22 @@ NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # DRAM bytes (read + write) per launch of the CCVV kernel from one ncu capture,
 # keyed by (workload, precision, item order); summaries under profiles/. Any
 # other combination, or a kernel changed since the capture, reports null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("naphthyne-v5z-1240", "bf16x3", 0): 10082152576,
+    ("naphthyne-v5z-1240", "bf16x3", 4): 12461248512,
+    ("naphthyne-v5z-1240", "bf16x3", 8): 18429093504,
+    ("naphthyne-v5z-1240", "bf16x3", 16): 19263530688,
+    ("naphthyne-v5z-1240", "bf16x3", 9): 9886302272,
+    ("naphthyne-v5z-1240", "bf16x3", 17): 10701434432,
+    ("naphthyne-v5z-1240", "bf16x3", 128): 17446319936,
+    ("naphthyne-v5z-1240", "bf16x3", 262144): 41468712704,
+    ("naphthyne-v5z-1240", "bf16x3", 262148): 46652614592,
+    ("naphthyne-v5z-1240", "bf16x3", 262152): 54084047104,
+    ("naphthyne-v5z-1240", "bf16x3", 262160): 55165200256,
+    ("naphthyne-v5z-1240", "bf16x3", 262153): 49783528960,
+    ("naphthyne-v5z-1240", "bf16x3", 262161): 45613238528,
+    ("naphthyne-v5z-1240", "bf16x3", 262272): 37016173824,
+}
 
 
 def ccvv_flops(nC, nV, Q):
@@ -275,6 +290,10 @@ def main():
                     help="also time the gradient at the cc-pVTZ size (FP64 and split)")
     ap.add_argument("--with-batch", type=int, default=0, metavar="NMOL",
                     help="also time a batch of NMOL uneven molecules vs one-by-one FP64 plans")
+    ap.add_argument("--item-order", type=int, default=None, metavar="CODE",
+                    help="fixed CCVV schedule code instead of autotuning it")
+    ap.add_argument("--schedule-sweep", action="store_true",
+                    help="time the CCVV kernel under every candidate schedule code and exit")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -307,8 +326,25 @@ def main():
     B, eps, g, l = pk.to_device(p)
     out = torch.empty(5, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    # schedule autotuning of the CCVV launch (setup, not timed): item orders timed on these inputs
-    item_order = plan.autotune(B, eps, p.s, reps=2) if prec != "fp64" else None
+    if args.schedule_sweep:
+        sweep = {}
+        for pf in (0, 4):
+            for o in (0, 2 << 1, 4 << 1, 8 << 1, (4 << 1) | 1, (8 << 1) | 1, 64 << 1):
+                plan.item_order = (pf << 16) | o
+                sweep[(pf << 16) | o] = plan.time_ccvv(B, eps, p.s, reps=3)
+        if rank == 0:
+            print(json.dumps({"schedule_sweep_ccvv_ms": sweep, "workload": args.workload,
+                              "precision": prec}), flush=True)
+        plan.close()
+        return
+    # schedule of the CCVV launch (setup, not timed): autotuned on these inputs, or fixed
+    if prec == "fp64":
+        item_order = None
+    elif args.item_order is not None:
+        plan.item_order = args.item_order
+        item_order = args.item_order
+    else:
+        item_order = plan.autotune(B, eps, p.s, reps=2)
 
     def step():
         plan.energy(B, eps, g, l, p.s, out=out)
