@@ -270,15 +270,17 @@ __global__ void xrows_kernel(const double* __restrict__ B, Sizes z, long long xr
   const double v = B[bidx(z, q, h, x)];
   Xq[k] = v;
   const size_t o = (size_t)(xrow0 + t) * Qld + q;
+  // the same split of fl32(B) as the main plane rows
+  const float vf = (float)v;
   if (BF16) {
-    const __nv_bfloat16 vh = __float2bfloat16_rn((float)v);
+    const __nv_bfloat16 vh = __float2bfloat16_rn(vf);
     ((__nv_bfloat16*)hi)[o] = vh;
-    ((__nv_bfloat16*)lo)[o] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(vh)));
+    ((__nv_bfloat16*)lo)[o] = __float2bfloat16_rn(vf - __bfloat162float(vh));
   } else {
-    uint32_t u = __float_as_uint((float)v);
+    uint32_t u = __float_as_uint(vf);
     if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0xfffu + ((u >> 13) & 1u)) & 0xffffe000u;
     const float vh = __uint_as_float(u);
-    uint32_t w = __float_as_uint((float)(v - (double)vh));
+    uint32_t w = __float_as_uint(vf - vh);
     if ((w & 0x7f800000u) != 0x7f800000u) w = (w + 0xfffu + ((w >> 13) & 1u)) & 0xffffe000u;
     ((float*)hi)[o] = vh;
     ((float*)lo)[o] = __uint_as_float(w);
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
   float* sXt = sX + NA * F2_T * (F2_T + 1);     // [NA][32][33]   X_u[f,e]
   __shared__ double sAe[NA][F2_T], sAf[NA][F2_T], sEe[F2_T], sEf[F2_T], sG[NA * NA];
   __shared__ double sE[NA], sBeta[NA];
-  __shared__ int sFact;
+  __shared__ int sFact, sFar;
   __shared__ double red[8];
   const int m = blockIdx.x / n_tp;
   const int2 ab = tps[blockIdx.x % n_tp];
@@ -404,8 +406,26 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
     sFact = fact;
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    // every D_u of the tile pair so far from 0 that exp(-s D_u^2) < 2^-63:
+    // then Rv = 1 and Rt = 1/D_u to FP64 precision
+    double elo = 1e300, flo = 1e300, ehi = -1e300, fhi = -1e300;
+    for (int t = 0; t < F2_T; ++t) {
+      if (E0 + t < z.nV) elo = fmin(elo, sEe[t]), ehi = fmax(ehi, sEe[t]);
+      if (F0 + t < z.nV) flo = fmin(flo, sEf[t]), fhi = fmax(fhi, sEf[t]);
+    }
+    int far = 1;
+    for (int u = 0; u < NA; ++u) {
+      const double dhi = sE[u] - elo - flo, dlo = sE[u] - ehi - fhi;
+      const double dn = dhi <= 0.0 ? dhi : (dlo >= 0.0 ? dlo : 0.0);
+      far = far && (dhi <= -0.25 || dlo >= 0.25) && s * dn * dn > 44.0;
+    }
+    sFar = far;
+  }
+  __syncthreads();
   const bool mirror = ab.x < ab.y;
   const bool fact = sFact != 0;
+  const bool tile_far = sFar != 0;
   const int c = threadIdx.x & 31;
   const int f = F0 + c;
   double acc = 0.0;
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
     for (int r = threadIdx.x >> 5; r < F2_T; r += 8) {
       const int e = E0 + r;
       if (e >= z.nV) break;
-      const double tau = fact ? tau1[(size_t)e * nVpad + f] : 0.0;
+      const double tau = (fact && !tile_far) ? tau1[(size_t)e * nVpad + f] : 0.0;
       const double eef = sEe[r] + sEf[c];
       double Rv[NA], Rt[NA];
       float X[NA], Xt[NA];
@@ -425,13 +445,14 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
         const double D = sE[u] - eef;
         far = far && fabs(D) >= 0.25;
       }
-      if (far) {
-        // every D_u away from 0: FP64 regulators from the factor tables, the
+      if (far || tile_far) {
+        // every D_u away from 0: FP64 regulators (from the factor tables, or
+        // Rv = 1, Rt = 1/D where exp(-s D^2) is below FP64 precision), the
         // exchange combination Q_uv = X_u (2 X_v - Xt_v) [+ mirror] in FP32
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
           const double D = sE[u] - eef;
-          const double g = sBeta[u] * sAe[u][r] * sAf[u][c] * tau;
+          const double g = tile_far ? 0.0 : sBeta[u] * sAe[u][r] * sAf[u][c] * tau;
           float r0f;
           asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
           const double r0 = (double)r0f;

@@ -357,6 +357,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       const double dmax = E - md->trange[2 * ip.A] - md->trange[2 * ip.Bt];
       const double dmin = E - md->trange[2 * ip.A + 1] - md->trange[2 * ip.Bt + 1];
       const bool fast = (pi[2] != 0.0) && (dmax <= -0.25 || dmin >= 0.25);
+      // every |D| of the tile pair so large that exp(-2 s D^2) < 2^-63: then
+      // (1 - exp(-2 s D^2)) / D equals 1/D to FP64 precision
+      const double dnear = dmax <= 0.0 ? dmax : (dmin >= 0.0 ? dmin : 0.0);
+      const bool far = (dmax <= -0.25 || dmin >= 0.25) && 2.0 * md->s * dnear * dnear > 44.0;
       named_bar(1, 32 * EPI_WARPS);
       if (et < TT) {
         const int b = ip.Bt * TT + et;
@@ -389,7 +393,21 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           if (ip.two) tmem_ld16(ty + c0, yr);
           tmem_ld_wait();
           if (!rok) continue;
-          if (fast) {
+          if (far) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int cb = c0 + k;
+              if (cb >= cend) break;
+              const float xf = __uint_as_float(xr[k]);
+              const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+              const double D = ca - sEps[cb];
+              float r0f;
+              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
+              const double r0 = (double)r0f;
+              const double R = fma(r0, fma(-D, r0, 1.0), r0);   // 1/D, one Newton step
+              acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
+            }
+          } else if (fast) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
               const int cb = c0 + k;
@@ -465,6 +483,9 @@ __device__ __forceinline__ float tf32_rne(float x) {
 
 // 64 x 64 tiles: coalesced 8-byte reads along the particle index, then each
 // thread splits 16 consecutive Q of one row and writes them as 16-byte stores.
+// The split is of fl32(B): hi = rn(fl32(B)), lo = rn(fl32(B) - hi); the
+// difference from splitting B itself is below 2^-24 relative, under the
+// dropped lo*lo product.
 template <bool BF16>
 __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restrict__ B, Sizes z,
                                                            int nVpad, int Qld,
@@ -487,9 +508,11 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
       uint32_t wh = 0, wl = 0;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const double x = t[qq + 2 * j + k][ar];
-        const __nv_bfloat16 xh = __float2bfloat16_rn((float)x);
-        const __nv_bfloat16 xl = __float2bfloat16_rn((float)(x - (double)__bfloat162float(xh)));
+        // one FP64 operation per element (the FP64 pipe is the scarce one):
+        // xf = fl32(x); hi = bf16(xf); xf - hi is exact in FP32; lo = bf16(xf - hi)
+        const float xf = (float)t[qq + 2 * j + k][ar];
+        const __nv_bfloat16 xh = __float2bfloat16_rn(xf);
+        const __nv_bfloat16 xl = __float2bfloat16_rn(xf - __bfloat162float(xh));
         wh |= (uint32_t)__bfloat16_as_ushort(xh) << (16 * k);
         wl |= (uint32_t)__bfloat16_as_ushort(xl) << (16 * k);
       }
@@ -510,9 +533,9 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
       float vh[4], vl[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const double x = t[qq + 4 * j + k][ar];
-        vh[k] = tf32_rne((float)x);
-        vl[k] = tf32_rne((float)(x - (double)vh[k]));
+        const float xf = (float)t[qq + 4 * j + k][ar];
+        vh[k] = tf32_rne(xf);
+        vl[k] = tf32_rne(xf - vh[k]);  // exact in FP32
       }
       dh[j] = make_float4(vh[0], vh[1], vh[2], vh[3]);
       dl[j] = make_float4(vl[0], vl[1], vl[2], vl[3]);
