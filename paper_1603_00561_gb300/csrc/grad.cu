@@ -1,10 +1,15 @@
 // Adjoint of the DSRG-MRPT2 energy: dE_total/dB, dE_total/deps, dE_total/ds.
 //
-// All adjoint arithmetic is FP64 on CUDA cores. Pair quantities are recomputed
-// per core row rather than stored: for a fixed core orbital k the kernel forms
-// v^{kj} for every j tile by tile and keeps only W^{kj} = dE/dv^{kj}, which a
-// GEMM turns into dB. dB is assembled with one thread per element in every
-// kernel (fixed order, bit-reproducible); deps and ds use FP64 atomics.
+// FP64 plans: all adjoint arithmetic is FP64 on CUDA cores. Split-precision
+// plans: the recomputed contractions over Q (v, X, Z) and the GEMMs that turn
+// the adjoints into dB run in FP32 on CUDA cores with round-to-nearest (the
+// truncating tensor-core accumulator would bias these long sums toward zero);
+// regulators, their derivatives and every epilogue stay FP64. Pair quantities
+// are recomputed per core row rather than stored: for a fixed core orbital k
+// the kernel forms v^{kj} for every j tile by tile and keeps only
+// W^{kj} = dE/dv^{kj}, which a GEMM turns into dB. dB is assembled with one
+// thread per element in every kernel (fixed order, bit-reproducible); deps and
+// ds use FP64 atomics.
 //
 // Derivatives (closed-shell spin-adapted forms of Table 2, Eqs. (12)-(15), (23)):
 //  F1: E = sum_{ij} sum_ab v_ab (2 v_ab - v_ba) R(D),  R = (1 - exp(-2 s D^2))/D
@@ -128,10 +133,98 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
   }
 }
 
+// The same contraction in FP32 (operands rounded to FP32, FP32 accumulation
+// with round-to-nearest), 128 x 128 tiles, 8 x 8 outputs per thread. Operand
+// tiles are read along whichever index is contiguous in memory.
+constexpr int SG_T = 128, SG_K = 16;
+
+__global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
+  __shared__ __align__(16) float sA[SG_K][SG_T + 4];
+  __shared__ __align__(16) float sB[SG_K][SG_T + 4];
+  const int i0 = blockIdx.y * SG_T, j0 = blockIdx.x * SG_T;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long long L = (long long)g.L1 * g.L2;
+  const bool a_kfast = g.a2 == 1 && g.L2 > 1, b_kfast = g.b2 == 1 && g.L2 > 1;
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  for (long long l0 = 0; l0 < L; l0 += SG_K) {
+    for (int e = threadIdx.x; e < SG_K * SG_T; e += 256) {
+      int ll, c;
+      if (a_kfast) {
+        ll = e % SG_K;
+        c = e / SG_K;
+      } else {
+        ll = e / SG_T;
+        c = e % SG_T;
+      }
+      const long long l = l0 + ll;
+      float v = 0.f;
+      if (l < L && i0 + c < g.M) {
+        const long long l1 = l / g.L2, l2 = l % g.L2;
+        v = (float)g.A[(long long)(i0 + c) * g.ai + l1 * g.a1 + l2 * g.a2];
+      }
+      sA[ll][c] = v;
+    }
+    for (int e = threadIdx.x; e < SG_K * SG_T; e += 256) {
+      int ll, c;
+      if (b_kfast) {
+        ll = e % SG_K;
+        c = e / SG_K;
+      } else {
+        ll = e / SG_T;
+        c = e % SG_T;
+      }
+      const long long l = l0 + ll;
+      float v = 0.f;
+      if (l < L && j0 + c < g.N) {
+        const long long l1 = l / g.L2, l2 = l % g.L2;
+        v = (float)g.Bm[l1 * g.b1 + l2 * g.b2 + (long long)(j0 + c) * g.bj];
+      }
+      sB[ll][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ll = 0; ll < SG_K; ++ll) {
+      const float4 a0 = *(const float4*)&sA[ll][ty * 8];
+      const float4 a1 = *(const float4*)&sA[ll][ty * 8 + 4];
+      const float4 b0 = *(const float4*)&sB[ll][tx * 8];
+      const float4 b1 = *(const float4*)&sB[ll][tx * 8 + 4];
+      const float ra[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float rb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ra[r], rb[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + ty * 8 + r;
+    if (i >= g.M) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = j0 + tx * 8 + c;
+      if (j >= g.N) continue;
+      double* p = g.C + (long long)i * g.ci + (long long)j * g.cj;
+      *p = g.accumulate ? fma(g.alpha, (double)acc[r][c], *p) : g.alpha * (double)acc[r][c];
+    }
+  }
+}
+
+// FP64 plans: FP64 GEMM; split-precision plans: FP32 GEMM.
 static cudaError_t gemm(dsrg_plan* p, const GemmArgs& g) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
-  gemm_fp64_kernel<<<grid, 256, 0, p->stream>>>(g);
+  if (p->prec == DSRG_PREC_FP64) {
+    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
+    gemm_fp64_kernel<<<grid, 256, 0, p->stream>>>(g);
+  } else {
+    dim3 grid((g.N + SG_T - 1) / SG_T, (g.M + SG_T - 1) / SG_T);
+    gemm_f32_kernel<<<grid, 256, 0, p->stream>>>(g);
+  }
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
@@ -142,13 +235,14 @@ static cudaError_t gemm(dsrg_plan* p, const GemmArgs& g) {
 // ---------------------------------------------------------------------------
 constexpr int GT = 64;
 
+template <typename T>
 __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict__ B,
                                                        const double* __restrict__ eps, double s,
                                                        Sizes z, int k, const int2* __restrict__ tps,
                                                        int n_tp, int nVp, double* __restrict__ Wk,
                                                        double* __restrict__ deps,
                                                        double* __restrict__ ds) {
-  __shared__ double sKA[16][GT], sJB[16][GT], sJA[16][GT], sKB[16][GT];
+  __shared__ T sKA[16][GT], sJB[16][GT], sJA[16][GT], sKB[16][GT];
   __shared__ double rowacc[GT], colacc[GT];
   __shared__ double red[8];
   const int j = blockIdx.x / n_tp;
@@ -160,26 +254,26 @@ __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict_
     rowacc[threadIdx.x] = 0.0;
     colacc[threadIdx.x] = 0.0;
   }
-  double x[4][4], y[4][4];
+  T x[4][4], y[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) x[r][c] = y[r][c] = 0.0;
+    for (int c = 0; c < 4; ++c) x[r][c] = y[r][c] = (T)0;
   for (int q0 = 0; q0 < z.Q; q0 += 16) {
     for (int e = threadIdx.x; e < 16 * GT; e += 256) {
       const int qq = e / GT, c = e % GT, q = q0 + qq;
       const bool qok = q < z.Q;
       const int a = a0 + c, b = b0 + c;
       const bool aok = qok && a < z.nV, bok = qok && b < z.nV;
-      sKA[qq][c] = aok ? B[bidx(z, q, k, pv + a)] : 0.0;
-      sJB[qq][c] = bok ? B[bidx(z, q, j, pv + b)] : 0.0;
-      sJA[qq][c] = aok ? B[bidx(z, q, j, pv + a)] : 0.0;
-      sKB[qq][c] = bok ? B[bidx(z, q, k, pv + b)] : 0.0;
+      sKA[qq][c] = aok ? (T)B[bidx(z, q, k, pv + a)] : (T)0;
+      sJB[qq][c] = bok ? (T)B[bidx(z, q, j, pv + b)] : (T)0;
+      sJA[qq][c] = aok ? (T)B[bidx(z, q, j, pv + a)] : (T)0;
+      sKB[qq][c] = bok ? (T)B[bidx(z, q, k, pv + b)] : (T)0;
     }
     __syncthreads();
 #pragma unroll 4
     for (int qq = 0; qq < 16; ++qq) {
-      double ra[4], rb[4], sa[4], sb[4];
+      T ra[4], rb[4], sa[4], sb[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         ra[r] = sKA[qq][ty * 4 + r];
@@ -212,7 +306,7 @@ __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict_
       if (b >= z.nV) continue;
       const double D = E - eps[ve + a] - eps[ve + b];
       const RegD R = rf1_d(D, s);
-      const double xv = x[r][c], yv = y[r][c];
+      const double xv = (double)x[r][c], yv = (double)y[r][c];
       Wk[((size_t)j * nVp + a) * nVp + b] = (4.0 * xv - 2.0 * yv) * R.v;
       if (mirror) Wk[((size_t)j * nVp + b) * nVp + a] = (4.0 * yv - 2.0 * xv) * R.v;
       const double q = fma(xv, xv - yv, yv * yv);
@@ -245,13 +339,13 @@ __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict_
 // ---------------------------------------------------------------------------
 // F2 adjoint: items (m, tile pair A<=B), 32 x 32 tiles; writes dX[m][u][e][f].
 // ---------------------------------------------------------------------------
-template <int NA>
+template <int NA, typename T>
 __global__ void __launch_bounds__(256) cavv_adj_kernel(
     const double* __restrict__ B, const double* __restrict__ eps, const double* __restrict__ G,
     double s, Sizes z, const int2* __restrict__ tps, int n_tp, int nVp, double* __restrict__ dX,
     double* __restrict__ deps, double* __restrict__ ds) {
-  __shared__ double sMA[8][32], sMB[8][32];
-  __shared__ double sUA[NA][8][32], sUB[NA][8][32];
+  __shared__ T sMA[8][32], sMB[8][32];
+  __shared__ T sUA[NA][8][32], sUB[NA][8][32];
   __shared__ double sG[NA][NA];
   __shared__ double rowacc[32], colacc[32], uacc[NA];
   __shared__ double red[8];
@@ -266,41 +360,49 @@ __global__ void __launch_bounds__(256) cavv_adj_kernel(
     colacc[threadIdx.x] = 0.0;
   }
   if (threadIdx.x < NA) uacc[threadIdx.x] = 0.0;
-  double X[NA][4], Xt[NA][4];
+  T Xa[NA][4], Xta[NA][4];
 #pragma unroll
   for (int u = 0; u < NA; ++u)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) X[u][r] = Xt[u][r] = 0.0;
+    for (int r = 0; r < 4; ++r) Xa[u][r] = Xta[u][r] = (T)0;
   for (int q0 = 0; q0 < z.Q; q0 += 8) {
     for (int e = threadIdx.x; e < 8 * 32; e += 256) {
       const int qq = e / 32, c = e % 32, q = q0 + qq;
       const bool qok = q < z.Q;
       const int a = a0 + c, b = b0 + c;
       const bool aok = qok && a < z.nV, bok = qok && b < z.nV;
-      sMA[qq][c] = aok ? B[bidx(z, q, m, pv + a)] : 0.0;
-      sMB[qq][c] = bok ? B[bidx(z, q, m, pv + b)] : 0.0;
+      sMA[qq][c] = aok ? (T)B[bidx(z, q, m, pv + a)] : (T)0;
+      sMB[qq][c] = bok ? (T)B[bidx(z, q, m, pv + b)] : (T)0;
 #pragma unroll
       for (int u = 0; u < NA; ++u) {
-        sUA[u][qq][c] = aok ? B[bidx(z, q, z.nC + u, pv + a)] : 0.0;
-        sUB[u][qq][c] = bok ? B[bidx(z, q, z.nC + u, pv + b)] : 0.0;
+        sUA[u][qq][c] = aok ? (T)B[bidx(z, q, z.nC + u, pv + a)] : (T)0;
+        sUB[u][qq][c] = bok ? (T)B[bidx(z, q, z.nC + u, pv + b)] : (T)0;
       }
     }
     __syncthreads();
 #pragma unroll
     for (int qq = 0; qq < 8; ++qq) {
-      const double mb = sMB[qq][tx];
+      const T mb = sMB[qq][tx];
 #pragma unroll
       for (int u = 0; u < NA; ++u) {
-        const double ub = sUB[u][qq][tx];
+        const T ub = sUB[u][qq][tx];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          X[u][r] = fma(sMA[qq][ty * 4 + r], ub, X[u][r]);
-          Xt[u][r] = fma(sUA[u][qq][ty * 4 + r], mb, Xt[u][r]);
+          Xa[u][r] = fma(sMA[qq][ty * 4 + r], ub, Xa[u][r]);
+          Xta[u][r] = fma(sUA[u][qq][ty * 4 + r], mb, Xta[u][r]);
         }
       }
     }
     __syncthreads();
   }
+  double X[NA][4], Xt[NA][4];
+#pragma unroll
+  for (int u = 0; u < NA; ++u)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      X[u][r] = (double)Xa[u][r];
+      Xt[u][r] = (double)Xta[u][r];
+    }
   const bool mirror = ab.x < ab.y;
   const int b = b0 + tx;
   double dm = 0.0, dss = 0.0, cacc = 0.0;
@@ -386,39 +488,40 @@ __global__ void __launch_bounds__(256) cavv_adj_kernel(
 // ---------------------------------------------------------------------------
 // F3 adjoint: one CTA per virtual e; writes dZ[w][m][n][e].
 // ---------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256) ccav_adj_kernel(
     const double* __restrict__ B, const double* __restrict__ eps, const double* __restrict__ G,
     double s, Sizes z, double* __restrict__ dZ, double* __restrict__ deps, double* __restrict__ ds) {
   extern __shared__ double smem[];
   const int nC = z.nC, nA = z.nA;
-  double* Z = smem;                    // [nA][nC][nC]
-  double* sBe = Z + nA * nC * nC;      // [8][nC]
-  double* sBu = sBe + 8 * nC;          // [8][nC][nA]
-  double* accm = sBu + 8 * nC * nA;    // [nC]  deps of core orbitals
+  double* accm = smem;                 // [nC]  deps of core orbitals
   double* accu = accm + nC;            // [nA]
+  T* Z = (T*)(accu + nA);              // [nA][nC][nC]
+  T* sBe = Z + nA * nC * nC;           // [8][nC]
+  T* sBu = sBe + 8 * nC;               // [8][nC][nA]
   __shared__ double red[8];
   const int e = blockIdx.x;
   const int nz = nA * nC * nC;
-  for (int k = threadIdx.x; k < nz; k += 256) Z[k] = 0.0;
+  for (int k = threadIdx.x; k < nz; k += 256) Z[k] = (T)0;
   for (int k = threadIdx.x; k < nC + nA; k += 256) accm[k] = 0.0;
   for (int q0 = 0; q0 < z.Q; q0 += 8) {
     __syncthreads();
     for (int k = threadIdx.x; k < 8 * nC * (1 + nA); k += 256) {
       const int qq = k / (nC * (1 + nA)), r = k % (nC * (1 + nA)), q = q0 + qq;
-      double v = 0.0;
+      T v = (T)0;
       if (r < nC) {
-        if (q < z.Q) v = B[bidx(z, q, r, nA + e)];
+        if (q < z.Q) v = (T)B[bidx(z, q, r, nA + e)];
         sBe[qq * nC + r] = v;
       } else {
         const int nu = r - nC, n = nu / nA, u = nu % nA;
-        if (q < z.Q) v = B[bidx(z, q, n, u)];
+        if (q < z.Q) v = (T)B[bidx(z, q, n, u)];
         sBu[(qq * nC + n) * nA + u] = v;
       }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nz; k += 256) {
       const int u = k / (nC * nC), mn = k % (nC * nC), m = mn / nC, n = mn % nC;
-      double acc = Z[k];
+      T acc = Z[k];
 #pragma unroll
       for (int qq = 0; qq < 8; ++qq) acc = fma(sBe[qq * nC + m], sBu[(qq * nC + n) * nA + u], acc);
       Z[k] = acc;
@@ -436,7 +539,7 @@ __global__ void __launch_bounds__(256) ccav_adj_kernel(
       const double D = base - eps[nC + u];
       Rv[u] = rv_d(D, s);
       Rt[u] = rt_d(D, s);
-      P[u] = 2.0 * Z[(u * nC + m) * nC + n] - Z[(u * nC + n) * nC + m];
+      P[u] = 2.0 * (double)Z[(u * nC + m) * nC + n] - (double)Z[(u * nC + n) * nC + m];
     }
     double gsum = 0.0;
     for (int w = 0; w < nA; ++w) {
@@ -446,9 +549,9 @@ __global__ void __launch_bounds__(256) ccav_adj_kernel(
         const double Huw = (u == w ? 2.0 : 0.0) - G[u * nA + w];
         s1 = fma(Hwu * Rt[u].v, P[u], s1);
         s2 = fma(Huw * Rv[u].v, P[u], s2);
-        cw = fma(Huw * Rv[u].v, Z[(u * nC + m) * nC + n], cw);
+        cw = fma(Huw * Rv[u].v, (double)Z[(u * nC + m) * nC + n], cw);
       }
-      const double zw = Z[(w * nC + m) * nC + n];
+      const double zw = (double)Z[(w * nC + m) * nC + n];
       dZ[(((size_t)w * nC + m) * nC + n) * z.nV + e] = Rv[w].v * s1 + Rt[w].v * s2;
       // dE/dD_w: y_wu Rv'_w Rt_u + y_vw Rv_v Rt'_w
       const double gD = zw * s1 * Rv[w].dD + cw * P[w] * Rt[w].dD;
@@ -1149,11 +1252,17 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   if ((e = cudaMemsetAsync(deps, 0, (size_t)z.n * 8, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ds, 0, 8, st)) != cudaSuccess) return e;
 
+  // FP64 plans recompute in FP64, split-precision plans in FP32 (round to nearest)
+  const bool fp64 = p->prec == DSRG_PREC_FP64;
   // ---- F1: per core row k, W^{kj} then dB[:, k, V] += 2 sum_j B_j W^{kj T}
   const int n_tp = p->n_tp_ccvv;  // 64-wide tile pairs of the FP64 work list
   for (int k = 0; k < z.nC; ++k) {
-    ccvv_adj_kernel<<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp, w->nVp, w->Wk,
-                                                 deps, ds);
+    if (fp64)
+      ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp, w->nVp,
+                                                           w->Wk, deps, ds);
+    else
+      ccvv_adj_kernel<float><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp, w->nVp,
+                                                          w->Wk, deps, ds);
     DSRG_LAUNCH_CHECK(p);
     const long long nVp = w->nVp;
     e = gemm(p, mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
@@ -1167,8 +1276,12 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   {
 #define CAVV_ADJ(NA_)                                                                            \
   case NA_:                                                                                      \
-    cavv_adj_kernel<NA_><<<z.nC * p->n_tp_cavv, 256, 0, st>>>(B, eps, G, s, z, p->d_tp_cavv,     \
-                                                              p->n_tp_cavv, z.nV, w->dX, deps, ds); \
+    if (fp64)                                                                                    \
+      cavv_adj_kernel<NA_, double><<<z.nC * p->n_tp_cavv, 256, 0, st>>>(                         \
+          B, eps, G, s, z, p->d_tp_cavv, p->n_tp_cavv, z.nV, w->dX, deps, ds);                   \
+    else                                                                                         \
+      cavv_adj_kernel<NA_, float><<<z.nC * p->n_tp_cavv, 256, 0, st>>>(                          \
+          B, eps, G, s, z, p->d_tp_cavv, p->n_tp_cavv, z.nV, w->dX, deps, ds);                   \
     break;
     switch (z.nA) {
       CAVV_ADJ(1) CAVV_ADJ(2) CAVV_ADJ(3) CAVV_ADJ(4) CAVV_ADJ(5) CAVV_ADJ(6) CAVV_ADJ(7) CAVV_ADJ(8)
@@ -1192,8 +1305,13 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   // ---- F3
   {
     const size_t sm = ccav_adj_smem(z);
-    raise_smem_limit((const void*)ccav_adj_kernel, sm);
-    ccav_adj_kernel<<<z.nV, 256, sm, st>>>(B, eps, G, s, z, w->dZ, deps, ds);
+    if (fp64) {
+      raise_smem_limit((const void*)ccav_adj_kernel<double>, sm);
+      ccav_adj_kernel<double><<<z.nV, 256, sm, st>>>(B, eps, G, s, z, w->dZ, deps, ds);
+    } else {
+      raise_smem_limit((const void*)ccav_adj_kernel<float>, sm);
+      ccav_adj_kernel<float><<<z.nV, 256, sm, st>>>(B, eps, G, s, z, w->dZ, deps, ds);
+    }
     DSRG_LAUNCH_CHECK(p);
     const long long nCV = (long long)z.nC * nV, nCCV = (long long)z.nC * nCV;
     for (int m = 0; m < z.nC; ++m) {

@@ -6,6 +6,13 @@ element, and (2) central finite differences of the GPU FP64 energy at the
 cc-pVTZ size on 200 random entries of B plus orbital energies and s, with the
 combined bound |g_fd - g| <= 1e-6 |g| + 10 eps_mach |E| / h (the second term is
 the rounding floor of a difference quotient of a number of size |E|).
+
+Split-precision plans compute the gradient's contractions over Q and its
+GEMMs in FP32 with round-to-nearest (FP64 regulators and epilogues): their
+gradient is checked against the oracle and against the FP64 plan with a bound
+from FP32 rounding, 1e-5 of the largest entry of each gradient array (FP32
+dot products of a few thousand terms carry about sqrt(n) * 2^-24 of the sum of
+their absolute terms).
 """
 import numpy as np
 import pytest
@@ -44,7 +51,8 @@ def test_grad_matches_oracle_autograd(pk, prec, nC, nA, nV, Q, s, seed):
     erre = np.abs(de - ref["deps"]).max() / np.abs(ref["deps"]).max()
     errs = abs(ds - ref["ds"]) / abs(ref["ds"])
     print(prec, nC, nA, nV, Q, "dB %.2e deps %.2e ds %.2e" % (errB, erre, errs))
-    assert errB < 1e-10 and erre < 1e-10 and errs < 1e-10
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert errB < tol and erre < tol and errs < tol
 
 
 def test_grad_finite_differences_vtz(pk):
@@ -110,3 +118,23 @@ def test_grad_requires_flag(pk):
     plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux)
     with pytest.raises(pk.DSRGError):
         plan.energy_grad(*pk.to_device(p), p.s)
+
+
+def test_split_grad_against_fp64_plan_vtz(pk):
+    """cc-pVTZ size: the gradient of a BF16x3 plan (FP32 contractions) against
+    the FP64 plan's, normalised by the largest entry of each array."""
+    p = make_problem(**CONFIGS["naphthyne-vtz-398"])
+    dev = pk.to_device(p)
+    res = {}
+    for prec in ("fp64", "bf16x3"):
+        plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, grad=True)
+        out, dB, de, ds = plan.energy_grad(*dev, p.s)
+        plan.sync()
+        res[prec] = (dB.cpu().numpy(), de.cpu().numpy(), float(ds.cpu()[0]))
+        plan.close()
+    (b64, e64, s64), (b32, e32, s32) = res["fp64"], res["bf16x3"]
+    errB = np.abs(b32 - b64).max() / np.abs(b64).max()
+    erre = np.abs(e32 - e64).max() / np.abs(e64).max()
+    errs = abs(s32 - s64) / abs(s64)
+    print("vtz split vs fp64 gradient: dB %.2e deps %.2e ds %.2e" % (errB, erre, errs))
+    assert errB < 1e-5 and erre < 1e-5 and errs < 1e-5
