@@ -78,10 +78,15 @@ struct GemmArgs {
   long long ci, cj;
   double alpha;
   int accumulate;
+  int nb;                // independent problems in one launch (blockIdx.z);
+  long long sa, sb, sc;  // their offsets of A, Bm, C
 };
 
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
   __shared__ double sA[16][65], sB[16][65];
+  g.A += blockIdx.z * g.sa;
+  g.Bm += blockIdx.z * g.sb;
+  g.C += blockIdx.z * g.sc;
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long long L = (long long)g.L1 * g.L2;
@@ -141,51 +146,71 @@ constexpr int SG_T = 128, SG_K = 16;
 __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
   __shared__ __align__(16) float sA[SG_K][SG_T + 4];
   __shared__ __align__(16) float sB[SG_K][SG_T + 4];
+  g.A += blockIdx.z * g.sa;
+  g.Bm += blockIdx.z * g.sb;
+  g.C += blockIdx.z * g.sc;
   const int i0 = blockIdx.y * SG_T, j0 = blockIdx.x * SG_T;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const long long L = (long long)g.L1 * g.L2;
+  const unsigned L = (unsigned)g.L1 * (unsigned)g.L2, L2 = (unsigned)g.L2;
   const bool a_kfast = g.a2 == 1 && g.L2 > 1, b_kfast = g.b2 == 1 && g.L2 > 1;
+  // element e = threadIdx.x + 256 t of a 16 x 128 operand tile: (k row, tile column)
+  auto kc = [&](bool kfast, int t, int& ll, int& c) {
+    const int e = threadIdx.x + 256 * t;
+    if (kfast) {
+      ll = e % SG_K;
+      c = e / SG_K;
+    } else {
+      ll = e / SG_T;
+      c = e % SG_T;
+    }
+  };
+  float ra_next[8], rb_next[8];
+  auto fetch = [&](unsigned l0) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      int ll, c;
+      kc(a_kfast, t, ll, c);
+      const unsigned l = l0 + ll;
+      float v = 0.f;
+      if (l < L && i0 + c < g.M) {
+        const unsigned l1 = l / L2, l2 = l - l1 * L2;
+        v = (float)g.A[(long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2];
+      }
+      ra_next[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      int ll, c;
+      kc(b_kfast, t, ll, c);
+      const unsigned l = l0 + ll;
+      float v = 0.f;
+      if (l < L && j0 + c < g.N) {
+        const unsigned l1 = l / L2, l2 = l - l1 * L2;
+        v = (float)g.Bm[(long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj];
+      }
+      rb_next[t] = v;
+    }
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      int ll, c;
+      kc(a_kfast, t, ll, c);
+      sA[ll][c] = ra_next[t];
+      kc(b_kfast, t, ll, c);
+      sB[ll][c] = rb_next[t];
+    }
+  };
   float acc[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-  for (long long l0 = 0; l0 < L; l0 += SG_K) {
-    for (int e = threadIdx.x; e < SG_K * SG_T; e += 256) {
-      int ll, c;
-      if (a_kfast) {
-        ll = e % SG_K;
-        c = e / SG_K;
-      } else {
-        ll = e / SG_T;
-        c = e % SG_T;
-      }
-      const long long l = l0 + ll;
-      float v = 0.f;
-      if (l < L && i0 + c < g.M) {
-        const long long l1 = l / g.L2, l2 = l % g.L2;
-        v = (float)g.A[(long long)(i0 + c) * g.ai + l1 * g.a1 + l2 * g.a2];
-      }
-      sA[ll][c] = v;
-    }
-    for (int e = threadIdx.x; e < SG_K * SG_T; e += 256) {
-      int ll, c;
-      if (b_kfast) {
-        ll = e % SG_K;
-        c = e / SG_K;
-      } else {
-        ll = e / SG_T;
-        c = e % SG_T;
-      }
-      const long long l = l0 + ll;
-      float v = 0.f;
-      if (l < L && j0 + c < g.N) {
-        const long long l1 = l / g.L2, l2 = l % g.L2;
-        v = (float)g.Bm[l1 * g.b1 + l2 * g.b2 + (long long)(j0 + c) * g.bj];
-      }
-      sB[ll][c] = v;
-    }
+  fetch(0);
+  for (unsigned l0 = 0; l0 < L; l0 += SG_K) {
+    stash();
     __syncthreads();
+    if (l0 + SG_K < L) fetch(l0 + SG_K);  // next chunk's loads overlap this chunk's FMAs
 #pragma unroll 4
     for (int ll = 0; ll < SG_K; ++ll) {
       const float4 a0 = *(const float4*)&sA[ll][ty * 8];
@@ -219,10 +244,10 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
 static cudaError_t gemm(dsrg_plan* p, const GemmArgs& g) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (p->prec == DSRG_PREC_FP64) {
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64);
+    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.nb);
     gemm_fp64_kernel<<<grid, 256, 0, p->stream>>>(g);
   } else {
-    dim3 grid((g.N + SG_T - 1) / SG_T, (g.M + SG_T - 1) / SG_T);
+    dim3 grid((g.N + SG_T - 1) / SG_T, (g.M + SG_T - 1) / SG_T, g.nb);
     gemm_f32_kernel<<<grid, 256, 0, p->stream>>>(g);
   }
   DSRG_LAUNCH_CHECK(p);
@@ -1181,8 +1206,9 @@ __global__ void adj_m_generic_kernel(ActAdjArgs a, const double* __restrict__ dP
 }
 
 struct GradWs {
-  double* Wk = nullptr;   // [nC][nVp][nVp]
+  double* Wk = nullptr;   // [kgroup][nC][nVp][nVp]
   int nVp = 0;
+  int kgroup = 1;         // core rows whose W^{kj} are formed before one batched GEMM
   double* dX = nullptr;   // [nC][nA][nV][nV]
   double* dZ = nullptr;   // [nA][nC][nC][nV]
   double *dW1Vt = nullptr, *dW1T = nullptr, *dTi = nullptr, *dV1 = nullptr;
@@ -1196,7 +1222,11 @@ bool grad_alloc(dsrg_plan* p) {
   GradWs* g = new GradWs();
   p->grad = g;
   g->nVp = (z.nV + GT - 1) / GT * GT;
-  bool ok = plan_alloc(p, (void**)&g->Wk, (size_t)z.nC * g->nVp * g->nVp * 8);
+  // as many rows as fit in 2 GiB of W (at least one)
+  const size_t per_k = (size_t)z.nC * g->nVp * g->nVp * 8;
+  const size_t kmax = ((size_t)2 << 30) / per_k;
+  g->kgroup = (int)(kmax < 1 ? 1 : (kmax > (size_t)z.nC ? (size_t)z.nC : kmax));
+  bool ok = plan_alloc(p, (void**)&g->Wk, per_k * g->kgroup);
   if (z.nA > 0) {
     const size_t w1n = p->act.w1n, w2n = p->act.w2n;
     const size_t nHP2 = (size_t)4 * z.nH * z.nP;
@@ -1231,6 +1261,17 @@ static GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, 
   g.C = C; g.ci = ci; g.cj = cj;
   g.alpha = alpha;
   g.accumulate = 1;
+  g.nb = 1;
+  g.sa = g.sb = g.sc = 0;
+  return g;
+}
+
+// The same GEMM for nb problems whose A, Bm, C start sa, sb, sc elements apart.
+static GemmArgs batched(GemmArgs g, int nb, long long sa, long long sb, long long sc) {
+  g.nb = nb;
+  g.sa = sa;
+  g.sb = sb;
+  g.sc = sc;
   return g;
 }
 
@@ -1256,17 +1297,23 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   const bool fp64 = p->prec == DSRG_PREC_FP64;
   // ---- F1: per core row k, W^{kj} then dB[:, k, V] += 2 sum_j B_j W^{kj T}
   const int n_tp = p->n_tp_ccvv;  // 64-wide tile pairs of the FP64 work list
-  for (int k = 0; k < z.nC; ++k) {
-    if (fp64)
-      ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp, w->nVp,
-                                                           w->Wk, deps, ds);
-    else
-      ccvv_adj_kernel<float><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp, w->nVp,
-                                                          w->Wk, deps, ds);
-    DSRG_LAUNCH_CHECK(p);
-    const long long nVp = w->nVp;
-    e = gemm(p, mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
-                   dB + (long long)k * z.nP + z.nA, HP, 1, 2.0));
+  // rows k in groups of w->kgroup: W^{kj} of the group, then one batched GEMM
+  const long long nVp = w->nVp, wstride = (long long)z.nC * nVp * nVp;
+  for (int k0 = 0; k0 < z.nC; k0 += w->kgroup) {
+    const int kg = (z.nC - k0) < w->kgroup ? (z.nC - k0) : w->kgroup;
+    for (int k = k0; k < k0 + kg; ++k) {
+      double* Wk = w->Wk + (k - k0) * wstride;
+      if (fp64)
+        ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
+                                                             w->nVp, Wk, deps, ds);
+      else
+        ccvv_adj_kernel<float><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
+                                                            w->nVp, Wk, deps, ds);
+      DSRG_LAUNCH_CHECK(p);
+    }
+    e = gemm(p, batched(mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
+                           dB + (long long)k0 * z.nP + z.nA, HP, 1, 2.0),
+                        kg, 0, wstride, z.nP));
     if (e != cudaSuccess) return e;
   }
   if (z.nA == 0) return cudaSuccess;
@@ -1289,18 +1336,15 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     }
 #undef CAVV_ADJ
     DSRG_LAUNCH_CHECK(p);
-    for (int m = 0; m < z.nC; ++m) {
-      e = gemm(p, mk(z.Q, z.nV, z.nA, z.nV, B + (long long)z.nC * z.nP + z.nA, HP, z.nP, 1,
-                     w->dX + (long long)m * z.nA * nV2, nV2, 1, nV, dB + (long long)m * z.nP + z.nA,
-                     HP, 1, 1.0));
-      if (e != cudaSuccess) return e;
-    }
-    for (int u = 0; u < z.nA; ++u) {
-      e = gemm(p, mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->dX + (long long)u * nV2,
-                     (long long)z.nA * nV2, nV, 1, dB + (long long)(z.nC + u) * z.nP + z.nA, HP, 1,
-                     1.0));
-      if (e != cudaSuccess) return e;
-    }
+    e = gemm(p, batched(mk(z.Q, z.nV, z.nA, z.nV, B + (long long)z.nC * z.nP + z.nA, HP, z.nP, 1,
+                           w->dX, nV2, 1, nV, dB + z.nA, HP, 1, 1.0),
+                        z.nC, 0, (long long)z.nA * nV2, z.nP));
+    if (e != cudaSuccess) return e;
+    e = gemm(p, batched(mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->dX,
+                           (long long)z.nA * nV2, nV, 1, dB + (long long)z.nC * z.nP + z.nA, HP, 1,
+                           1.0),
+                        z.nA, 0, nV2, z.nP));
+    if (e != cudaSuccess) return e;
   }
   // ---- F3
   {
@@ -1314,16 +1358,14 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     }
     DSRG_LAUNCH_CHECK(p);
     const long long nCV = (long long)z.nC * nV, nCCV = (long long)z.nC * nCV;
-    for (int m = 0; m < z.nC; ++m) {
-      e = gemm(p, mk(z.Q, z.nV, z.nC, z.nA, B, HP, z.nP, 1, w->dZ + (long long)m * nCV, nV, nCCV, 1,
-                     dB + (long long)m * z.nP + z.nA, HP, 1, 1.0));
-      if (e != cudaSuccess) return e;
-    }
-    for (int u = 0; u < z.nA; ++u) {
-      e = gemm(p, mk(z.Q, z.nC, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->dZ + (long long)u * nCCV, nCV,
-                     1, nV, dB + u, HP, z.nP, 1.0));
-      if (e != cudaSuccess) return e;
-    }
+    e = gemm(p, batched(mk(z.Q, z.nV, z.nC, z.nA, B, HP, z.nP, 1, w->dZ, nV, nCCV, 1, dB + z.nA, HP,
+                           1, 1.0),
+                        z.nC, 0, nCV, z.nP));
+    if (e != cudaSuccess) return e;
+    e = gemm(p, batched(mk(z.Q, z.nC, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->dZ, nCV, 1, nV, dB, HP,
+                           z.nP, 1.0),
+                        z.nA, 0, nCCV, 1));
+    if (e != cudaSuccess) return e;
   }
   // ---- active block
   {
@@ -1376,18 +1418,15 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     adj_k_to_b_kernel<<<blocks((size_t)z.Q * HP), 256, 0, st>>>(a, B, dB);
     DSRG_LAUNCH_CHECK(p);
     const long long CP = (long long)z.nC * z.nP;
-    for (int x = 0; x < z.nA; ++x) {
-      e = gemm(p, mk(z.Q, z.nV, z.nA, z.nV, B + CP + z.nA, HP, z.nP, 1,
-                     w->dM + (long long)x * z.nA * nV2, nV2, 1, nV,
-                     dB + (long long)(z.nC + x) * z.nP + z.nA, HP, 1, 1.0));
-      if (e != cudaSuccess) return e;
-    }
-    for (int u = 0; u < z.nA; ++u) {
-      e = gemm(p, mk(z.Q, z.nV, z.nA, z.nV, B + CP + z.nA, HP, z.nP, 1, w->dM + (long long)u * nV2,
-                     (long long)z.nA * nV2, nV, 1, dB + (long long)(z.nC + u) * z.nP + z.nA, HP, 1,
-                     1.0));
-      if (e != cudaSuccess) return e;
-    }
+    e = gemm(p, batched(mk(z.Q, z.nV, z.nA, z.nV, B + CP + z.nA, HP, z.nP, 1, w->dM, nV2, 1, nV,
+                           dB + (long long)z.nC * z.nP + z.nA, HP, 1, 1.0),
+                        z.nA, 0, (long long)z.nA * nV2, z.nP));
+    if (e != cudaSuccess) return e;
+    e = gemm(p, batched(mk(z.Q, z.nV, z.nA, z.nV, B + CP + z.nA, HP, z.nP, 1, w->dM,
+                           (long long)z.nA * nV2, nV, 1, dB + (long long)z.nC * z.nP + z.nA, HP, 1,
+                           1.0),
+                        z.nA, 0, nV2, z.nP));
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
