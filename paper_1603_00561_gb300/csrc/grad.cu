@@ -164,17 +164,19 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
       c = e % SG_T;
     }
   };
-  float ra_next[8], rb_next[8];
+  // raw FP64 values of the next chunk: converted only when stored to shared
+  // memory, so the loads stay in flight during this chunk's FMAs
+  double ra_next[8], rb_next[8];
   auto fetch = [&](unsigned l0) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       int ll, c;
       kc(a_kfast, t, ll, c);
       const unsigned l = l0 + ll;
-      float v = 0.f;
+      double v = 0.0;
       if (l < L && i0 + c < g.M) {
         const unsigned l1 = l / L2, l2 = l - l1 * L2;
-        v = (float)g.A[(long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2];
+        v = g.A[(long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2];
       }
       ra_next[t] = v;
     }
@@ -183,10 +185,10 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
       int ll, c;
       kc(b_kfast, t, ll, c);
       const unsigned l = l0 + ll;
-      float v = 0.f;
+      double v = 0.0;
       if (l < L && j0 + c < g.N) {
         const unsigned l1 = l / L2, l2 = l - l1 * L2;
-        v = (float)g.Bm[(long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj];
+        v = g.Bm[(long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj];
       }
       rb_next[t] = v;
     }
@@ -196,9 +198,9 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
     for (int t = 0; t < 8; ++t) {
       int ll, c;
       kc(a_kfast, t, ll, c);
-      sA[ll][c] = ra_next[t];
+      sA[ll][c] = (float)ra_next[t];
       kc(b_kfast, t, ll, c);
-      sB[ll][c] = rb_next[t];
+      sB[ll][c] = (float)rb_next[t];
     }
   };
   float acc[8][8];
@@ -332,6 +334,87 @@ __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict_
       const double D = E - eps[ve + a] - eps[ve + b];
       const RegD R = rf1_d(D, s);
       const double xv = (double)x[r][c], yv = (double)y[r][c];
+      Wk[((size_t)j * nVp + a) * nVp + b] = (4.0 * xv - 2.0 * yv) * R.v;
+      if (mirror) Wk[((size_t)j * nVp + b) * nVp + a] = (4.0 * yv - 2.0 * xv) * R.v;
+      const double q = fma(xv, xv - yv, yv * yv);
+      dk = fma(2.0 * wt * q, R.dD, dk);
+      dss = fma(wt * q, R.ds, dss);
+      const double gv = -2.0 * q * R.dD;
+      racc[r] += gv;
+      if (mirror) cacc[c] += gv;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) atomicAdd(&rowacc[ty * 4 + r], racc[r]);
+  if (mirror) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) atomicAdd(&colacc[tx * 4 + c], cacc[c]);
+  }
+  const double tk = block_sum<256>(dk, red);
+  const double ts = block_sum<256>(dss, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&deps[k], tk);
+    atomicAdd(ds, ts);
+  }
+  if (threadIdx.x < GT) {
+    const int a = a0 + threadIdx.x, b = b0 + threadIdx.x;
+    if (a < z.nV) atomicAdd(&deps[ve + a], rowacc[threadIdx.x]);
+    if (mirror && b < z.nV) atomicAdd(&deps[ve + b], colacc[threadIdx.x]);
+  }
+}
+
+// F1 adjoint from precomputed pair blocks (split-precision plans): the FP32
+// GEMM has formed V_k[a][j*nP + p] = v^{kj}_{a,p-nA} for the rows k of a group;
+// this kernel forms W^{kj} and the eps / s derivatives exactly as the
+// epilogue of ccvv_adj_kernel, reading x = v^{kj}_ab and y = v^{kj}_ba through
+// two 64 x 64 shared-memory tiles. Grid: (group row, j, tile pair A <= B).
+__global__ void __launch_bounds__(256) ccvv_adj_w_kernel(const double* __restrict__ V,
+                                                         const double* __restrict__ eps, double s,
+                                                         Sizes z, int k0, const int2* __restrict__ tps,
+                                                         int n_tp, int nVp, double* __restrict__ W,
+                                                         double* __restrict__ deps,
+                                                         double* __restrict__ ds) {
+  extern __shared__ double vsm[];
+  double* tX = vsm;                 // [64][65]  V[a0 + r][j, b0 + c]
+  double* tY = vsm + GT * (GT + 1); // [64][65]  V[b0 + r][j, a0 + c]
+  __shared__ double rowacc[GT], colacc[GT];
+  __shared__ double red[8];
+  const int kl = blockIdx.x / (z.nC * n_tp);
+  const int rem = blockIdx.x % (z.nC * n_tp);
+  const int j = rem / n_tp, k = k0 + kl;
+  const int2 ab = tps[rem % n_tp];
+  const int a0 = ab.x * GT, b0 = ab.y * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int ve = z.nC + z.nA;
+  const long long ldv = (long long)z.nC * z.nP;
+  const double* Vk = V + (long long)kl * z.nV * ldv + (long long)j * z.nP + z.nA;
+  double* Wk = W + (long long)kl * z.nC * nVp * nVp;
+  if (threadIdx.x < GT) {
+    rowacc[threadIdx.x] = 0.0;
+    colacc[threadIdx.x] = 0.0;
+  }
+  for (int e = threadIdx.x; e < GT * GT; e += 256) {
+    const int r = e / GT, c = e % GT;
+    tX[r * (GT + 1) + c] = (a0 + r < z.nV && b0 + c < z.nV) ? Vk[(long long)(a0 + r) * ldv + b0 + c] : 0.0;
+    tY[r * (GT + 1) + c] = (b0 + r < z.nV && a0 + c < z.nV) ? Vk[(long long)(b0 + r) * ldv + a0 + c] : 0.0;
+  }
+  __syncthreads();
+  const double E = eps[k] + eps[j];
+  const bool mirror = ab.x < ab.y;
+  const double wt = mirror ? 2.0 : 1.0;
+  double dk = 0.0, dss = 0.0;
+  double racc[4] = {0, 0, 0, 0}, cacc[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int al = ty * 4 + r, a = a0 + al;
+    if (a >= z.nV) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int bl = tx * 4 + c, b = b0 + bl;
+      if (b >= z.nV) continue;
+      const double D = E - eps[ve + a] - eps[ve + b];
+      const RegD R = rf1_d(D, s);
+      const double xv = tX[al * (GT + 1) + bl], yv = tY[bl * (GT + 1) + al];
       Wk[((size_t)j * nVp + a) * nVp + b] = (4.0 * xv - 2.0 * yv) * R.v;
       if (mirror) Wk[((size_t)j * nVp + b) * nVp + a] = (4.0 * yv - 2.0 * xv) * R.v;
       const double q = fma(xv, xv - yv, yv * yv);
@@ -1209,6 +1292,7 @@ struct GradWs {
   double* Wk = nullptr;   // [kgroup][nC][nVp][nVp]
   int nVp = 0;
   int kgroup = 1;         // core rows whose W^{kj} are formed before one batched GEMM
+  double* V = nullptr;    // [kgroup][nV][nC*nP] pair blocks v^{kj} (split plans)
   double* dX = nullptr;   // [nC][nA][nV][nV]
   double* dZ = nullptr;   // [nA][nC][nC][nV]
   double *dW1Vt = nullptr, *dW1T = nullptr, *dTi = nullptr, *dV1 = nullptr;
@@ -1222,11 +1306,14 @@ bool grad_alloc(dsrg_plan* p) {
   GradWs* g = new GradWs();
   p->grad = g;
   g->nVp = (z.nV + GT - 1) / GT * GT;
-  // as many rows as fit in 2 GiB of W (at least one)
-  const size_t per_k = (size_t)z.nC * g->nVp * g->nVp * 8;
-  const size_t kmax = ((size_t)2 << 30) / per_k;
+  // as many rows as fit in 2 GiB of W (plus the pair blocks V of split plans; at least one)
+  const bool split = p->prec != DSRG_PREC_FP64;
+  const size_t per_w = (size_t)z.nC * g->nVp * g->nVp * 8;
+  const size_t per_v = split ? (size_t)z.nV * z.nC * z.nP * 8 : 0;
+  const size_t kmax = ((size_t)2 << 30) / (per_w + per_v);
   g->kgroup = (int)(kmax < 1 ? 1 : (kmax > (size_t)z.nC ? (size_t)z.nC : kmax));
-  bool ok = plan_alloc(p, (void**)&g->Wk, per_k * g->kgroup);
+  bool ok = plan_alloc(p, (void**)&g->Wk, per_w * g->kgroup);
+  if (ok && split) ok = plan_alloc(p, (void**)&g->V, per_v * g->kgroup);
   if (z.nA > 0) {
     const size_t w1n = p->act.w1n, w2n = p->act.w2n;
     const size_t nHP2 = (size_t)4 * z.nH * z.nP;
@@ -1301,14 +1388,25 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   const long long nVp = w->nVp, wstride = (long long)z.nC * nVp * nVp;
   for (int k0 = 0; k0 < z.nC; k0 += w->kgroup) {
     const int kg = (z.nC - k0) < w->kgroup ? (z.nC - k0) : w->kgroup;
-    for (int k = k0; k < k0 + kg; ++k) {
-      double* Wk = w->Wk + (k - k0) * wstride;
-      if (fp64)
+    if (fp64) {
+      for (int k = k0; k < k0 + kg; ++k) {
         ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
-                                                             w->nVp, Wk, deps, ds);
-      else
-        ccvv_adj_kernel<float><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
-                                                            w->nVp, Wk, deps, ds);
+                                                             w->nVp, w->Wk + (k - k0) * wstride,
+                                                             deps, ds);
+        DSRG_LAUNCH_CHECK(p);
+      }
+    } else {
+      // V_k[a][(j,p)] = sum_Q B[Q,k,a] B[Q,j,p] for the group (FP32 GEMM), then W
+      const long long ldv = (long long)z.nC * z.nP;
+      GemmArgs gv = batched(mk(z.nV, (int)ldv, z.Q, 1, B + (long long)k0 * z.nP + z.nA, 1, HP, 0, B,
+                               HP, 0, 1, w->V, ldv, 1, 1.0),
+                            kg, z.nP, 0, (long long)z.nV * ldv);
+      gv.accumulate = 0;
+      if ((e = gemm(p, gv)) != cudaSuccess) return e;
+      const size_t smw = (size_t)2 * GT * (GT + 1) * 8;
+      raise_smem_limit((const void*)ccvv_adj_w_kernel, smw);
+      ccvv_adj_w_kernel<<<kg * z.nC * n_tp, 256, smw, st>>>(w->V, eps, s, z, k0, p->d_tp_ccvv, n_tp,
+                                                            w->nVp, w->Wk, deps, ds);
       DSRG_LAUNCH_CHECK(p);
     }
     e = gemm(p, batched(mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
