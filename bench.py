@@ -32,6 +32,8 @@ WORKLOADS = {
     "naphthyne-vtz-398": dict(ncore=24, nactive=2, nvirt=372, naux=1200, s=0.5),
     # a smaller case of the same shape family, for ncu captures (B = 147 MB > L2)
     "profile-16x600": dict(ncore=16, nactive=2, nvirt=600, naux=1700, s=0.5),
+    # the small synthetic system (quick runs of the reference arm)
+    "tiny-74": dict(ncore=10, nactive=4, nvirt=60, naux=200, s=0.5),
 }
 # nominal dense rates (TFLOP/s) of the recipe, used to scale the measured BF16 peak
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
@@ -130,6 +132,24 @@ def dist_init():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x, world, device):
+    """The largest value of a per-rank number over all ranks (a timing: the job
+    is as slow as its slowest rank). One rank: x itself."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput under weak scaling: every rank processes the same
+    units (its own molecule), so the job does world * units in `seconds`."""
+    return world * units_per_rank / seconds
 
 
 def run_reference(args, world, rank):
@@ -370,14 +390,11 @@ def main():
         barrier()
     clocks = cs.summary()
     t_local = e0.elapsed_time(e1) / 1e3 / args.steps
-    t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_step = float(t.item())
+    t_step = max_over_ranks(t_local, world, "cuda")
     energies = out.cpu().numpy().tolist()
 
     flops = ccvv_flops(p.ncore, p.nvirt, p.naux)
-    value = world * flops / t_step / 1e12
+    value = job_rate(world, flops, t_step) / 1e12
 
     # dominant kernel: the CCVV pair contraction alone, timed with CUDA events on the
     # plan's stream inside the library (planes staged first, one untimed launch)
@@ -428,10 +445,7 @@ def main():
         plan.energy_host(Bh, eh, gh, lh, p.s, out=oh)   # synchronises (host out)
         te2e.append(time.perf_counter() - t0)
     t_e2e = float(np.median(te2e))
-    te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    t_e2e = float(te.item())
+    t_e2e = max_over_ranks(t_e2e, world, "cuda")
     h2d = (Bh.numel() + eh.numel() + gh.numel() + lh.numel()) * 8
 
     # accuracy against the FP64 GPU path, and its E2 time per molecule
@@ -476,7 +490,7 @@ def main():
             "energies_eh": dict(zip(pk.BLOCKS, energies)),
             "roofline": roofline,
             "cpu_baseline": cb,
-            "e2e": {"value": world * flops / t_e2e / 1e12, "unit": UNIT,
+            "e2e": {"value": job_rate(world, flops, t_e2e) / 1e12, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 40,
                     "ms_per_step": t_e2e * 1e3},
             "gpu_launches": launches_per_step * args.steps,
