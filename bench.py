@@ -314,6 +314,9 @@ def main():
                     help="fixed CCVV schedule code instead of autotuning it")
     ap.add_argument("--schedule-sweep", action="store_true",
                     help="time the CCVV kernel under every candidate schedule code and exit")
+    ap.add_argument("--only", choices=["grad", "batch"], default=None,
+                    help="run only the gradient leg, or only the batch leg (64 molecules unless "
+                         "--with-batch says otherwise), print its JSON and exit (for profiling)")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -331,6 +334,15 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     pk.build()
+    if args.only == "grad":
+        if rank == 0:
+            print(json.dumps({"gradient": time_gradient(pk, torch)}), flush=True)
+        return
+    if args.only == "batch":
+        if rank == 0:
+            print(json.dumps({"batch": time_batch(pk, torch, args.with_batch or 64, args.precision)}),
+                  flush=True)
+        return
     cfg = WORKLOADS[args.workload]
     # weak scaling: each rank its own molecule of the same size
     p = make_problem(seed=rank, **cfg)

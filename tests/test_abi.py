@@ -62,3 +62,23 @@ def test_argument_errors_without_gpu(lib):
     assert L.dsrg_df_plan(ctypes.byref(h), ctypes.byref(sz), 7, None, 0) == _native.ERR_INVALID_ARG
     assert L.dsrg_mrpt2_energy(None, None, None, None, None, 0.5, None) == _native.ERR_INVALID_ARG
     assert L.dsrg_plan_destroy(None) == _native.OK
+
+
+def test_missing_library_raises(monkeypatch):
+    """No fallback: without the compiled library the binding raises."""
+    from paper_1603_00561_gb300 import _native
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(RuntimeError):
+        _native.load(os.path.join(ROOT, "no-such-dir", "libdsrg.so"))
+
+
+def test_no_cpu_path_without_gpu():
+    """On a machine without a GPU the plan refuses to exist (there is no CPU path)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1603_00561_gb300 as pk
+    with pytest.raises(RuntimeError):
+        pk.Plan(2, 1, 10, 8)
+    with pytest.raises(RuntimeError):
+        pk.Batch([(2, 1, 10, 8)])

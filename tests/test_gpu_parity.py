@@ -162,3 +162,28 @@ def test_allocation_failure_is_reported(pkg, monkeypatch):
     with pytest.raises(pkg.DSRGError) as ei:
         pkg.Plan(3, 2, 20, 10)
     assert ei.value.status == _native.ERR_OOM
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_energy_call_captures_into_a_cuda_graph(pkg, prec):
+    """An energy call neither allocates nor synchronises, so it can be captured
+    into a CUDA graph by the caller and replayed: the replay gives the same
+    numbers bit for bit."""
+    import torch
+    p = make_problem(6, 2, 150, 90, s=0.5, seed=40)
+    plan = pkg.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec)
+    dev = pkg.to_device(p)
+    out = plan.energy(*dev, p.s)          # first call outside the capture
+    torch.cuda.synchronize()
+    ref = out.clone()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.energy(*dev, p.s, out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    plan.sync()
