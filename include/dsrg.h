@@ -73,7 +73,11 @@ typedef enum {
  *   DSRG_PREC_FP64    plain FP64 products and sums on CUDA cores;
  *   DSRG_PREC_TF32X3  B = hi + lo split into two TF32 planes, products
  *                     hi*hi + hi*lo + lo*hi on tcgen05 tensor cores with FP32
- *                     accumulation;
+ *                     accumulation (and lo*lo where both operands are the
+ *                     same rows, whose diagonal is a sum of squares); the
+ *                     first 32 auxiliary functions, the largest terms, are
+ *                     summed on CUDA cores in FP32 from fl32(B), because the
+ *                     tensor-core accumulator truncates toward zero;
  *   DSRG_PREC_BF16X3  same with BF16 planes.
  * In every mode the regulator (Delta, exp(-s Delta^2), the denominator), the
  * combination with the exchange integral and every sum of energy

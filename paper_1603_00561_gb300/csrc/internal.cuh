@@ -203,6 +203,8 @@ void rest_free(dsrg_plan* p);
 cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
                               double s);
 void* split_plane_ptr(const dsrg_plan* p, bool hi);
+const float* split_tail_ptr(const dsrg_plan* p);  // [plane rows + 256][32] fl32(B), Q < 32
+size_t split_tail_bytes(const Sizes& z);
 // Factor tables of exp(-s D^2) for the active pairs and the pair-independent
 // table, formed by launch_split_rest of the same call.
 void rest_act_tables(const dsrg_plan* p, const double** alpha, const double** pinfo,

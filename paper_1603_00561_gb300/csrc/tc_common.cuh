@@ -9,6 +9,13 @@ namespace dsrg {
 
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bound of every device-side wait
 
+// The first TAIL_Q auxiliary functions (with decaying factors the largest
+// terms) are contracted on CUDA cores in FP32 with round-to-nearest; the
+// tensor cores, whose FP32 accumulator truncates toward zero at every
+// instruction, take Q >= TAIL_Q.
+constexpr int TAIL_Q = 32;
+constexpr int TAIL_PAD = 256;  // zero rows after the last plane row of the FP32 tail rows
+
 // ------------------------------- PTX helpers -------------------------------
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -79,22 +86,29 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                    su32(bar))
                : "memory");
 }
-template <bool BF16>
+// One MMA D (+)= A·B. COL selects the A-operand collector buffer: 0 reads A from
+// shared memory and keeps nothing, 1 reads it and keeps it (fill), 2 takes the
+// A kept by the previous MMA of this thread, which must have had the same
+// descriptor, and releases it (lastuse). Reusing A saves one shared-memory
+// read of the A tile.
+template <bool BF16, int COL = 0>
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t acc) {
+#define DSRG_MMA(KIND, CU)                                                                   \
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"                               \
+               " tcgen05.mma.cta_group::1.kind::" KIND CU " [%0], %1, %2, %3, p;\n}\n" ::"r"(d), \
+               "l"(a), "l"(b), "r"(idesc), "r"(acc)                                          \
+               : "memory")
   if (BF16) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    if (COL == 1) DSRG_MMA("f16", ".collector::a::fill");
+    else if (COL == 2) DSRG_MMA("f16", ".collector::a::lastuse");
+    else DSRG_MMA("f16", "");
   } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    if (COL == 1) DSRG_MMA("tf32", ".collector::a::fill");
+    else if (COL == 2) DSRG_MMA("tf32", ".collector::a::lastuse");
+    else DSRG_MMA("tf32", "");
   }
+#undef DSRG_MMA
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -110,6 +124,31 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 __device__ __forceinline__ void named_bar(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// x_ab += sum_{q < TAIL_Q} T_a[q] T_b[q] for the 16 columns b of one chunk, in
+// FP32 with round-to-nearest, q from the last to the first. T holds fl32(B) of
+// the first TAIL_Q auxiliary functions, one 128-byte row per plane row; `ra` is
+// this thread's row, `rb` the first of the chunk's 16 rows (the same for every
+// lane of the warp, so each load is a broadcast).
+__device__ __forceinline__ void tail_add16(const float* __restrict__ ra,
+                                           const float* __restrict__ rb, uint32_t (&r)[16]) {
+  float t[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t[k] = 0.f;
+#pragma unroll 2
+  for (int q4 = TAIL_Q / 4 - 1; q4 >= 0; --q4) {
+    const float4 a4 = __ldg((const float4*)ra + q4);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float4 b4 = __ldg((const float4*)(rb + k * TAIL_Q) + q4);
+      t[k] = fmaf(a4.w, b4.w, t[k]);
+      t[k] = fmaf(a4.z, b4.z, t[k]);
+      t[k] = fmaf(a4.y, b4.y, t[k]);
+      t[k] = fmaf(a4.x, b4.x, t[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) r[k] = __float_as_uint(__uint_as_float(r[k]) + t[k]);
 }
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows at a
 // 64-byte pitch (8-row groups 512 bytes apart).

@@ -7,7 +7,10 @@
 // hold the rows (g, e) for every hole g and virtual e (K-major over Q); the
 // rows (h, x) of the active particles are appended to them (nH*nA rows,
 // padded to 64). One GEMM
-//     Y = P[(g,e)] . P[(u,f) ; (h,x)]^T       (hi.hi + hi.lo + lo.hi, FP32 accumulation)
+//     Y = P[(g,e)] . P[(u,f) ; (h,x)]^T       (hi.hi + hi.lo + lo.hi, FP32 accumulation,
+//                                              + lo.lo on tiles where the rows overlap;
+//                                              the first 32 auxiliary functions are added
+//                                              in the epilogue in FP32 round-to-nearest)
 // then holds, at row (g, e):
 //     columns u*nVpad + f   ->  (ge|uf) = X_u[e,f] of F2 for g = m core,
 //                               M_xu[e,f] = (xe|uf) for g = x active
@@ -48,7 +51,10 @@ constexpr int F2_T = 32;                              // F2 epilogue tile edge
 struct GemmArgs {
   int a_row0;        // row r of Y is plane row a_row0 + r
   int b_row0;        // column c of Y is plane row b_row0 + c
-  int m_tiles, n_tiles, kblocks;
+  int m_tiles, n_tiles;
+  int kblocks;        // K stages on the tensor cores: Q from kq0 to the padded end
+  int kq0;            // = TAIL_Q: Q < kq0 is added in the epilogue from `tail`
+  const float* tail;  // [plane rows + TAIL_PAD][TAIL_Q] fl32(B) of Q < TAIL_Q
   float* Y;
   long long ldy;
   int* status;
@@ -57,6 +63,32 @@ struct GemmArgs {
 __host__ __device__ constexpr uint32_t idesc_mn(bool bf16, uint32_t m, uint32_t n) {
   return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) | ((n >> 3) << 17) |
          ((m >> 4) << 24);
+}
+
+// The MMAs of one K stage of one tile (two K steps). K runs from the last
+// auxiliary function to the first and the cross products go before hi*hi: the
+// FP32 accumulator truncates toward zero at every instruction, and with
+// factors that decrease along Q this keeps it small until the largest terms
+// arrive. GRAM (the tile's A rows and B rows overlap, so its diagonal holds
+// squares sum_Q P_r^2) also keeps lo*lo, whose omission would bias them low.
+template <bool BF16, bool GRAM>
+__device__ __forceinline__ void gemm_stage_mmas(uint32_t d, uint32_t sa, uint32_t sb, int kb) {
+  constexpr uint32_t idesc = idesc_mn(BF16, G_BM, G_BN);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t off = (uint32_t)((1 - k) * 32);
+    const uint64_t ah = desc_sw64(sa + off), al = desc_sw64(sa + G_A_BYTES + off);
+    const uint64_t bh = desc_sw64(sb + off), bl = desc_sw64(sb + G_B_BYTES + off);
+    const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+    if (GRAM) {
+      tc_mma<BF16>(d, al, bl, idesc, acc0);
+      tc_mma<BF16>(d, al, bh, idesc, 1u);
+    } else {
+      tc_mma<BF16>(d, al, bh, idesc, acc0);
+    }
+    tc_mma<BF16, 1>(d, ah, bl, idesc, 1u);
+    tc_mma<BF16, 2>(d, ah, bh, idesc, 1u);
+  }
 }
 
 template <bool BF16>
@@ -120,7 +152,7 @@ __global__ void __launch_bounds__(G_THREADS, 1)
           uint8_t* st = tiles + stage * G_STAGE_BYTES;
           mbar_expect_tx(&full[stage], (uint32_t)G_STAGE_BYTES);
           // the last auxiliary functions first (see the K order of the MMA issuer)
-          const int kq = (a.kblocks - 1 - kb) * (G_KB / (BF16 ? 2 : 4));
+          const int kq = a.kq0 + (a.kblocks - 1 - kb) * (G_KB / (BF16 ? 2 : 4));
           tma_load_2d(st, &map_hi, &full[stage], kq, arow);
           tma_load_2d(st + G_A_BYTES, &map_lo, &full[stage], kq, arow);
           uint8_t* sb = st + 2 * G_A_BYTES;
@@ -150,7 +182,6 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_mn(BF16, G_BM, G_BN);
       int stage = 0;
       uint32_t phase = 0;
       int tbuf = 0;
@@ -163,6 +194,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(tbuf * G_BN);
+        const int arow = a.a_row0 + (it / a.n_tiles) * G_BM;
+        const int brow = a.b_row0 + (it % a.n_tiles) * G_BN;
+        const bool gram = arow < brow + G_BN && brow < arow + G_BM;
         for (int kb = 0; kb < a.kblocks; ++kb) {
           if (!mbar_wait(&full[stage], phase, abort_flag, a.status)) {
             ok = false;
@@ -171,20 +205,10 @@ __global__ void __launch_bounds__(G_THREADS, 1)
           tc_fence_after();
           const uint32_t sa = su32(tiles + stage * G_STAGE_BYTES);
           const uint32_t sb = sa + 2 * G_A_BYTES;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            // K from the last auxiliary function to the first, cross products
-            // before hi*hi: the FP32 accumulator truncates toward zero at every
-            // instruction, and with factors that decrease along Q this keeps it
-            // small until the largest terms arrive
-            const uint32_t off = (uint32_t)((1 - k) * 32);
-            const uint64_t ah = desc_sw64(sa + off), al = desc_sw64(sa + G_A_BYTES + off);
-            const uint64_t bh = desc_sw64(sb + off), bl = desc_sw64(sb + G_B_BYTES + off);
-            const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-            tc_mma<BF16>(d, al, bh, idesc, acc0);
-            tc_mma<BF16>(d, ah, bl, idesc, 1u);
-            tc_mma<BF16>(d, ah, bh, idesc, 1u);
-          }
+          if (gram)
+            gemm_stage_mmas<BF16, true>(d, sa, sb, kb);
+          else
+            gemm_stage_mmas<BF16, false>(d, sa, sb, kb);
           issued = true;
           tc_commit(&empty[stage]);
           if (++stage == G_STAGES) {
@@ -218,11 +242,16 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       if (ok) {
         const uint32_t t = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * G_BN);
         float* y = a.Y + (size_t)((it / a.n_tiles) * G_BM + row) * a.ldy + (it % a.n_tiles) * G_BN;
+        const float* ta = a.tail + (size_t)(a.a_row0 + (it / a.n_tiles) * G_BM + row) * TAIL_Q;
+        const float* tb = a.tail + (size_t)(a.b_row0 + (it % a.n_tiles) * G_BN) * TAIL_Q;
         for (int c0 = 0; c0 < G_BN; c0 += 32) {
           uint32_t r0[16], r1[16];
           tmem_ld16(t + c0, r0);
           tmem_ld16(t + c0 + 16, r1);
           tmem_ld_wait();
+          // the first TAIL_Q auxiliary functions in FP32 round-to-nearest
+          tail_add16(ta, tb + (size_t)c0 * TAIL_Q, r0);
+          tail_add16(ta, tb + (size_t)(c0 + 16) * TAIL_Q, r1);
           float4* o = (float4*)(y + c0);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
@@ -261,7 +290,8 @@ __global__ void __launch_bounds__(G_THREADS, 1)
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void xrows_kernel(const double* __restrict__ B, Sizes z, long long xrow0, int Qld,
-                             void* __restrict__ hi, void* __restrict__ lo, double* __restrict__ Xq) {
+                             void* __restrict__ hi, void* __restrict__ lo, double* __restrict__ Xq,
+                             float* __restrict__ tail) {
   const int T = z.nH * z.nA;
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= (size_t)T * z.Q) return;
@@ -272,6 +302,7 @@ __global__ void xrows_kernel(const double* __restrict__ B, Sizes z, long long xr
   const size_t o = (size_t)(xrow0 + t) * Qld + q;
   // the same split of fl32(B) as the main plane rows
   const float vf = (float)v;
+  if (q < TAIL_Q) tail[(size_t)(xrow0 + t) * TAIL_Q + q] = vf;
   if (BF16) {
     const __nv_bfloat16 vh = __float2bfloat16_rn(vf);
     ((__nv_bfloat16*)hi)[o] = vh;
@@ -718,11 +749,14 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     const size_t n = (size_t)T * z.Q;
     void* hi = split_plane_ptr(p, true);
     void* lo = split_plane_ptr(p, false);
+    float* tail = (float*)split_tail_ptr(p);
     const int Qld = split_qld(p);
     if (bf16)
-      xrows_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(B, z, xrow0, Qld, hi, lo, st->Xq);
+      xrows_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(B, z, xrow0, Qld, hi, lo,
+                                                                         st->Xq, tail);
     else
-      xrows_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(B, z, xrow0, Qld, hi, lo, st->Xq);
+      xrows_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(B, z, xrow0, Qld, hi, lo,
+                                                                          st->Xq, tail);
     DSRG_LAUNCH_CHECK(p);
   }
   {
@@ -731,7 +765,9 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     a.b_row0 = z.nC * st->nVpad;
     a.m_tiles = st->m_tiles;
     a.n_tiles = st->n_tiles;
-    a.kblocks = split_qpad(p) / (G_KB / (bf16 ? 2 : 4));
+    a.kq0 = TAIL_Q;
+    a.kblocks = (split_qpad(p) - TAIL_Q) / (G_KB / (bf16 ? 2 : 4));
+    a.tail = split_tail_ptr(p);
     a.Y = st->Y;
     a.ldy = st->ldy;
     a.status = p->d_status;

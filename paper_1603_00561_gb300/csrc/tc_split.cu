@@ -7,7 +7,10 @@
 // CTA accumulates in TMEM
 //     x = v^{ij}[A,B],  x_ab = sum_Q B_ia B_jb  ~ hi.hi + hi.lo + lo.hi
 //     y = v^{ji}[A,B],  y_ab = sum_Q B_ja B_ib  (= v^{ij}_{ba})
-// with FP32 accumulation, then an FP64 epilogue adds
+// with FP32 accumulation over Q >= 32; the epilogue adds the terms of the
+// first 32 auxiliary functions (the largest) in FP32 with round-to-nearest from
+// fl32(B) rows, because the tensor-core accumulator truncates toward zero and
+// its bias would otherwise be set by the largest partial sums. Then it adds
 //     w * sum_ab (x^2 - x y + y^2) R_ab,   R = (1 - exp(-2 s D^2)) / D,
 // D = e_i + e_j - e_a - e_b, w = (2 if i<j) * (2 if A<B); for i = j only x is
 // formed (y = x). The regulator is FP64 throughout: exp(-2 s D^2) is the
@@ -53,6 +56,7 @@ struct SplitWs {
   long long row_base = 0;   // first row of this molecule in a shared (batched) plane buffer
   void* hi = nullptr;
   void* lo = nullptr;
+  float* tail = nullptr;    // [rows + TAIL_PAD][TAIL_Q]  fl32(B) of the first TAIL_Q auxiliary functions
   CUtensorMap map_hi, map_lo;
   double* alpha = nullptr;  // [n_pairs][nVpad]  exp(4 s E_p e_b)
   double* pinfo = nullptr;  // [n_pairs][4]      E_p, exp(-2 s E_p^2), factorisable flag
@@ -68,7 +72,10 @@ struct SplitWs {
 struct MolDesc {
   const double* eps;      // orbital energies [core | active | virtual]
   double s;
-  int nC, nA, nV, nVpad, row0, kblocks, n_tp;
+  int nC, nA, nV, nVpad, row0, n_tp;
+  int kblocks;            // K stages on the tensor cores: Q from kq0 to the padded end
+  int kq0;                // first Q of the tensor-core stages (TAIL_Q)
+  const float* tail;      // [plane rows][TAIL_Q] fl32(B) of Q < TAIL_Q (rows local to the molecule)
   const double* alpha;    // [pairs][nVpad]  exp(4 s E_p e_b)
   const double* pinfo;    // [pairs][4]      E_p, exp(-2 s E_p^2), factorisable flag
   const double* tau;      // [nVpad][nVpad]  exp(-2 s (e_a + e_b)^2)
@@ -138,6 +145,40 @@ __device__ __forceinline__ int slot_row(const ItemPlan& ip, int slot, int nVpad)
     case 1: return ip.j * nVpad + ip.Bt * TT;
     case 2: return ip.j * nVpad + ip.A * TT;
     default: return ip.i * nVpad + ip.Bt * TT;
+  }
+}
+
+// The MMAs of one K stage of one item (two K steps of 16 BF16 / 8 TF32 values).
+// K runs from the last auxiliary function to the first and the small cross
+// products go before hi*hi: the accumulator truncates toward zero at every
+// instruction, and with the factors' magnitudes decreasing along Q this keeps
+// the accumulator small until the largest terms arrive, so few truncations act
+// on the full-size sum. hi*lo and hi*hi share their A operand, which the second
+// takes from the collector buffer.
+template <bool BF16>
+__device__ __forceinline__ void ccvv_stage_mmas(uint32_t dx, uint32_t dy, uint32_t sb,
+                                                const ItemPlan& ip, int kb) {
+  constexpr uint32_t idesc = idesc_128x128<BF16>();
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t off = (uint32_t)((1 - k) * 32);
+    const uint64_t a1h = desc_sw64(sb + (ip.g1a * 2 + 0) * SLOT_BYTES + off);
+    const uint64_t a1l = desc_sw64(sb + (ip.g1a * 2 + 1) * SLOT_BYTES + off);
+    const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + off);
+    const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + off);
+    const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+    tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
+    tc_mma<BF16, 1>(dx, a1h, b1l, idesc, 1u);
+    tc_mma<BF16, 2>(dx, a1h, b1h, idesc, 1u);
+    if (ip.two) {
+      const uint64_t a2h = desc_sw64(sb + (ip.g2a * 2 + 0) * SLOT_BYTES + off);
+      const uint64_t a2l = desc_sw64(sb + (ip.g2a * 2 + 1) * SLOT_BYTES + off);
+      const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + off);
+      const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + off);
+      tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
+      tc_mma<BF16, 1>(dy, a2h, b2l, idesc, 1u);
+      tc_mma<BF16, 2>(dy, a2h, b2h, idesc, 1u);
+    }
   }
 }
 
@@ -213,7 +254,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           }
           uint8_t* st = tiles + stage * STAGE_BYTES;
           mbar_expect_tx(&full[stage], (uint32_t)(ip.nload * 2 * SLOT_BYTES));
-          const int kq = (kblocks - 1 - kb) * KE;
+          const int kq = md->kq0 + (kblocks - 1 - kb) * KE;
           for (int l = 0; l < ip.nload; ++l) {
             const int sl = ip.load[l];
             const int row = row0 + slot_row(ip, sl, nVpad);
@@ -224,14 +265,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
             // L2 prefetch of the stage `prefetch` ahead (in this item or the next)
             const int kf = kb + a.prefetch;
             if (kf < kblocks) {
-              const int kqf = (kblocks - 1 - kf) * KE;
+              const int kqf = md->kq0 + (kblocks - 1 - kf) * KE;
               for (int l = 0; l < ip.nload; ++l) {
                 const int row = row0 + slot_row(ip, ip.load[l], nVpad);
                 tma_prefetch_2d(&map_hi, kqf, row);
                 tma_prefetch_2d(&map_lo, kqf, row);
               }
             } else if (has_next && kf - kblocks < mdn->kblocks) {
-              const int kqf = (mdn->kblocks - 1 - (kf - kblocks)) * KE;
+              const int kqf = mdn->kq0 + (mdn->kblocks - 1 - (kf - kblocks)) * KE;
               for (int l = 0; l < ipn.nload; ++l) {
                 const int row = mdn->row0 + slot_row(ipn, ipn.load[l], mdn->nVpad);
                 tma_prefetch_2d(&map_hi, kqf, row);
@@ -263,7 +304,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_128x128<BF16>();
       int stage = 0;
       uint32_t phase = 0;
       int tbuf = 0;
@@ -288,32 +328,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t sb = su32(tiles + stage * STAGE_BYTES);
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            // K runs from the last auxiliary function to the first and the small
-            // cross products go before hi*hi: the accumulator truncates toward zero
-            // at every instruction, and with the factors' magnitudes decreasing
-            // along Q this keeps the accumulator small until the largest terms
-            // arrive, so few truncations act on the full-size sum.
-            const uint32_t off = (uint32_t)((1 - k) * 32);
-            const uint64_t a1h = desc_sw64(sb + (ip.g1a * 2 + 0) * SLOT_BYTES + off);
-            const uint64_t a1l = desc_sw64(sb + (ip.g1a * 2 + 1) * SLOT_BYTES + off);
-            const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + off);
-            const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + off);
-            const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-            tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
-            tc_mma<BF16>(dx, a1h, b1l, idesc, 1u);
-            tc_mma<BF16>(dx, a1h, b1h, idesc, 1u);
-            if (ip.two) {
-              const uint64_t a2h = desc_sw64(sb + (ip.g2a * 2 + 0) * SLOT_BYTES + off);
-              const uint64_t a2l = desc_sw64(sb + (ip.g2a * 2 + 1) * SLOT_BYTES + off);
-              const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + off);
-              const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + off);
-              tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
-              tc_mma<BF16>(dy, a2h, b2l, idesc, 1u);
-              tc_mma<BF16>(dy, a2h, b2h, idesc, 1u);
-            }
-          }
+          ccvv_stage_mmas<BF16>(dx, dy, sb, ip, kb);
           issued = true;
           tc_commit(&empty[stage]);
           if (++stage == STAGES) {
@@ -380,6 +395,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       const int cend = min(cbeg + 64, ncols);
       const double s = md->s;
       const double* taucol = md->tau + (size_t)(ip.Bt * TT) * nVpad + arow;
+      const float* tail_ia = md->tail + (size_t)(ip.i * nVpad + arow) * TAIL_Q;
+      const float* tail_ja = md->tail + (size_t)(ip.j * nVpad + arow) * TAIL_Q;
 
       bool ok = mbar_wait(&tfull[tbuf], tphase, abort_flag, a.status);
       tc_fence_after();
@@ -393,6 +410,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           if (ip.two) tmem_ld16(ty + c0, yr);
           tmem_ld_wait();
           if (!rok) continue;
+          // the first TAIL_Q auxiliary functions, the largest terms, in FP32
+          // round-to-nearest (the tensor cores took the rest)
+          tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
+          if (ip.two)
+            tail_add16(tail_ja, md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
           if (far) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -490,7 +512,8 @@ template <bool BF16>
 __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restrict__ B, Sizes z,
                                                            int nVpad, int Qld,
                                                            void* __restrict__ hi,
-                                                           void* __restrict__ lo) {
+                                                           void* __restrict__ lo,
+                                                           float* __restrict__ tail) {
   __shared__ double t[64][65];
   const int q0 = blockIdx.x * 64, a0 = blockIdx.y * 64, h = blockIdx.z;
   for (int k = threadIdx.x; k < 64 * 64; k += 256) {
@@ -499,6 +522,13 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
     t[r][c] = (q < z.Q && a < z.nV) ? B[bidx(z, q, h, z.nA + a)] : 0.0;
   }
   __syncthreads();
+  if (q0 == 0) {
+    // fl32(B) of the first TAIL_Q auxiliary functions, row-major per plane row
+    for (int k = threadIdx.x; k < 64 * TAIL_Q; k += 256) {
+      const int c = k / TAIL_Q, q = k % TAIL_Q;
+      tail[((size_t)h * nVpad + a0 + c) * TAIL_Q + q] = (float)t[q][c];
+    }
+  }
   const int ar = threadIdx.x >> 2, qq = (threadIdx.x & 3) * 16;
   const size_t o = ((size_t)h * nVpad + a0 + ar) * Qld + q0 + qq;
   if (BF16) {
@@ -651,6 +681,12 @@ int split_ccvv_blocks(const dsrg_plan* p) {
 // then the active-particle rows (h, x) of tc_rest.cu.
 int split_plane_rows(const Sizes& z) { return z.nH * ((z.nV + TT - 1) / TT * TT) + rest_xrows(z); }
 int split_plane_qpad(const Sizes& z) { return (z.Q + 63) / 64 * 64; }
+// FP32 rows of the first TAIL_Q auxiliary functions: one per plane row plus
+// TAIL_PAD zero rows, so that a GEMM tile running past the last plane row
+// reads zeros as its TMA loads do.
+size_t split_tail_bytes(const Sizes& z) {
+  return ((size_t)split_plane_rows(z) + TAIL_PAD) * TAIL_Q * sizeof(float);
+}
 
 // Static schedule: items in their global order (molecule, pair, tile pair) are
 // dealt to the CTA with the least accumulated cost (ties: lowest index), which
@@ -757,8 +793,10 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
        plan_alloc(p, (void**)&w->pinfo, (size_t)p->n_pairs * 4 * 8) &&
        plan_alloc(p, (void**)&w->tau, (size_t)w->nVpad * w->nVpad * 8) &&
        plan_alloc(p, (void**)&w->trange, (size_t)w->nT * 2 * 8) &&
-       plan_alloc(p, (void**)&w->d_mol, sizeof(MolDesc));
+       plan_alloc(p, (void**)&w->d_mol, sizeof(MolDesc)) &&
+       plan_alloc(p, (void**)&w->tail, split_tail_bytes(z));
   if (!ok) return false;
+  if (cudaMemset(w->tail, 0, split_tail_bytes(z)) != cudaSuccess) return false;
   if (!hi && (cudaMemset(w->hi, 0, plane) != cudaSuccess || cudaMemset(w->lo, 0, plane) != cudaSuccess))
     return false;
   // this molecule's own maps (CAVV kernel, single-molecule CCVV)
@@ -775,7 +813,9 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
   md.nV = z.nV;
   md.nVpad = w->nVpad;
   md.row0 = 0;
-  md.kblocks = w->Qpad / w->kb_elems;
+  md.kq0 = TAIL_Q;
+  md.kblocks = (w->Qpad - TAIL_Q) / w->kb_elems;
+  md.tail = w->tail;
   md.n_tp = w->n_tp;
   md.alpha = w->alpha;
   md.pinfo = w->pinfo;
@@ -849,6 +889,7 @@ bool split_alloc(dsrg_plan* p) {
 int split_qpad(const dsrg_plan* p) { return p->split->Qpad; }
 int split_qld(const dsrg_plan* p) { return p->split->Qld; }
 void* split_plane_ptr(const dsrg_plan* p, bool hi) { return hi ? p->split->hi : p->split->lo; }
+const float* split_tail_ptr(const dsrg_plan* p) { return p->split->tail; }
 
 const CUtensorMap* split_map(const dsrg_plan* p, bool hi) {
   return hi ? &p->split->map_hi : &p->split->map_lo;
@@ -871,9 +912,11 @@ cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double
   {
     dim3 grid(w->Qpad / 64, w->nVpad / 64, z.nH);
     if (bf16)
-      split_planes_kernel<true><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
+      split_planes_kernel<true><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
+                                                             w->tail);
     else
-      split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo);
+      split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
+                                                              w->tail);
     DSRG_LAUNCH_CHECK(p);
   }
   {
@@ -900,7 +943,9 @@ void split_fill_mol_desc(const dsrg_plan* p, long long row0, void* out) {
   md.nV = p->z.nV;
   md.nVpad = w->nVpad;
   md.row0 = (int)row0;
-  md.kblocks = w->Qpad / w->kb_elems;
+  md.kq0 = TAIL_Q;
+  md.kblocks = (w->Qpad - TAIL_Q) / w->kb_elems;
+  md.tail = w->tail;
   md.n_tp = w->n_tp;
   md.alpha = w->alpha;
   md.pinfo = w->pinfo;
