@@ -412,7 +412,22 @@ dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const
   if (!out_host) return fail(p, DSRG_ERR_INVALID_ARG, "out_host must not be NULL");
   const Sizes& z = p->z;
   const size_t nb = (size_t)z.Q * z.nH * z.nP, ng = (size_t)z.nA * z.nA;
-  cudaError_t e = cudaMemcpyAsync(p->st_B, B_host, nb * 8, cudaMemcpyHostToDevice, p->stream);
+  // Split-precision plans whose CAVV/CCAV/active integrals come from the tensor-core
+  // GEMM read B exactly once, in the kernels that split it into planes. When B_host
+  // is page-locked (and so mapped for the GPU), those kernels read it in place over
+  // the host link instead of after a staging copy; pageable memory is copied.
+  const double* B_use = p->st_B;
+  cudaError_t e = cudaSuccess;
+  if (p->prec != DSRG_PREC_FP64 && p->rest_tc) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, B_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer && !((uintptr_t)at.devicePointer & 7u))
+      B_use = (const double*)at.devicePointer;
+    else
+      cudaGetLastError();  // an unregistered pointer is not an error here
+  }
+  if (B_use == p->st_B)
+    e = cudaMemcpyAsync(p->st_B, B_host, nb * 8, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->st_eps, eps_host, (size_t)z.n * 8, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && ng)
@@ -421,7 +436,7 @@ dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const
     e = cudaMemcpyAsync(p->st_l, lambda2_host, ng * ng * 8, cudaMemcpyHostToDevice, p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
   p->launches = 0;
-  st = run_energy(p, p->st_B, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+  st = run_energy(p, B_use, p->st_eps, p->st_g, p->st_l, s, p->st_out);
   if (st != DSRG_OK) return st;
   e = cudaMemcpyAsync(out_host, p->st_out, 5 * 8, cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

@@ -135,6 +135,24 @@ def test_host_io_entry_matches_device_entry(pkg):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+def test_host_io_entry_pinned_matches_device_entry(pkg, prec):
+    """Page-locked host inputs: split plans read B in place over the host link,
+    FP64 plans copy it; either way the result equals the device entry's bit for bit."""
+    import torch
+    p = make_problem(5, 2, 140, 70, s=0.5, seed=12)
+    plan = pkg.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, host_io=True)
+    dev = pkg.to_device(p)
+    a = plan.energy(*dev, p.s).cpu().numpy()
+    pinned = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+              for x in (p.B, p.eps, p.gamma1, p.lambda2)]
+    out = torch.zeros(5, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        out.zero_()
+        plan.energy_host(*pinned, p.s, out=out)
+        assert np.array_equal(a, out.numpy())
+
+
 def test_error_statuses(pkg):
     import torch
     from paper_1603_00561_gb300 import _native
