@@ -145,10 +145,11 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t *plan, const double *B, const d
  * inputs into plan-owned device staging (plan created with DSRG_PLAN_HOST_IO),
  * runs, copies the result back and waits for the stream. Pinned host memory
  * gives the fastest copies. For split-precision plans whose CAVV/CCAV/active
- * integrals come from the tensor-core GEMM, a page-locked B_host is not copied:
- * the kernels that split B into planes, the only readers of B in those plans,
- * read it in place over the host link (same values, same results). B_host must
- * then stay unchanged until the call returns, as for the copy. */
+ * integrals come from the tensor-core GEMM, B is copied in groups of core rows
+ * (up to eight, sized at plan creation) on a second stream owned by the plan, and the CCVV work of the pairs
+ * (i, j) whose larger index j lies in a group starts once that group has
+ * arrived, while the later groups are still being copied; the result is the
+ * same, bit for bit, as dsrg_mrpt2_energy's on the same inputs. */
 dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t *plan, const double *B_host,
                                      const double *eps_host, const double *gamma1_host,
                                      const double *lambda2_host, double s, double *out_host);

@@ -67,7 +67,55 @@ static dsrg_status_t cuda_fail(dsrg_plan* p, cudaError_t e, const char* where) {
   return fail(p, DSRG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Row groups of the host-buffer entry's copy/compute pipeline (split plans).
+// Group g's copy takes c per core row; its CCVV launch takes q per pair (i <= j)
+// with j in the group, plus a fixed o per launch, and starts when both the
+// previous launch and its own copy are done. The bounds minimise the finish time
+// of the last launch over at most HOST_IO_MAX_GROUPS groups (dynamic program over
+// the last row of each group). The rates are rough estimates (host link about
+// 200 GB/s, tensor cores about 1 PFLOP/s on the three split products); they only
+// place the group bounds, never the result.
+constexpr int HOST_IO_MAX_GROUPS = 8;
+
+static std::vector<int> host_io_bounds(const Sizes& z) {
+  const int nC = z.nC;
+  const double c = (double)z.Q * z.nP * 8.0 / 200e9;
+  const double q = 6.0 * z.Q * (double)z.nV * z.nV / 1e15;
+  const double o = 120e-6;
+  const int G = nC < HOST_IO_MAX_GROUPS ? nC : HOST_IO_MAX_GROUPS;
+  const double inf = 1e300;
+  // t[g][h]: earliest finish of the launch of group g when it ends at row h
+  std::vector<std::vector<double>> t(G + 1, std::vector<double>(nC + 1, inf));
+  std::vector<std::vector<int>> from(G + 1, std::vector<int>(nC + 1, -1));
+  t[0][0] = 0.0;
+  auto pairs = [](int h0, int h1) {  // pairs i <= j with h0 <= j < h1
+    return 0.5 * ((double)h1 * (h1 + 1) - (double)h0 * (h0 + 1));
+  };
+  for (int g = 1; g <= G; ++g)
+    for (int h = g; h <= nC; ++h)
+      for (int h0 = g - 1; h0 < h; ++h0) {
+        if (t[g - 1][h0] >= inf) continue;
+        const double start = t[g - 1][h0] > c * h ? t[g - 1][h0] : c * h;
+        const double fin = start + q * pairs(h0, h) + o;
+        if (fin < t[g][h]) {
+          t[g][h] = fin;
+          from[g][h] = h0;
+        }
+      }
+  int best = 1;
+  for (int g = 2; g <= G; ++g)
+    if (t[g][nC] < t[best][nC]) best = g;
+  std::vector<int> b(best + 1);
+  b[best] = nC;
+  for (int g = best; g > 0; --g) b[g - 1] = from[g][b[g]];
+  return b;
+}
+
 static void free_all(dsrg_plan* p) {
+  for (cudaEvent_t ev : p->st_ev) cudaEventDestroy(ev);
+  p->st_ev.clear();
+  if (p->st_copy) cudaStreamDestroy(p->st_copy);
+  p->st_copy = nullptr;
   if (p->split) split_free(p);
   if (p->rest) rest_free(p);
   if (p->grad) grad_free(p);
@@ -198,6 +246,18 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
       p->st_g = p->st_eps + ne;
       p->st_l = p->st_g + ng;
       p->st_out = p->st_l + nl;
+    }
+    if (ok && p->rest_tc && !share) {
+      // pipeline of the host-buffer entry over groups of core rows
+      const std::vector<int> bounds = host_io_bounds(z);
+      const int ngroups = (int)bounds.size() - 1;
+      ok = cudaStreamCreateWithFlags(&p->st_copy, cudaStreamNonBlocking) == cudaSuccess;
+      for (int g = 0; ok && g < ngroups + 2; ++g) {
+        cudaEvent_t ev = nullptr;
+        ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) p->st_ev.push_back(ev);
+      }
+      ok = ok && split_alloc_groups(p, bounds);
     }
   }
   if (!ok) {
@@ -412,31 +472,56 @@ dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const
   if (!out_host) return fail(p, DSRG_ERR_INVALID_ARG, "out_host must not be NULL");
   const Sizes& z = p->z;
   const size_t nb = (size_t)z.Q * z.nH * z.nP, ng = (size_t)z.nA * z.nA;
-  // Split-precision plans whose CAVV/CCAV/active integrals come from the tensor-core
-  // GEMM read B exactly once, in the kernels that split it into planes. When B_host
-  // is page-locked (and so mapped for the GPU), those kernels read it in place over
-  // the host link instead of after a staging copy; pageable memory is copied.
-  const double* B_use = p->st_B;
-  cudaError_t e = cudaSuccess;
-  if (p->prec != DSRG_PREC_FP64 && p->rest_tc) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, B_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-        at.devicePointer && !((uintptr_t)at.devicePointer & 7u))
-      B_use = (const double*)at.devicePointer;
-    else
-      cudaGetLastError();  // an unregistered pointer is not an error here
-  }
-  if (B_use == p->st_B)
-    e = cudaMemcpyAsync(p->st_B, B_host, nb * 8, cudaMemcpyHostToDevice, p->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(p->st_eps, eps_host, (size_t)z.n * 8, cudaMemcpyHostToDevice, p->stream);
+  const int G = split_n_groups(p);
+  cudaError_t e = cudaMemcpyAsync(p->st_eps, eps_host, (size_t)z.n * 8, cudaMemcpyHostToDevice,
+                                  p->stream);
   if (e == cudaSuccess && ng)
     e = cudaMemcpyAsync(p->st_g, gamma1_host, ng * 8, cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && ng)
     e = cudaMemcpyAsync(p->st_l, lambda2_host, ng * ng * 8, cudaMemcpyHostToDevice, p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
   p->launches = 0;
-  st = run_energy(p, B_use, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+  if (G > 0 && p->st_copy) {
+    // Split plans: B goes over in groups of core rows on the copy stream, and the
+    // CCVV items of a group (pairs i <= j with j in the group) start as soon as
+    // its rows are staged, while later groups are still on the way. The partial
+    // sums and their reduction are those of dsrg_mrpt2_energy: same result bits.
+    const size_t pitch = (size_t)z.nH * z.nP * 8;
+    auto copy_rows = [&](int h0, int h1) {
+      return cudaMemcpy2DAsync(p->st_B + (size_t)h0 * z.nP, pitch, B_host + (size_t)h0 * z.nP,
+                               pitch, (size_t)(h1 - h0) * z.nP * 8, (size_t)z.Q,
+                               cudaMemcpyHostToDevice, p->st_copy);
+    };
+    // the copies must not overwrite st_B while work queued earlier still reads it
+    e = cudaEventRecord(p->st_ev[G + 1], p->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st_copy, p->st_ev[G + 1], 0);
+    for (int g = 0; e == cudaSuccess && g < G; ++g) {
+      int h0 = 0, h1 = 0;
+      split_group_rows(p, g, &h0, &h1);
+      e = copy_rows(h0, h1);
+      if (e == cudaSuccess) e = cudaEventRecord(p->st_ev[g], p->st_copy);
+    }
+    if (e == cudaSuccess && z.nH > z.nC) e = copy_rows(z.nC, z.nH);
+    if (e == cudaSuccess) e = cudaEventRecord(p->st_ev[G], p->st_copy);
+    if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
+    if ((e = split_stage_tables(p, p->st_eps, s)) == cudaSuccess)
+      e = split_prepare_single(p, p->st_eps, s);
+    for (int g = 0; e == cudaSuccess && g < G; ++g) {
+      int h0 = 0, h1 = 0;
+      split_group_rows(p, g, &h0, &h1);
+      e = cudaStreamWaitEvent(p->stream, p->st_ev[g], 0);
+      if (e == cudaSuccess) e = split_stage_rows(p, p->st_B, h0, h1);
+      if (e == cudaSuccess) e = split_launch_group(p, g);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->st_ev[G], 0);
+    if (e == cudaSuccess) e = split_stage_rows(p, p->st_B, z.nC, z.nH);
+    if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
+    st = run_rest(p, p->st_B, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+  } else {
+    e = cudaMemcpyAsync(p->st_B, B_host, nb * 8, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
+    st = run_energy(p, p->st_B, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+  }
   if (st != DSRG_OK) return st;
   e = cudaMemcpyAsync(out_host, p->st_out, 5 * 8, cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

@@ -100,6 +100,11 @@ struct dsrg_plan {
 
   // device staging of dsrg_mrpt2_energy_host (DSRG_PLAN_HOST_IO)
   double *st_B = nullptr, *st_eps = nullptr, *st_g = nullptr, *st_l = nullptr, *st_out = nullptr;
+  // split plans: B is copied in groups of core rows on st_copy while the CCVV
+  // items of the groups already staged run; st_ev[g] marks group g copied,
+  // st_ev[G] the active rows, st_ev[G + 1] the previous call done with st_B
+  cudaStream_t st_copy = nullptr;
+  std::vector<cudaEvent_t> st_ev;
 
   // device status word (bounded waits)
   int* d_status = nullptr;
@@ -169,6 +174,13 @@ int split_kb_elems(bool bf16);
 size_t split_mol_desc_bytes();
 void split_fill_mol_desc(const dsrg_plan* p, long long row0, void* out);
 cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double s);
+cudaError_t split_stage_rows(dsrg_plan* p, const double* B, int h0, int h1);
+cudaError_t split_stage_tables(dsrg_plan* p, const double* eps, double s);
+// host-buffer pipeline: CCVV items grouped by the core row j of their pair
+bool split_alloc_groups(dsrg_plan* p, const std::vector<int>& bounds);
+int split_n_groups(const dsrg_plan* p);
+void split_group_rows(const dsrg_plan* p, int g, int* h0, int* h1);
+cudaError_t split_launch_group(dsrg_plan* p, int g);
 cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols, int first, int n,
                              const double* const* eps, const double* s);
 cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,

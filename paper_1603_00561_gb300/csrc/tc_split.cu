@@ -66,6 +66,15 @@ struct SplitWs {
   int4* d_items = nullptr;  // single-molecule schedule
   int* d_begin = nullptr;
   int order = 0;            // item order of that schedule (split_item_list)
+  // The same items split by the core row j of their pair (i <= j) into groups of
+  // consecutive rows [h0, h1): a group's items read only rows < h1, so they can
+  // run as soon as those rows are staged (the host-buffer entry's pipeline).
+  struct Group {
+    int h0 = 0, h1 = 0, n = 0, grid = 0;
+    int4* d_items = nullptr;
+    int* d_begin = nullptr;
+  };
+  std::vector<Group> groups;
 };
 
 // One molecule of a (possibly batched) CCVV launch.
@@ -513,9 +522,9 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
                                                            int nVpad, int Qld,
                                                            void* __restrict__ hi,
                                                            void* __restrict__ lo,
-                                                           float* __restrict__ tail) {
+                                                           float* __restrict__ tail, int h0) {
   __shared__ double t[64][65];
-  const int q0 = blockIdx.x * 64, a0 = blockIdx.y * 64, h = blockIdx.z;
+  const int q0 = blockIdx.x * 64, a0 = blockIdx.y * 64, h = h0 + blockIdx.z;
   for (int k = threadIdx.x; k < 64 * 64; k += 256) {
     const int r = k >> 6, c = k & 63;
     const int q = q0 + r, a = a0 + c;
@@ -848,8 +857,71 @@ cudaError_t split_set_order(dsrg_plan* p, int order) {
   cudaError_t e = cudaMemcpy(w->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(w->d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice);
+  for (SplitWs::Group& g : w->groups) {
+    if (e != cudaSuccess) break;
+    std::vector<int4> gi;
+    std::vector<double> gc;
+    for (size_t k = 0; k < items.size(); ++k) {
+      const int j = items[k].y & 0xffff;
+      if (j >= g.h0 && j < g.h1) {
+        gi.push_back(items[k]);
+        gc.push_back(cost[k]);
+      }
+    }
+    split_schedule(gi, gc, g.grid, sched, begin);
+    e = cudaMemcpy(g.d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g.d_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) w->order = order;
   return e;
+}
+
+// Split the core rows into groups of consecutive rows for the host-buffer
+// pipeline (bounds[0] = 0 < ... < bounds.back() = nC) and build their schedules
+// (item order of the plan).
+bool split_alloc_groups(dsrg_plan* p, const std::vector<int>& bounds) {
+  SplitWs* w = p->split;
+  const int ngroups = (int)bounds.size() - 1;
+  if (ngroups < 1) return true;
+  int nsm = 148;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
+  std::vector<int4> items;
+  std::vector<double> cost;
+  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, 0);
+  w->groups.resize(ngroups);
+  for (int g = 0; g < ngroups; ++g) {
+    SplitWs::Group& G = w->groups[g];
+    G.h0 = bounds[g];
+    G.h1 = bounds[g + 1];
+    G.n = 0;
+    for (const int4& it : items) {
+      const int j = it.y & 0xffff;
+      G.n += (j >= G.h0 && j < G.h1) ? 1 : 0;
+    }
+    G.grid = G.n < nsm ? G.n : nsm;
+    if (G.n == 0) continue;
+    if (!plan_alloc(p, (void**)&G.d_items, (size_t)G.n * sizeof(int4)) ||
+        !plan_alloc(p, (void**)&G.d_begin, (size_t)(G.grid + 1) * sizeof(int)))
+      return false;
+  }
+  return split_set_order(p, w->order) == cudaSuccess;
+}
+
+int split_n_groups(const dsrg_plan* p) { return p->split ? (int)p->split->groups.size() : 0; }
+
+void split_group_rows(const dsrg_plan* p, int g, int* h0, int* h1) {
+  *h0 = p->split->groups[g].h0;
+  *h1 = p->split->groups[g].h1;
+}
+
+// The CCVV items of row group g (planes of rows < its h1 and the tables staged).
+cudaError_t split_launch_group(dsrg_plan* p, int g) {
+  SplitWs* w = p->split;
+  const SplitWs::Group& G = w->groups[g];
+  if (G.n == 0) return cudaSuccess;
+  return split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, G.d_items, G.d_begin, G.grid,
+                           p->prec == DSRG_PREC_BF16X3, w->order >> 16);
 }
 
 int split_order(const dsrg_plan* p) { return p->split ? p->split->order : -1; }
@@ -904,28 +976,37 @@ static size_t split_smem_bytes() {
   return (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (2 * TT + EPI_WARPS) * 8 + TT * 4 + 64;
 }
 
-// Stage this molecule's planes and pair tables (no CCVV launch).
-cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double s) {
+// Planes (and FP32 tail rows) of the hole rows h0 <= h < h1 of B.
+cudaError_t split_stage_rows(dsrg_plan* p, const double* B, int h0, int h1) {
   SplitWs* w = p->split;
   const Sizes& z = p->z;
-  const bool bf16 = p->prec == DSRG_PREC_BF16X3;
-  {
-    dim3 grid(w->Qpad / 64, w->nVpad / 64, z.nH);
-    if (bf16)
-      split_planes_kernel<true><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
-                                                             w->tail);
-    else
-      split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
-                                                              w->tail);
-    DSRG_LAUNCH_CHECK(p);
-  }
-  {
-    const size_t n = (size_t)p->n_pairs * w->nVpad + (size_t)w->nVpad * w->nVpad + w->nT;
-    split_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
-        eps, s, z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange);
-    DSRG_LAUNCH_CHECK(p);
-  }
+  if (h1 <= h0) return cudaSuccess;
+  dim3 grid(w->Qpad / 64, w->nVpad / 64, h1 - h0);
+  if (p->prec == DSRG_PREC_BF16X3)
+    split_planes_kernel<true><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
+                                                           w->tail, h0);
+  else
+    split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
+                                                            w->tail, h0);
+  DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
+}
+
+// Pair tables of the regulator (they read eps only).
+cudaError_t split_stage_tables(dsrg_plan* p, const double* eps, double s) {
+  SplitWs* w = p->split;
+  const size_t n = (size_t)p->n_pairs * w->nVpad + (size_t)w->nVpad * w->nVpad + w->nT;
+  split_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
+      eps, s, p->z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange);
+  DSRG_LAUNCH_CHECK(p);
+  return cudaSuccess;
+}
+
+// Stage this molecule's planes and pair tables (no CCVV launch).
+cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double s) {
+  cudaError_t e = split_stage_rows(p, B, 0, p->z.nH);
+  if (e == cudaSuccess) e = split_stage_tables(p, eps, s);
+  return e;
 }
 
 size_t split_mol_desc_bytes() { return sizeof(MolDesc); }

@@ -135,12 +135,16 @@ def test_host_io_entry_matches_device_entry(pkg):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
-def test_host_io_entry_pinned_matches_device_entry(pkg, prec):
-    """Page-locked host inputs: split plans read B in place over the host link,
-    FP64 plans copy it; either way the result equals the device entry's bit for bit."""
+@pytest.mark.parametrize("prec,nC,nV,Q", [("bf16x3", 5, 140, 70), ("bf16x3", 12, 298, 4000),
+                                          ("tf32x3", 24, 600, 2000), ("fp64", 5, 140, 70)])
+def test_host_io_entry_pinned_matches_device_entry(pkg, prec, nC, nV, Q):
+    """Page-locked host inputs: split plans copy B in groups of core rows while
+    the CCVV work of the groups already copied runs (one group for the small
+    case; three and five for the larger two, whose copy time is comparable to
+    their CCVV time); FP64 plans copy it whole. Either way the result equals the
+    device entry's bit for bit, call after call."""
     import torch
-    p = make_problem(5, 2, 140, 70, s=0.5, seed=12)
+    p = make_problem(nC, 2, nV, Q, s=0.5, seed=12)
     plan = pkg.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, host_io=True)
     dev = pkg.to_device(p)
     a = plan.energy(*dev, p.s).cpu().numpy()
