@@ -400,8 +400,9 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
   extern __shared__ float f2s[];
   float* sX = f2s;                              // [NA][32][33]   X_u[e,f]
   float* sXt = sX + NA * F2_T * (F2_T + 1);     // [NA][32][33]   X_u[f,e]
-  __shared__ double sAe[NA][F2_T], sAf[NA][F2_T], sEe[F2_T], sEf[F2_T], sG[NA * NA];
-  __shared__ double sE[NA], sBeta[NA];
+  // sBAe = beta_u * alpha_u(e): the row factor of exp(-s D^2) with the pair factor folded in
+  __shared__ double sBAe[NA][F2_T], sAf[NA][F2_T], sEe[F2_T], sEf[F2_T], sG[NA * NA];
+  __shared__ double sE[NA];
   __shared__ int sFact, sFar;
   __shared__ double red[8];
   const int m = blockIdx.x / n_tp;
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
 #pragma unroll
     for (int u = 0; u < NA; ++u) {
       const double* al = alpha + (size_t)(m * z.nA + u) * nVpad;
-      sAe[u][t] = al[E0 + t];
+      sBAe[u][t] = pinfo[4 * (m * z.nA + u) + 1] * al[E0 + t];
       sAf[u][t] = al[F0 + t];
     }
   }
@@ -431,7 +432,6 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
     int fact = 1;
     for (int u = 0; u < NA; ++u) {
       sE[u] = pinfo[4 * (m * z.nA + u)];
-      sBeta[u] = pinfo[4 * (m * z.nA + u) + 1];
       fact = fact && (pinfo[4 * (m * z.nA + u) + 2] != 0.0);
     }
     sFact = fact;
@@ -466,15 +466,17 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
       if (e >= z.nV) break;
       const double tau = (fact && !tile_far) ? tau1[(size_t)e * nVpad + f] : 0.0;
       const double eef = sEe[r] + sEf[c];
-      double Rv[NA], Rt[NA];
-      float X[NA], Xt[NA];
+      double Rv[NA], Rt[NA], Dd[NA];
+      float X[NA], Xt[NA], Df[NA];
       bool far = fact;
 #pragma unroll
       for (int u = 0; u < NA; ++u) {
         X[u] = sX[(u * F2_T + r) * (F2_T + 1) + c];
         Xt[u] = sXt[(u * F2_T + r) * (F2_T + 1) + c];
-        const double D = sE[u] - eef;
-        far = far && fabs(D) >= 0.25;
+        Dd[u] = sE[u] - eef;
+        Df[u] = (float)Dd[u];
+        // the threshold is not sharp (both paths are accurate near it): FP32 compare
+        far = far && fabsf(Df[u]) >= 0.25f;
       }
       if (far || tile_far) {
         // every D_u away from 0: FP64 regulators (from the factor tables, or
@@ -482,10 +484,10 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
         // exchange combination Q_uv = X_u (2 X_v - Xt_v) [+ mirror] in FP32
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
-          const double D = sE[u] - eef;
-          const double g = tile_far ? 0.0 : sBeta[u] * sAe[u][r] * sAf[u][c] * tau;
+          const double D = Dd[u];
+          const double g = tile_far ? 0.0 : sBAe[u][r] * sAf[u][c] * tau;
           float r0f;
-          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(Df[u]));
           const double r0 = (double)r0f;
           const double en = fma(-D, r0, 1.0);
           const double R0 = fma(-g, r0, r0);
@@ -510,9 +512,8 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
         // and the exchange combination in FP64
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
-          const double D = sE[u] - eef;
-          Rt[u] = reg_t(D, s);
-          Rv[u] = reg_v(D, s);
+          Rt[u] = reg_t(Dd[u], s);
+          Rv[u] = reg_v(Dd[u], s);
         }
         double t1 = 0.0, t2 = 0.0;
 #pragma unroll
