@@ -850,6 +850,7 @@ __global__ void __launch_bounds__(TERM_NT) terms_kernel(Sizes z, TermArgs t,
   __shared__ double red[TERM_NT / 32];
   const ActDims d = act_dims(z);
   const int term = blockIdx.y;
+  if (term == T_F6 || term == T_F7) return;  // term_f6_kernel, term_f7_kernel
   const long n = term_count(term, d);
   double v = 0.0;
   for (long o = (long)blockIdx.x * TERM_NT + threadIdx.x; o < n; o += (long)gridDim.x * TERM_NT)
@@ -859,6 +860,130 @@ __global__ void __launch_bounds__(TERM_NT) terms_kernel(Sizes z, TermArgs t,
 }
 
 static int term_blocks(const Sizes&) { return TERM_BLOCKS; }
+
+// Terms F6 and F7 (Table 2) factorised. Their sums over spin orbitals are
+// contractions of small active-index tensors with the spin-diagonal gamma and
+// eta, so per virtual (and core) index they are evaluated as chains of matrix
+// products in shared memory instead of one nested loop per output entry:
+//   F7 = 1/2 sum_E sum_{Y,Z,V} vt[Y,Z,V] S3[Y,Z,V],   vt[Y,Z,V] = Vt_{yz}^{ve},
+//        S1[W,X,V] = sum_U t[W,X,U] eta_v^u,  t[W,X,U] = T_{wx}^{ue},
+//        S2[W,Z,V] = sum_X gamma_x^z S1[W,X,V],  S3[Y,Z,V] = sum_W gamma_w^y S2[W,Z,V];
+//   F6 = sum_{M,E} sum_{X,V} vt[X,V] Q[X,V],   vt[X,V] = Vt_{mx}^{ve},
+//        P[X,U] = sum_Y gamma_y^x T_{my}^{ue},  Q[X,V] = sum_U P[X,U] eta_v^u.
+// gamma and eta vanish between spin orbitals of different spin, so each sum runs
+// over the nA orbitals of one spin. The CTA count and partial slots are those of
+// terms_kernel (TERM_BLOCKS per term), which skips these two terms.
+template <int NA>
+__global__ void __launch_bounds__(TERM_NT) term_f7_kernel(Sizes z, TermArgs t,
+                                                          double* __restrict__ partials) {
+  constexpr int A2 = 2 * NA, A3 = A2 * A2 * A2;
+  extern __shared__ double f7s[];
+  double* sa = f7s;        // [A3]
+  double* sb = f7s + A3;   // [A3]
+  __shared__ double sg[A2 * A2], se[A2 * A2], red[TERM_NT / 32];
+  const ActDims d = act_dims(z);
+  const int C2 = d.nC2;
+  for (int k = threadIdx.x; k < A2 * A2; k += TERM_NT) {
+    sg[k] = t.gA[k];
+    se[k] = ((k / A2) == (k % A2) ? 1.0 : 0.0) - t.gA[k];
+  }
+  double acc = 0.0;
+  for (int e = blockIdx.x; e < d.nV2; e += gridDim.x) {
+    const int Ap = A2 + e;
+    __syncthreads();
+    for (int k = threadIdx.x; k < A3; k += TERM_NT) {  // t[W,X,U], U fastest
+      const int U = k % A2, X = (k / A2) % A2, W = k / (A2 * A2);
+      sa[k] = t.W1T[w1i(d, C2 + W, X, Ap, U)];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < A3; k += TERM_NT) {  // S1[W,X,V] = sum_U t[W,X,U] eta[U,V]
+      const int V = k % A2, WX = k / A2;
+      double v = 0.0;
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        const int U = 2 * u + (V & 1);
+        v = fma(sa[WX * A2 + U], se[U * A2 + V], v);
+      }
+      sb[k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < A3; k += TERM_NT) {  // S2[W,Z,V] = sum_X gamma[Z,X] S1[W,X,V]
+      const int V = k % A2, Z = (k / A2) % A2, W = k / (A2 * A2);
+      double v = 0.0;
+#pragma unroll
+      for (int x = 0; x < NA; ++x) {
+        const int X = 2 * x + (Z & 1);
+        v = fma(sg[Z * A2 + X], sb[(W * A2 + X) * A2 + V], v);
+      }
+      sa[k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < A3; k += TERM_NT) {  // vt[Y,Z,V] * sum_W gamma[Y,W] S2[W,Z,V]
+      const int V = k % A2, Z = (k / A2) % A2, Y = k / (A2 * A2);
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < NA; ++w) {
+        const int W = 2 * w + (Y & 1);
+        v = fma(sg[Y * A2 + W], sa[(W * A2 + Z) * A2 + V], v);
+      }
+      acc = fma(t.W1Vt[w1i(d, C2 + Y, Z, Ap, V)], v, acc);
+    }
+  }
+  const double tot = block_sum<TERM_NT>(0.5 * acc, red);
+  if (threadIdx.x == 0) partials[(size_t)T_F7 * gridDim.x + blockIdx.x] = tot;
+}
+
+template <int NA>
+__global__ void __launch_bounds__(TERM_NT) term_f6_kernel(Sizes z, TermArgs t,
+                                                          double* __restrict__ partials) {
+  constexpr int A2 = 2 * NA, NW = TERM_NT / 32;
+  __shared__ double sT[NW][A2 * A2], sP[NW][A2 * A2];
+  __shared__ double sg[A2 * A2], se[A2 * A2], red[NW];
+  const ActDims d = act_dims(z);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < A2 * A2; k += TERM_NT) {
+    sg[k] = t.gA[k];
+    se[k] = ((k / A2) == (k % A2) ? 1.0 : 0.0) - t.gA[k];
+  }
+  __syncthreads();
+  double acc = 0.0;
+  const long n = (long)d.nC2 * d.nV2;
+  for (long me = (long)blockIdx.x * NW + warp; me < n; me += (long)gridDim.x * NW) {
+    const int M = (int)(me / d.nV2), Ap = A2 + (int)(me % d.nV2);
+    for (int k = lane; k < A2 * A2; k += 32)  // T[Y,U] = T_{my}^{ue}
+      sT[warp][k] = t.W1T[w1i(d, M, k / A2, Ap, k % A2)];
+    __syncwarp();
+    for (int k = lane; k < A2 * A2; k += 32) {  // P[X,U] = sum_Y gamma[X,Y] T[Y,U]
+      const int X = k / A2, U = k % A2;
+      double v = 0.0;
+#pragma unroll
+      for (int y = 0; y < NA; ++y) {
+        const int Y = 2 * y + (X & 1);
+        v = fma(sg[X * A2 + Y], sT[warp][Y * A2 + U], v);
+      }
+      sP[warp][k] = v;
+    }
+    __syncwarp();
+    for (int k = lane; k < A2 * A2; k += 32) {  // vt[X,V] * sum_U P[X,U] eta[U,V]
+      const int X = k / A2, V = k % A2;
+      double v = 0.0;
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        const int U = 2 * u + (V & 1);
+        v = fma(sP[warp][X * A2 + U], se[U * A2 + V], v);
+      }
+      acc = fma(t.W1Vt[w1i(d, M, X, Ap, V)], v, acc);
+    }
+    __syncwarp();
+  }
+  const double tot = block_sum<TERM_NT>(acc, red);
+  if (threadIdx.x == 0) partials[(size_t)T_F6 * gridDim.x + blockIdx.x] = tot;
+}
+
+static size_t f7_smem_bytes(int nA) {
+  const size_t a2 = 2 * (size_t)nA;
+  return 2 * a2 * a2 * a2 * sizeof(double);
+}
 
 bool active_alloc(dsrg_plan* p) {
   const Sizes& z = p->z;
@@ -983,6 +1108,21 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     const Segment& sg = p->segs[p->seg_active[0]];
     dim3 grid(term_blocks(z), N_TERMS);
     terms_kernel<<<grid, TERM_NT, 0, st>>>(z, ta, p->d_partials + sg.begin);
+    DSRG_LAUNCH_CHECK(p);
+    const size_t smf7 = f7_smem_bytes(z.nA);
+#define F67_LAUNCH(NA_)                                                                        \
+  case NA_:                                                                                    \
+    raise_smem_limit((const void*)term_f7_kernel<NA_>, smf7);                                  \
+    term_f7_kernel<NA_><<<term_blocks(z), TERM_NT, smf7, st>>>(z, ta, p->d_partials + sg.begin); \
+    DSRG_LAUNCH_CHECK(p);                                                                      \
+    term_f6_kernel<NA_><<<term_blocks(z), TERM_NT, 0, st>>>(z, ta, p->d_partials + sg.begin);   \
+    break;
+    switch (z.nA) {
+      F67_LAUNCH(1) F67_LAUNCH(2) F67_LAUNCH(3) F67_LAUNCH(4)
+      F67_LAUNCH(5) F67_LAUNCH(6) F67_LAUNCH(7) F67_LAUNCH(8)
+      default: return cudaErrorInvalidValue;
+    }
+#undef F67_LAUNCH
     DSRG_LAUNCH_CHECK(p);
   }
   return cudaSuccess;
