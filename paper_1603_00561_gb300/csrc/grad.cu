@@ -19,6 +19,8 @@
 //  F3: dE/dZ_w = Rv_w sum_u Hh_wu (2 Z_u - Z_u^T) Rt_u + Rt_w sum_v Hh_vw Rv_v (2 Z_v - Z_v^T)
 //  active block: reverse pass through the term sums, T1 / modified Fock, the
 //      dressed T of term I, the (A,A|V,V) spin sums and the spin-orbital tables.
+#include <type_traits>
+
 #include "internal.cuh"
 #include "regulators.cuh"
 
@@ -80,6 +82,9 @@ struct GemmArgs {
   int accumulate;
   int nb;                // independent problems in one launch (blockIdx.z);
   long long sa, sb, sc;  // their offsets of A, Bm, C
+  // FP32 copies of A and Bm (same element offsets) for the FP32 GEMM, or null
+  const float* A32;
+  const float* B32;
 };
 
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
@@ -143,11 +148,16 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
 // tiles are read along whichever index is contiguous in memory.
 constexpr int SG_T = 128, SG_K = 16;
 
+// FA / FB: the A / Bm operand is read from its FP32 copy (A32 / B32), which
+// holds the same values the FP64 operand rounds to when staged.
+template <bool FA, bool FB>
 __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
   __shared__ __align__(16) float sA[SG_K][SG_T + 4];
   __shared__ __align__(16) float sB[SG_K][SG_T + 4];
-  g.A += blockIdx.z * g.sa;
-  g.Bm += blockIdx.z * g.sb;
+  const double* Ad = g.A + blockIdx.z * g.sa;
+  const double* Bd = g.Bm + blockIdx.z * g.sb;
+  const float* Af = FA ? g.A32 + blockIdx.z * g.sa : nullptr;
+  const float* Bf = FB ? g.B32 + blockIdx.z * g.sb : nullptr;
   g.C += blockIdx.z * g.sc;
   const int i0 = blockIdx.y * SG_T, j0 = blockIdx.x * SG_T;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -164,33 +174,34 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
       c = e % SG_T;
     }
   };
-  // raw FP64 values of the next chunk: converted only when stored to shared
-  // memory, so the loads stay in flight during this chunk's FMAs
-  double ra_next[8], rb_next[8];
+  // raw values of the next chunk: converted (FP64 operands) only when stored to
+  // shared memory, so the loads stay in flight during this chunk's FMAs
+  typename std::conditional<FA, float, double>::type ra_next[8];
+  typename std::conditional<FB, float, double>::type rb_next[8];
   auto fetch = [&](unsigned l0) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       int ll, c;
       kc(a_kfast, t, ll, c);
       const unsigned l = l0 + ll;
-      double v = 0.0;
+      ra_next[t] = 0;
       if (l < L && i0 + c < g.M) {
         const unsigned l1 = l / L2, l2 = l - l1 * L2;
-        v = g.A[(long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2];
+        const long long o = (long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2;
+        if constexpr (FA) ra_next[t] = Af[o]; else ra_next[t] = Ad[o];
       }
-      ra_next[t] = v;
     }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       int ll, c;
       kc(b_kfast, t, ll, c);
       const unsigned l = l0 + ll;
-      double v = 0.0;
+      rb_next[t] = 0;
       if (l < L && j0 + c < g.N) {
         const unsigned l1 = l / L2, l2 = l - l1 * L2;
-        v = g.Bm[(long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj];
+        const long long o = (long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj;
+        if constexpr (FB) rb_next[t] = Bf[o]; else rb_next[t] = Bd[o];
       }
-      rb_next[t] = v;
     }
   };
   auto stash = [&]() {
@@ -203,6 +214,9 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
       sB[ll][c] = (float)rb_next[t];
     }
   };
+  // thread (tx, ty) owns rows {4ty..4ty+3, 64+4ty..64+4ty+3} and the same
+  // columns with tx: each fragment load reads 16 consecutive float4 (no bank
+  // conflicts) and is a broadcast across the lanes that share it
   float acc[8][8];
 #pragma unroll
   for (int r = 0; r < 8; ++r)
@@ -215,10 +229,10 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
     if (l0 + SG_K < L) fetch(l0 + SG_K);  // next chunk's loads overlap this chunk's FMAs
 #pragma unroll 4
     for (int ll = 0; ll < SG_K; ++ll) {
-      const float4 a0 = *(const float4*)&sA[ll][ty * 8];
-      const float4 a1 = *(const float4*)&sA[ll][ty * 8 + 4];
-      const float4 b0 = *(const float4*)&sB[ll][tx * 8];
-      const float4 b1 = *(const float4*)&sB[ll][tx * 8 + 4];
+      const float4 a0 = *(const float4*)&sA[ll][ty * 4];
+      const float4 a1 = *(const float4*)&sA[ll][64 + ty * 4];
+      const float4 b0 = *(const float4*)&sB[ll][tx * 4];
+      const float4 b1 = *(const float4*)&sB[ll][64 + tx * 4];
       const float ra[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float rb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -230,16 +244,38 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
   }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    const int i = i0 + ty * 8 + r;
+    const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
     if (i >= g.M) continue;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const int j = j0 + tx * 8 + c;
+      const int j = j0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + c - 4);
       if (j >= g.N) continue;
       double* p = g.C + (long long)i * g.ci + (long long)j * g.cj;
       *p = g.accumulate ? fma(g.alpha, (double)acc[r][c], *p) : g.alpha * (double)acc[r][c];
     }
   }
+}
+
+// Gradient workspace (DSRG_PLAN_GRAD).
+struct GradWs {
+  double* Wk = nullptr;   // [kgroup][nC][nVp][nVp]
+  int nVp = 0;
+  int kgroup = 1;         // core rows whose W^{kj} are formed before one batched GEMM
+  double* V = nullptr;    // [kgroup][nV][nC*nP] pair blocks v^{kj} (split plans)
+  float* B32 = nullptr;   // [naux][nH][nP] fl32 of the call's B (split plans), read by the GEMMs
+  const double* Bsrc = nullptr;  // the call's B, whose FP32 copy B32 holds
+  size_t nB = 0;          // elements of B
+  double* dX = nullptr;   // [nC][nA][nV][nV]
+  double* dZ = nullptr;   // [nA][nC][nC][nV]
+  double *dW1Vt = nullptr, *dW1T = nullptr, *dTi = nullptr, *dV1 = nullptr;
+  double *dW2Vt = nullptr, *dW2T = nullptr, *dV2 = nullptr;
+  double *dt1 = nullptr, *dft = nullptr, *dS = nullptr, *dP12 = nullptr;
+  double *dK1 = nullptr, *dK2 = nullptr, *dK3 = nullptr, *dM = nullptr;
+};
+
+__global__ void to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = (float)x[k];
 }
 
 // FP64 plans: FP64 GEMM; split-precision plans: FP32 GEMM.
@@ -249,8 +285,21 @@ static cudaError_t gemm(dsrg_plan* p, const GemmArgs& g) {
     dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.nb);
     gemm_fp64_kernel<<<grid, 256, 0, p->stream>>>(g);
   } else {
+    // operands that lie in the call's B are read from its FP32 copy
+    GemmArgs h = g;
+    const GradWs* w = p->grad;
+    auto in_b = [&](const double* x) { return w->B32 && x >= w->Bsrc && x < w->Bsrc + w->nB; };
+    if (!h.A32) h.A32 = in_b(g.A) ? w->B32 + (g.A - w->Bsrc) : nullptr;
+    if (!h.B32) h.B32 = in_b(g.Bm) ? w->B32 + (g.Bm - w->Bsrc) : nullptr;
     dim3 grid((g.N + SG_T - 1) / SG_T, (g.M + SG_T - 1) / SG_T, g.nb);
-    gemm_f32_kernel<<<grid, 256, 0, p->stream>>>(g);
+    if (h.A32 && h.B32)
+      gemm_f32_kernel<true, true><<<grid, 256, 0, p->stream>>>(h);
+    else if (h.A32)
+      gemm_f32_kernel<true, false><<<grid, 256, 0, p->stream>>>(h);
+    else if (h.B32)
+      gemm_f32_kernel<false, true><<<grid, 256, 0, p->stream>>>(h);
+    else
+      gemm_f32_kernel<false, false><<<grid, 256, 0, p->stream>>>(h);
   }
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
@@ -368,10 +417,13 @@ __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict_
 // this kernel forms W^{kj} and the eps / s derivatives exactly as the
 // epilogue of ccvv_adj_kernel, reading x = v^{kj}_ab and y = v^{kj}_ba through
 // two 64 x 64 shared-memory tiles. Grid: (group row, j, tile pair A <= B).
+// W is written in TW: FP32 for the FP32 GEMM that consumes it (the rounding that
+// GEMM would apply when staging an FP64 W).
+template <typename TW>
 __global__ void __launch_bounds__(256) ccvv_adj_w_kernel(const double* __restrict__ V,
                                                          const double* __restrict__ eps, double s,
                                                          Sizes z, int k0, const int2* __restrict__ tps,
-                                                         int n_tp, int nVp, double* __restrict__ W,
+                                                         int n_tp, int nVp, TW* __restrict__ W,
                                                          double* __restrict__ deps,
                                                          double* __restrict__ ds) {
   extern __shared__ double vsm[];
@@ -388,7 +440,7 @@ __global__ void __launch_bounds__(256) ccvv_adj_w_kernel(const double* __restric
   const int ve = z.nC + z.nA;
   const long long ldv = (long long)z.nC * z.nP;
   const double* Vk = V + (long long)kl * z.nV * ldv + (long long)j * z.nP + z.nA;
-  double* Wk = W + (long long)kl * z.nC * nVp * nVp;
+  TW* Wk = W + (long long)kl * z.nC * nVp * nVp;
   if (threadIdx.x < GT) {
     rowacc[threadIdx.x] = 0.0;
     colacc[threadIdx.x] = 0.0;
@@ -415,8 +467,8 @@ __global__ void __launch_bounds__(256) ccvv_adj_w_kernel(const double* __restric
       const double D = E - eps[ve + a] - eps[ve + b];
       const RegD R = rf1_d(D, s);
       const double xv = tX[al * (GT + 1) + bl], yv = tY[bl * (GT + 1) + al];
-      Wk[((size_t)j * nVp + a) * nVp + b] = (4.0 * xv - 2.0 * yv) * R.v;
-      if (mirror) Wk[((size_t)j * nVp + b) * nVp + a] = (4.0 * yv - 2.0 * xv) * R.v;
+      Wk[((size_t)j * nVp + a) * nVp + b] = (TW)((4.0 * xv - 2.0 * yv) * R.v);
+      if (mirror) Wk[((size_t)j * nVp + b) * nVp + a] = (TW)((4.0 * yv - 2.0 * xv) * R.v);
       const double q = fma(xv, xv - yv, yv * yv);
       dk = fma(2.0 * wt * q, R.dD, dk);
       dss = fma(wt * q, R.ds, dss);
@@ -1288,18 +1340,6 @@ __global__ void adj_m_generic_kernel(ActAdjArgs a, const double* __restrict__ dP
   if (dss != 0.0) atomicAdd(a.ds, dss);
 }
 
-struct GradWs {
-  double* Wk = nullptr;   // [kgroup][nC][nVp][nVp]
-  int nVp = 0;
-  int kgroup = 1;         // core rows whose W^{kj} are formed before one batched GEMM
-  double* V = nullptr;    // [kgroup][nV][nC*nP] pair blocks v^{kj} (split plans)
-  double* dX = nullptr;   // [nC][nA][nV][nV]
-  double* dZ = nullptr;   // [nA][nC][nC][nV]
-  double *dW1Vt = nullptr, *dW1T = nullptr, *dTi = nullptr, *dV1 = nullptr;
-  double *dW2Vt = nullptr, *dW2T = nullptr, *dV2 = nullptr;
-  double *dt1 = nullptr, *dft = nullptr, *dS = nullptr, *dP12 = nullptr;
-  double *dK1 = nullptr, *dK2 = nullptr, *dK3 = nullptr, *dM = nullptr;
-};
 
 bool grad_alloc(dsrg_plan* p) {
   const Sizes& z = p->z;
@@ -1314,6 +1354,8 @@ bool grad_alloc(dsrg_plan* p) {
   g->kgroup = (int)(kmax < 1 ? 1 : (kmax > (size_t)z.nC ? (size_t)z.nC : kmax));
   bool ok = plan_alloc(p, (void**)&g->Wk, per_w * g->kgroup);
   if (ok && split) ok = plan_alloc(p, (void**)&g->V, per_v * g->kgroup);
+  g->nB = (size_t)z.Q * z.nH * z.nP;
+  if (ok && split) ok = plan_alloc(p, (void**)&g->B32, g->nB * sizeof(float));
   if (z.nA > 0) {
     const size_t w1n = p->act.w1n, w2n = p->act.w2n;
     const size_t nHP2 = (size_t)4 * z.nH * z.nP;
@@ -1350,6 +1392,7 @@ static GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, 
   g.accumulate = 1;
   g.nb = 1;
   g.sa = g.sb = g.sc = 0;
+  g.A32 = g.B32 = nullptr;
   return g;
 }
 
@@ -1382,6 +1425,12 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
 
   // FP64 plans recompute in FP64, split-precision plans in FP32 (round to nearest)
   const bool fp64 = p->prec == DSRG_PREC_FP64;
+  if (!fp64) {
+    // fl32(B) once, for every GEMM that reads B (the same rounding as at staging)
+    w->Bsrc = B;
+    to_f32_kernel<<<(unsigned)((w->nB + 255) / 256), 256, 0, st>>>(B, w->B32, w->nB);
+    DSRG_LAUNCH_CHECK(p);
+  }
   // ---- F1: per core row k, W^{kj} then dB[:, k, V] += 2 sum_j B_j W^{kj T}
   const int n_tp = p->n_tp_ccvv;  // 64-wide tile pairs of the FP64 work list
   // rows k in groups of w->kgroup: W^{kj} of the group, then one batched GEMM
@@ -1404,15 +1453,17 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
       gv.accumulate = 0;
       if ((e = gemm(p, gv)) != cudaSuccess) return e;
       const size_t smw = (size_t)2 * GT * (GT + 1) * 8;
-      raise_smem_limit((const void*)ccvv_adj_w_kernel, smw);
-      ccvv_adj_w_kernel<<<kg * z.nC * n_tp, 256, smw, st>>>(w->V, eps, s, z, k0, p->d_tp_ccvv, n_tp,
-                                                            w->nVp, w->Wk, deps, ds);
+      // W in FP32 (the Wk buffer holds it at the same element offsets)
+      raise_smem_limit((const void*)ccvv_adj_w_kernel<float>, smw);
+      ccvv_adj_w_kernel<float><<<kg * z.nC * n_tp, 256, smw, st>>>(
+          w->V, eps, s, z, k0, p->d_tp_ccvv, n_tp, w->nVp, (float*)w->Wk, deps, ds);
       DSRG_LAUNCH_CHECK(p);
     }
-    e = gemm(p, batched(mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
-                           dB + (long long)k0 * z.nP + z.nA, HP, 1, 2.0),
-                        kg, 0, wstride, z.nP));
-    if (e != cudaSuccess) return e;
+    GemmArgs gw = batched(mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
+                             dB + (long long)k0 * z.nP + z.nA, HP, 1, 2.0),
+                          kg, 0, wstride, z.nP);
+    if (!fp64) gw.B32 = (const float*)w->Wk;
+    if ((e = gemm(p, gw)) != cudaSuccess) return e;
   }
   if (z.nA == 0) return cudaSuccess;
   const long long nV = z.nV, nV2 = nV * nV;
