@@ -125,31 +125,40 @@ __device__ __forceinline__ void tmem_ld_wait() {
 __device__ __forceinline__ void named_bar(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
+// Eight consecutive floats from global memory, read-only path (32-byte aligned).
+__device__ __forceinline__ void ldg8(const float* p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+        "=f"(v[7])
+      : "l"(p));
+}
+
 // x_ab += sum_{q < TAIL_Q} T_a[q] T_b[q] for the 16 columns b of one chunk, in
 // FP32 with round-to-nearest, q from the last to the first. T holds fl32(B) of
 // the first TAIL_Q auxiliary functions, one 128-byte row per plane row; `ra` is
 // this thread's row, `rb` the first of the chunk's 16 rows (the same for every
-// lane of the warp, so each load is a broadcast).
+// lane of the warp, so each load is a broadcast; 32-byte loads halve their count).
 __device__ __forceinline__ void tail_add16(const float* __restrict__ ra,
                                            const float* __restrict__ rb, uint32_t (&r)[16]) {
   float t[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) t[k] = 0.f;
-#pragma unroll 2
-  for (int q4 = TAIL_Q / 4 - 1; q4 >= 0; --q4) {
-    const float4 a4 = __ldg((const float4*)ra + q4);
+#pragma unroll 1
+  for (int q8 = TAIL_Q / 8 - 1; q8 >= 0; --q8) {
+    float a[8];
+    ldg8(ra + 8 * q8, a);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const float4 b4 = __ldg((const float4*)(rb + k * TAIL_Q) + q4);
-      t[k] = fmaf(a4.w, b4.w, t[k]);
-      t[k] = fmaf(a4.z, b4.z, t[k]);
-      t[k] = fmaf(a4.y, b4.y, t[k]);
-      t[k] = fmaf(a4.x, b4.x, t[k]);
+      float b[8];
+      ldg8(rb + k * TAIL_Q + 8 * q8, b);
+#pragma unroll
+      for (int i = 7; i >= 0; --i) t[k] = fmaf(a[i], b[i], t[k]);
     }
   }
 #pragma unroll
   for (int k = 0; k < 16; ++k) r[k] = __float_as_uint(__uint_as_float(r[k]) + t[k]);
 }
+
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows at a
 // 64-byte pitch (8-row groups 512 bytes apart).
 __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
