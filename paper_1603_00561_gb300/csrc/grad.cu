@@ -178,7 +178,24 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
   // shared memory, so the loads stay in flight during this chunk's FMAs
   typename std::conditional<FA, float, double>::type ra_next[8];
   typename std::conditional<FB, float, double>::type rb_next[8];
+  // K index l = l1 * L2 + l2: one division per chunk (l0 is the same for every
+  // thread), then each element steps from (l0 / L2, l0 % L2)
+  auto split_l = [&](unsigned l0, unsigned l1_0, unsigned l2_0, int ll, unsigned& l1,
+                     unsigned& l2) {
+    if (L2 == 1) {
+      l1 = l0 + ll;
+      l2 = 0;
+    } else {
+      l1 = l1_0;
+      l2 = l2_0 + ll;
+      while (l2 >= L2) {
+        l2 -= L2;
+        ++l1;
+      }
+    }
+  };
   auto fetch = [&](unsigned l0) {
+    const unsigned l1_0 = L2 == 1 ? l0 : l0 / L2, l2_0 = l0 - l1_0 * L2;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       int ll, c;
@@ -186,7 +203,8 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
       const unsigned l = l0 + ll;
       ra_next[t] = 0;
       if (l < L && i0 + c < g.M) {
-        const unsigned l1 = l / L2, l2 = l - l1 * L2;
+        unsigned l1, l2;
+        split_l(l0, l1_0, l2_0, ll, l1, l2);
         const long long o = (long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2;
         if constexpr (FA) ra_next[t] = Af[o]; else ra_next[t] = Ad[o];
       }
@@ -198,7 +216,8 @@ __global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
       const unsigned l = l0 + ll;
       rb_next[t] = 0;
       if (l < L && j0 + c < g.N) {
-        const unsigned l1 = l / L2, l2 = l - l1 * L2;
+        unsigned l1, l2;
+        split_l(l0, l1_0, l2_0, ll, l1, l2);
         const long long o = (long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj;
         if constexpr (FB) rb_next[t] = Bf[o]; else rb_next[t] = Bd[o];
       }
