@@ -46,9 +46,11 @@ __device__ __forceinline__ RegD rt_d(double D, double s) {
     r.v = s * D * (1.0 - 0.5 * x + x * x / 6.0);
     r.dD = s * (1.0 - 1.5 * x + 5.0 / 6.0 * x * x);
   } else {
-    const double em = expm1(-x);
-    r.v = -em / D;
-    r.dD = (2.0 * x * g + em) / (D * D);
+    // for x > 1/2, e^{-x} < 0.61 and e^{-x} - 1 has no cancellation: one exponential
+    const double em = x > 0.5 ? g - 1.0 : expm1(-x);
+    const double inv = 1.0 / D;
+    r.v = -em * inv;
+    r.dD = (2.0 * x * g + em) * inv * inv;
   }
   r.ds = D * g;
   return r;
