@@ -72,6 +72,7 @@ CASES = [
     (4, 3, 128, 33, 0.5, 4),     # exactly one tile; naux not a multiple of the K block
     (2, 8, 140, 70, 0.6, 5),     # the largest active space the kernels are built for (nA = 8)
     (3, 5, 33, 1, 0.5, 6),       # one auxiliary function; nV below one 32-wide F2 tile pair
+    (2, 2, 150, 32, 0.5, 7),     # exactly the FP32 tail: the tensor-core stages hold only padding
 ]
 
 
