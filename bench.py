@@ -41,20 +41,20 @@ NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # keyed by (workload, precision, item order); summaries under profiles/. Any
 # other combination, or a kernel changed since the capture, reports null.
 TRAFFIC = {
-    ("naphthyne-v5z-1240", "bf16x3", 0): 11509079424,
-    ("naphthyne-v5z-1240", "bf16x3", 4): 9611267392,
-    ("naphthyne-v5z-1240", "bf16x3", 8): 16070795776,
-    ("naphthyne-v5z-1240", "bf16x3", 16): 20557212608,
-    ("naphthyne-v5z-1240", "bf16x3", 9): 10886923776,
-    ("naphthyne-v5z-1240", "bf16x3", 17): 10934718528,
-    ("naphthyne-v5z-1240", "bf16x3", 128): 18659875200,
-    ("naphthyne-v5z-1240", "bf16x3", 262144): 23185906496,
-    ("naphthyne-v5z-1240", "bf16x3", 262148): 34937363072,
-    ("naphthyne-v5z-1240", "bf16x3", 262152): 46399879232,
-    ("naphthyne-v5z-1240", "bf16x3", 262160): 50292482688,
-    ("naphthyne-v5z-1240", "bf16x3", 262153): 33279151616,
-    ("naphthyne-v5z-1240", "bf16x3", 262161): 36398713728,
-    ("naphthyne-v5z-1240", "bf16x3", 262272): 36099204800,
+    ("naphthyne-v5z-1240", "bf16x3", 0): 12917796992,
+    ("naphthyne-v5z-1240", "bf16x3", 4): 7441687488,
+    ("naphthyne-v5z-1240", "bf16x3", 8): 14148086656,
+    ("naphthyne-v5z-1240", "bf16x3", 16): 18160743488,
+    ("naphthyne-v5z-1240", "bf16x3", 9): 10657107840,
+    ("naphthyne-v5z-1240", "bf16x3", 17): 12629118592,
+    ("naphthyne-v5z-1240", "bf16x3", 128): 20207734336,
+    ("naphthyne-v5z-1240", "bf16x3", 262144): 30338915328,
+    ("naphthyne-v5z-1240", "bf16x3", 262148): 37821449728,
+    ("naphthyne-v5z-1240", "bf16x3", 262152): 44162787776,
+    ("naphthyne-v5z-1240", "bf16x3", 262160): 49224539776,
+    ("naphthyne-v5z-1240", "bf16x3", 262153): 39407163776,
+    ("naphthyne-v5z-1240", "bf16x3", 262161): 38555878336,
+    ("naphthyne-v5z-1240", "bf16x3", 262272): 35005312896,
 }
 
 
