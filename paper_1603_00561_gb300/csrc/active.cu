@@ -851,6 +851,7 @@ __global__ void __launch_bounds__(TERM_NT) terms_kernel(Sizes z, TermArgs t,
   const ActDims d = act_dims(z);
   const int term = blockIdx.y;
   if (term == T_F6 || term == T_F7) return;  // term_f6_kernel, term_f7_kernel
+  if (term == T_I && z.nA <= 6) return;      // term_i_kernel
   const long n = term_count(term, d);
   double v = 0.0;
   for (long o = (long)blockIdx.x * TERM_NT + threadIdx.x; o < n; o += (long)gridDim.x * TERM_NT)
@@ -978,6 +979,69 @@ __global__ void __launch_bounds__(TERM_NT) term_f6_kernel(Sizes z, TermArgs t,
   }
   const double tot = block_sum<TERM_NT>(acc, red);
   if (threadIdx.x == 0) partials[(size_t)T_F6 * gridDim.x + blockIdx.x] = tot;
+}
+
+// Term I, vt_{jx}^{bu} Ti_{jv}^{by} lambda_{uv}^{xy} summed over (J, B, U, X, V, Y),
+// for nA <= 6: the spin-orbital cumulant is staged once per CTA in shared memory,
+// transposed to [V][Y][U][X] so that the lanes (consecutive X) read consecutive
+// entries, and the dressed Ti rows of TI_ROWS (J, B) pairs at a time beside it.
+constexpr int TI_ROWS = 8, TI_NT = 256;
+template <int NA>
+__global__ void __launch_bounds__(TI_NT) term_i_kernel(Sizes z, TermArgs t,
+                                                       double* __restrict__ partials) {
+  constexpr int A2 = 2 * NA, AA = A2 * A2, A4 = AA * AA;
+  extern __shared__ double ism[];
+  double* lamT = ism;       // [V][Y][U][X]
+  double* sTi = ism + A4;   // [TI_ROWS][V][Y]
+  __shared__ double red[TI_NT / 32];
+  const ActDims d = act_dims(z);
+  for (int k = threadIdx.x; k < A4; k += TI_NT) {
+    const int X = k % A2, U = (k / A2) % A2, Y = (k / AA) % A2, V = k / (AA * A2);
+    lamT[k] = t.lam[lami(d, U, V, X, Y)];
+  }
+  double acc = 0.0;
+  const long n = (long)d.nH2 * d.nP2;
+  for (long r0 = (long)blockIdx.x * TI_ROWS; r0 < n; r0 += (long)gridDim.x * TI_ROWS) {
+    __syncthreads();  // the previous rows' reads are done (and the cumulant is staged)
+    for (int k = threadIdx.x; k < TI_ROWS * AA; k += TI_NT) {
+      const long r = r0 + k / AA;
+      double v = 0.0;
+      if (r < n) {
+        const int J = (int)(r / d.nP2), Bp = (int)(r % d.nP2), V = (k % AA) / A2, Y = k % A2;
+        v = t.Ti[w1i(d, J, V, Bp, Y)];
+      }
+      sTi[k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < TI_ROWS * AA; k += TI_NT) {
+      const long r = r0 + k / AA;
+      if (r >= n) break;
+      const int J = (int)(r / d.nP2), Bp = (int)(r % d.nP2);
+      const int U = (k % AA) / A2, X = k % A2;
+      const double vt = t.W1Vt[w1i(d, J, X, Bp, U)];
+      if (vt == 0.0) continue;
+      const double* ti = sTi + (k / AA) * AA;
+      double c = 0.0;
+#pragma unroll
+      for (int V = 0; V < A2; ++V) {
+        const int sy = (U & 1) + (V & 1) - (X & 1);  // cumulant spin rule
+        if (sy < 0 || sy > 1) continue;
+#pragma unroll
+        for (int y = 0; y < NA; ++y) {
+          const int Y = 2 * y + sy;
+          c = fma(ti[V * A2 + Y], lamT[((V * A2 + Y) * A2 + U) * A2 + X], c);
+        }
+      }
+      acc = fma(vt, c, acc);
+    }
+  }
+  const double tot = block_sum<TI_NT>(acc, red);
+  if (threadIdx.x == 0) partials[(size_t)T_I * gridDim.x + blockIdx.x] = tot;
+}
+
+static size_t ti_smem_bytes(int nA) {
+  const size_t aa = 4 * (size_t)nA * nA;
+  return (aa * aa + TI_ROWS * aa) * sizeof(double);
 }
 
 static size_t f7_smem_bytes(int nA) {
@@ -1109,13 +1173,19 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     dim3 grid(term_blocks(z), N_TERMS);
     terms_kernel<<<grid, TERM_NT, 0, st>>>(z, ta, p->d_partials + sg.begin);
     DSRG_LAUNCH_CHECK(p);
-    const size_t smf7 = f7_smem_bytes(z.nA);
+    const size_t smf7 = f7_smem_bytes(z.nA), smti = ti_smem_bytes(z.nA);
 #define F67_LAUNCH(NA_)                                                                        \
   case NA_:                                                                                    \
     raise_smem_limit((const void*)term_f7_kernel<NA_>, smf7);                                  \
     term_f7_kernel<NA_><<<term_blocks(z), TERM_NT, smf7, st>>>(z, ta, p->d_partials + sg.begin); \
     DSRG_LAUNCH_CHECK(p);                                                                      \
     term_f6_kernel<NA_><<<term_blocks(z), TERM_NT, 0, st>>>(z, ta, p->d_partials + sg.begin);   \
+    if (NA_ <= 6) {                                                                            \
+      DSRG_LAUNCH_CHECK(p);                                                                    \
+      raise_smem_limit((const void*)term_i_kernel<(NA_ <= 6 ? NA_ : 6)>, smti);                \
+      term_i_kernel<(NA_ <= 6 ? NA_ : 6)><<<term_blocks(z), TI_NT, smti, st>>>(                \
+          z, ta, p->d_partials + sg.begin);                                                     \
+    }                                                                                          \
     break;
     switch (z.nA) {
       F67_LAUNCH(1) F67_LAUNCH(2) F67_LAUNCH(3) F67_LAUNCH(4)
