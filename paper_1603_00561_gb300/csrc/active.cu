@@ -1013,14 +1013,28 @@ __global__ void __launch_bounds__(TI_NT) term_i_kernel(Sizes z, TermArgs t,
       sTi[k] = v;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < TI_ROWS * AA; k += TI_NT) {
-      const long r = r0 + k / AA;
+    // only spin-allowed (U, X): vt_{jx}^{bu} conserves spin, s_J + s_X = s_B + s_U, so a
+    // row with s_J = s_B has 2 nA^2 pairs (U and X alike) and any other row nA^2
+    // (U of spin s_J, X of spin s_B)
+    constexpr int NUX = 2 * NA * NA;
+    for (int k = threadIdx.x; k < TI_ROWS * NUX; k += TI_NT) {
+      const long r = r0 + k / NUX;
       if (r >= n) break;
       const int J = (int)(r / d.nP2), Bp = (int)(r % d.nP2);
-      const int U = (k % AA) / A2, X = k % A2;
+      const int sJ = J & 1, sB = Bp & 1, m = k % NUX;
+      int U, X;
+      if (sJ == sB) {
+        const int mm = m % (NA * NA), sp = m / (NA * NA);
+        U = 2 * (mm / NA) + sp;
+        X = 2 * (mm % NA) + sp;
+      } else {
+        if (m >= NA * NA) continue;
+        U = 2 * (m / NA) + sJ;
+        X = 2 * (m % NA) + sB;
+      }
       const double vt = t.W1Vt[w1i(d, J, X, Bp, U)];
       if (vt == 0.0) continue;
-      const double* ti = sTi + (k / AA) * AA;
+      const double* ti = sTi + (k / NUX) * AA;
       double c = 0.0;
 #pragma unroll
       for (int V = 0; V < A2; ++V) {
