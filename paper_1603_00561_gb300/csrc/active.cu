@@ -22,6 +22,8 @@
 // spin input L: same spin L[u,v,x,y] - L[u,v,y,x]; (alpha beta|alpha beta)
 // L[u,v,x,y]; (beta alpha|beta alpha) L[v,u,y,x]; (alpha beta|beta alpha)
 // -L[u,v,y,x]; (beta alpha|alpha beta) -L[v,u,x,y].
+#include <type_traits>
+
 #include "internal.cuh"
 #include "regulators.cuh"
 
@@ -483,16 +485,20 @@ __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restri
 // each thread holding a fixed set of (p, q).
 constexpr int ACTVV_CH = 64;
 
-template <int NA>
+// F32 (split-precision plans): the regulated factors are rounded to FP32 and each
+// 64-term chunk of the sum over (e, f) runs in FP32 on CUDA cores (round to
+// nearest), the chunk sums in FP64; the regulators themselves stay FP64.
+template <int NA, bool F32>
 __global__ void __launch_bounds__(256) actvv_gen_kernel(const double* __restrict__ eps, double s,
                                                         Sizes z, const double* __restrict__ M,
                                                         ActFact F, double* __restrict__ part) {
+  using T = typename std::conditional<F32, float, double>::type;
   constexpr int NA2 = NA * NA, NA4 = NA2 * NA2;
   constexpr int PER = (NA4 + 255) / 256;  // (p,q) outputs per thread
   extern __shared__ double avs[];
-  double* sa = avs;                        // [NA2][CH]
-  double* sb = sa + NA2 * ACTVV_CH;        // [NA2][CH]
-  double* sc = sb + NA2 * ACTVV_CH;        // [NA2][CH]
+  T* sa = (T*)avs;                         // [NA2][CH]
+  T* sb = sa + NA2 * ACTVV_CH;             // [NA2][CH]
+  T* sc = sb + NA2 * ACTVV_CH;             // [NA2][CH]
   __shared__ double red[8];
   const size_t nV2 = (size_t)z.nV * z.nV;
   const int ve = z.nC + z.nA;
@@ -524,26 +530,37 @@ __global__ void __launch_bounds__(256) actvv_gen_kernel(const double* __restrict
         b = m * rt;
         c = mt * rt;
       }
-      sa[it] = a;
-      sb[it] = b;
-      sc[it] = c;
+      sa[it] = (T)a;
+      sb[it] = (T)b;
+      sc[it] = (T)c;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
       const int o = threadIdx.x + 256 * r;
       if (o < NA4) {
-        const double* ap = sa + (o / NA2) * ACTVV_CH;
-        const double* bq = sb + (o % NA2) * ACTVV_CH;
-        const double* cq = sc + (o % NA2) * ACTVV_CH;
-        double t1 = acc1[r], t2 = acc2[r];
+        const T* ap = sa + (o / NA2) * ACTVV_CH;
+        const T* bq = sb + (o % NA2) * ACTVV_CH;
+        const T* cq = sc + (o % NA2) * ACTVV_CH;
+        if constexpr (F32) {
+          float t1 = 0.f, t2 = 0.f;
 #pragma unroll 8
-        for (int kk = 0; kk < ACTVV_CH; ++kk) {
-          t1 = fma(ap[kk], bq[kk], t1);
-          t2 = fma(ap[kk], cq[kk], t2);
+          for (int kk = 0; kk < ACTVV_CH; ++kk) {
+            t1 = fmaf(ap[kk], bq[kk], t1);
+            t2 = fmaf(ap[kk], cq[kk], t2);
+          }
+          acc1[r] += (double)t1;
+          acc2[r] += (double)t2;
+        } else {
+          double t1 = acc1[r], t2 = acc2[r];
+#pragma unroll 8
+          for (int kk = 0; kk < ACTVV_CH; ++kk) {
+            t1 = fma(ap[kk], bq[kk], t1);
+            t2 = fma(ap[kk], cq[kk], t2);
+          }
+          acc1[r] = t1;
+          acc2[r] = t2;
         }
-        acc1[r] = t1;
-        acc2[r] = t2;
       }
     }
   }
@@ -1148,8 +1165,13 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     if (ints_ready) rest_act_tables(p, &F.alpha, &F.pinfo, &F.tau, &F.ld);
 #define ACTVV_GEN(NA_)                                                                       \
   case NA_:                                                                                  \
-    raise_smem_limit((const void*)actvv_gen_kernel<NA_>, smg);                               \
-    actvv_gen_kernel<NA_><<<ACTVV_BLOCKS, 256, smg, st>>>(eps, s, z, w.M, F, w.P12part);     \
+    if (ints_ready) {                                                                        \
+      raise_smem_limit((const void*)actvv_gen_kernel<NA_, true>, smg);                       \
+      actvv_gen_kernel<NA_, true><<<ACTVV_BLOCKS, 256, smg, st>>>(eps, s, z, w.M, F, w.P12part); \
+    } else {                                                                                 \
+      raise_smem_limit((const void*)actvv_gen_kernel<NA_, false>, smg);                      \
+      actvv_gen_kernel<NA_, false><<<ACTVV_BLOCKS, 256, smg, st>>>(eps, s, z, w.M, F, w.P12part); \
+    }                                                                                        \
     break;
     switch (z.nA) {
       case 1:
