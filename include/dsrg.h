@@ -247,6 +247,16 @@ dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t *sz, const double *B, 
  * since the last call (DSRG_ERR_TIMEOUT), then clear it. */
 dsrg_status_t dsrg_plan_sync(dsrg_plan_t *plan);
 
+/* Self-test of the failure path of the tensor-core kernels (the paper has no
+ * counterpart). Every wait in those kernels (on TMA copies, MMAs, TMEM buffers)
+ * gives up after about 2 s, records a status word and lets the kernel return,
+ * so a lost arrival becomes an error status instead of a hung GPU. This call
+ * queues, on the plan's stream, one such wait on a barrier that nothing ever
+ * completes; the next dsrg_plan_sync then returns DSRG_ERR_TIMEOUT (after about
+ * 2 s) and clears the status, and the plan stays usable. Returns DSRG_OK when
+ * the launch was queued. */
+dsrg_status_t dsrg_plan_selftest_wait_timeout(dsrg_plan_t *plan);
+
 /* Number of kernel launches the last energy/gradient call queued. */
 int32_t dsrg_plan_last_launch_count(const dsrg_plan_t *plan);
 

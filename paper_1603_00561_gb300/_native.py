@@ -26,6 +26,7 @@ EXPORTS = [
     "dsrg_batch_launch_count", "dsrg_batch_last_error", "dsrg_ccvv_energy_noalloc",
     "dsrg_plan_autotune", "dsrg_batch_autotune", "dsrg_plan_item_order", "dsrg_batch_item_order",
     "dsrg_plan_time_ccvv", "dsrg_plan_set_item_order", "dsrg_batch_set_item_order",
+    "dsrg_plan_selftest_wait_timeout",
 ]
 
 
@@ -62,6 +63,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_mrpt2_energy_host.restype = st
     lib.dsrg_plan_sync.argtypes = [vp]
     lib.dsrg_plan_sync.restype = st
+    lib.dsrg_plan_selftest_wait_timeout.argtypes = [vp]
+    lib.dsrg_plan_selftest_wait_timeout.restype = st
     lib.dsrg_plan_last_launch_count.argtypes = [vp]
     lib.dsrg_plan_last_launch_count.restype = C.c_int32
     lib.dsrg_plan_workspace_bytes.argtypes = [vp]

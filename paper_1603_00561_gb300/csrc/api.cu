@@ -529,6 +529,14 @@ dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const
   return DSRG_OK;
 }
 
+dsrg_status_t dsrg_plan_selftest_wait_timeout(dsrg_plan_t* p) {
+  if (!p) return DSRG_ERR_INVALID_ARG;
+  p->launches = 0;
+  cudaError_t e = launch_wait_selftest(p);
+  if (e != cudaSuccess) return cuda_fail(p, e, "wait self-test");
+  return DSRG_OK;
+}
+
 dsrg_status_t dsrg_plan_sync(dsrg_plan_t* p) {
   if (!p) return DSRG_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(p->stream);

@@ -174,6 +174,8 @@ int split_kb_elems(bool bf16);
 size_t split_mol_desc_bytes();
 void split_fill_mol_desc(const dsrg_plan* p, long long row0, void* out);
 cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double s);
+// one bounded wait that runs out (about 2 s) and records DSRG_ERR_TIMEOUT's status word
+cudaError_t launch_wait_selftest(dsrg_plan* p);
 cudaError_t split_stage_rows(dsrg_plan* p, const double* B, int h0, int h1);
 cudaError_t split_stage_tables(dsrg_plan* p, const double* eps, double s);
 // host-buffer pipeline: CCVV items grouped by the core row j of their pair

@@ -1009,6 +1009,27 @@ cudaError_t split_stage(dsrg_plan* p, const double* B, const double* eps, double
   return e;
 }
 
+// Self-test of the timeout path of the kernels' bounded waits: one thread waits,
+// through the same mbar_wait, on an mbarrier that nothing arrives on. After the
+// bound (TC_WAIT_NS) it records the status word and the kernel returns.
+__global__ void wait_selftest_kernel(int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) (void)mbar_wait(&bar, 0u, (volatile int*)&abort_flag, status);
+}
+
+cudaError_t launch_wait_selftest(dsrg_plan* p) {
+  wait_selftest_kernel<<<1, 32, 0, p->stream>>>(p->d_status);
+  DSRG_LAUNCH_CHECK(p);
+  return cudaSuccess;
+}
+
 size_t split_mol_desc_bytes() { return sizeof(MolDesc); }
 int split_kb_elems(bool bf16) { return KB_BYTES / (bf16 ? 2 : 4); }
 
