@@ -74,15 +74,34 @@ def _haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
     return q
 
 
+# Planted orbital energies of the "degenerate" spectrum (dyadic, so every sum
+# and difference below is exact in binary floating point):
+#   core 0, 1 = -1/2, -1/4; active 0 = 1/8; virtual 0..3 = -1/2, -1/4, 1/8, -7/8,
+# which make one denominator of each kind exactly zero: core pair (0, 1) with
+# virtuals (0, 1); core 0, active 0 with virtuals (0, 2); core pair (0, 1) with
+# virtual 3 and active 0.
+DEGENERATE = dict(core=(-0.5, -0.25), active=(0.125,), virt=(-0.5, -0.25, 0.125, -0.875))
+
+
 def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5,
                  seed: int = 0, b_scale: float = 0.3, b_decay: float = 0.02,
-                 occupation: str = "random") -> Problem:
+                 occupation: str = "random", spectrum: str = "sorted") -> Problem:
     """Draw one synthetic problem.
 
     ``occupation`` selects gamma1: ``"random"`` (the recipe above), ``"full"``
     (gamma1 = 2 I: the active orbitals doubly occupied) or ``"empty"``
     (gamma1 = 0). ``lambda2`` is drawn in all cases; callers zero it when a
     test needs a one-determinant reference.
+
+    ``spectrum`` selects the orbital energies: ``"sorted"`` (the recipe above);
+    ``"overlap"`` (core ~ U[-2.0, -0.3], active ~ U[-0.2, 0.1], virtual ~
+    U[-1.2, 5.0], none of the blocks sorted, so virtual energies fall below core
+    and active ones and the denominators of every block cross zero);
+    ``"degenerate"`` (``"overlap"`` with the energies of ``DEGENERATE`` planted
+    at the start of each block, so that some denominators are exactly zero;
+    needs ncore >= 2, nactive >= 1, nvirt >= 4); ``"negative"`` (virtual ~
+    U[-1.9, -0.4], sorted, core and active as in the recipe: every virtual
+    energy negative).
     """
     if min(ncore, nactive, nvirt) < 0 or naux < 1:
         raise ValueError("sizes must be >= 0 and naux >= 1")
@@ -101,9 +120,26 @@ def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5
         B[:, ncore:, :nactive] = aa
     B *= b_scale * np.exp(-b_decay * np.arange(naux, dtype=np.float64))[:, None, None]
 
-    eC = np.sort(re.uniform(-2.0, -0.3, ncore))
-    eA = np.sort(re.uniform(-0.2, 0.1, nactive))
-    eV = np.sort(re.uniform(0.05, 5.0, nvirt))
+    if spectrum == "sorted":
+        eC = np.sort(re.uniform(-2.0, -0.3, ncore))
+        eA = np.sort(re.uniform(-0.2, 0.1, nactive))
+        eV = np.sort(re.uniform(0.05, 5.0, nvirt))
+    elif spectrum in ("overlap", "degenerate"):
+        eC = re.uniform(-2.0, -0.3, ncore)
+        eA = re.uniform(-0.2, 0.1, nactive)
+        eV = re.uniform(-1.2, 5.0, nvirt)
+        if spectrum == "degenerate":
+            if ncore < 2 or nactive < 1 or nvirt < 4:
+                raise ValueError("the degenerate spectrum needs ncore >= 2, nactive >= 1, nvirt >= 4")
+            eC[:2] = DEGENERATE["core"]
+            eA[:1] = DEGENERATE["active"]
+            eV[:4] = DEGENERATE["virt"]
+    elif spectrum == "negative":
+        eC = np.sort(re.uniform(-2.0, -0.3, ncore))
+        eA = np.sort(re.uniform(-0.2, 0.1, nactive))
+        eV = np.sort(re.uniform(-1.9, -0.4, nvirt))
+    else:
+        raise ValueError(spectrum)
     eps = np.concatenate([eC, eA, eV])
 
     if occupation == "random":

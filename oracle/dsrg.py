@@ -48,10 +48,12 @@ def _t(x):
 
 
 def reg_t(D, s):
-    """(1 - exp(-s D^2)) / D (Eq. (13)), 0 at D == 0."""
+    """(1 - exp(-s D^2)) / D (Eq. (13)). At D == 0 it takes the leading Maclaurin
+    term s D of Sec. II.B: the value there is 0, and autograd sees the slope s
+    of this analytic function (the quotient form has no derivative at 0)."""
     nz = D != 0
     Ds = torch.where(nz, D, torch.ones_like(D))
-    return torch.where(nz, -torch.expm1(-s * D * D) / Ds, torch.zeros_like(D))
+    return torch.where(nz, -torch.expm1(-s * D * D) / Ds, s * D)
 
 
 def reg_v(D, s):
@@ -60,10 +62,11 @@ def reg_v(D, s):
 
 
 def reg_f1(D, s):
-    """(1 - exp(-2 s D^2)) / D: the product of Eq. (13) and Eq. (15) (Eq. (23)), 0 at D == 0."""
+    """(1 - exp(-2 s D^2)) / D: the product of Eq. (13) and Eq. (15) (Eq. (23)).
+    At D == 0 the leading Maclaurin term 2 s D (value 0, slope 2 s), as in reg_t."""
     nz = D != 0
     Ds = torch.where(nz, D, torch.ones_like(D))
-    return torch.where(nz, -torch.expm1(-2.0 * s * D * D) / Ds, torch.zeros_like(D))
+    return torch.where(nz, -torch.expm1(-2.0 * s * D * D) / Ds, 2.0 * s * D)
 
 
 # --------------------------------------------------------------------------

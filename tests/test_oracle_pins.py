@@ -154,6 +154,46 @@ def test_size_consistency():
     assert _rel(r0["total"], ra["total"] + rb["total"]) < 1e-12
 
 
+@pytest.mark.parametrize("spectrum,seed", [("overlap", 20), ("degenerate", 21), ("negative", 22)])
+def test_tiers_agree_on_unusual_spectra(spectrum, seed):
+    """Neither Table 1 nor Table 2 assumes an order of the orbital energies or a
+    sign of the denominators: with virtual energies below core and active ones
+    (denominators of both signs, unsorted blocks), with exactly zero
+    denominators, and with every virtual energy negative, the literal
+    spin-orbital tier and the pair-loop tier agree per block."""
+    p = make_problem(2, 2, 5, 9, s=0.7, seed=seed, spectrum=spectrum)
+    r0 = spinorb.energy(*_args(p))
+    r1 = dsrg.energy(*_args(p))
+    for k in BLOCKS:
+        assert abs(r0[k] - r1[k]) <= 1e-12 * max(abs(r0[k]), 1.0), (k, r0[k], r1[k])
+
+
+def test_zero_denominator_is_the_removable_limit():
+    """Sec. II.B, Maclaurin form: the regulated amplitude behaves as t ~ v s D
+    for small D, so each term is continuous through D = 0 with value 0 there.
+    With exactly zero denominators planted in F1, F2 and F3, moving one of the
+    planted virtual energies by delta changes the energy linearly in delta:
+    E(2 delta) - E(0) = 2 (E(delta) - E(0)) + O(delta^2). A regulator with any
+    other value at D = 0 would leave a jump that does not shrink with delta."""
+    p = make_problem(2, 1, 5, 8, s=0.6, seed=23, spectrum="degenerate")
+    ve = p.ncore + p.nactive
+
+    def e_at(delta, tier):
+        eps = p.eps.copy()
+        eps[ve + 1] += delta   # virtual 1: the D = 0 quadruple of F1
+        eps[ve + 2] += delta   # virtual 2: the D = 0 position of F2
+        eps[ve + 3] += delta   # virtual 3: the D = 0 position of F3
+        args = list(_args(p))
+        args[1] = eps
+        return tier.energy(*args)
+    for tier in (dsrg, spinorb):
+        r0, r1, r2 = e_at(0.0, tier), e_at(1e-5, tier), e_at(2e-5, tier)
+        for k in ("ccvv", "cavv", "ccav", "total"):
+            d1, d2 = r1[k] - r0[k], r2[k] - r0[k]
+            assert np.isfinite(r0[k])
+            assert abs(d2 - 2.0 * d1) <= 1e-3 * abs(d1) + 1e-12 * abs(r0[k]), (tier.__name__, k, d1, d2)
+
+
 def test_power_of_two_scaling_is_exact():
     """E is homogeneous of degree 4 in B (Eqs. (12)-(15) with f^(1) = 0, Eq. (19)):
     B -> 2B multiplies every block by 16 exactly, bit for bit."""
@@ -222,6 +262,32 @@ def test_gradient_matches_finite_differences_of_tier0():
         assert abs(fd - g["deps"][k]) <= 1e-7 * max(1.0, abs(fd)), (k, fd, g["deps"][k])
     fd = (e0(s=p.s + h) - e0(s=p.s - h)) / (2 * h)
     assert abs(fd - g["ds"]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_gradient_at_zero_denominators():
+    """With denominators exactly 0 in F1, F2 and F3 (planted degenerate orbital
+    energies), the energy is still an analytic function of eps (Sec. II.B:
+    t ~ v s D near D = 0). Autograd of tier 1 at that point equals central
+    differences of tier 0, for the energies of the planted orbitals and for B
+    entries of the orbitals involved."""
+    p = make_problem(2, 1, 5, 8, s=0.6, seed=23, spectrum="degenerate")
+    g = dsrg.energy_and_grad(*_args(p))
+    h = 1e-6
+
+    def e0(B=p.B, eps=p.eps):
+        return spinorb.energy(B, eps, p.gamma1, p.lambda2, p.s, p.ncore, p.nactive, p.nvirt)["total"]
+
+    for k in range(p.norb):
+        ep = p.eps.copy(); ep[k] += h
+        em = p.eps.copy(); em[k] -= h
+        fd = (e0(eps=ep) - e0(eps=em)) / (2 * h)
+        assert abs(fd - g["deps"][k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g["deps"][k])
+    A = p.nactive
+    for ix in [(0, 0, A + 0), (1, 1, A + 1), (2, 0, A + 2), (0, 1, A + 3), (3, p.ncore, A + 2)]:
+        Bp = p.B.copy(); Bp[ix] += h
+        Bm = p.B.copy(); Bm[ix] -= h
+        fd = (e0(B=Bp) - e0(B=Bm)) / (2 * h)
+        assert abs(fd - g["dB"][ix]) <= 1e-6 * max(1.0, abs(fd)), (ix, fd, g["dB"][ix])
 
 
 # ---------------------------------------------------------------------------
