@@ -8,6 +8,13 @@ whose B (0.86 GB) is larger than L2, in split precision.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision tf32x3|bf16x3|fp64]
     python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
 
+Besides the timed energy step, the JSON line carries two more legs (each
+timed with CUDA events after its own warm-up): ``gradient`` (E + dE/dB +
+dE/deps + dE/ds at the cc-pVTZ size, FP64 and BF16x3 plans, with the split
+gradient's error against the FP64 one; ``--no-grad`` skips it) and ``batch``
+(64 molecules of uneven size in one graph-captured call against one-by-one
+FP64 plans; ``--with-batch 0`` skips it).
+
 Under torchrun each rank computes its own molecule (weak scaling, no
 data-path collective); rank 0 prints one JSON line.
 """
@@ -233,16 +240,20 @@ def _events(torch):
 
 
 def time_gradient(pk, torch):
-    """E + dE/dB + dE/deps + dE/ds at the cc-pVTZ size, per molecule, FP64 and BF16x3 plans."""
+    """E + dE/dB + dE/deps + dE/ds at the cc-pVTZ size, per molecule, FP64 and BF16x3
+    plans; the energy alone for the ratio; the split gradient's error against the
+    FP64 plan's (largest difference over the largest entry, per array)."""
     from dsrg_synth import make_problem
     cfg = WORKLOADS["naphthyne-vtz-398"]
     p = make_problem(seed=0, **cfg)
     dev = pk.to_device(p)
     res = {"workload": "naphthyne-vtz-398"}
+    grads = {}
     for prec in ("fp64", "bf16x3"):
         plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, grad=True)
-        plan.energy_grad(*dev, p.s)
+        out, dB, de, ds = plan.energy_grad(*dev, p.s)
         torch.cuda.synchronize()
+        grads[prec] = (dB.clone(), de.clone(), float(ds[0]))
         e0, e1 = _events(torch)
         e0.record()
         for _ in range(3):
@@ -250,7 +261,22 @@ def time_gradient(pk, torch):
         e1.record()
         torch.cuda.synchronize()
         res[f"{prec}_ms_per_gradient"] = e0.elapsed_time(e1) / 3
+        plan.energy(*dev, p.s, out=out)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            plan.energy(*dev, p.s, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        res[f"{prec}_ms_per_energy"] = e0.elapsed_time(e1) / 3
+        plan.sync()
         plan.close()
+    (b64, e64, s64), (b32, e32, s32) = grads["fp64"], grads["bf16x3"]
+    res["bf16x3_gradient_over_energy"] = res["bf16x3_ms_per_gradient"] / res["bf16x3_ms_per_energy"]
+    res["bf16x3_vs_fp64_rel_err"] = {
+        "dB": float((b32 - b64).abs().max() / b64.abs().max()),
+        "deps": float((e32 - e64).abs().max() / e64.abs().max()),
+        "ds": abs(s32 - s64) / abs(s64)}
     return res
 
 
@@ -309,10 +335,11 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--with-grad", action="store_true",
-                    help="also time the gradient at the cc-pVTZ size (FP64 and split)")
-    ap.add_argument("--with-batch", type=int, default=0, metavar="NMOL",
-                    help="also time a batch of NMOL uneven molecules vs one-by-one FP64 plans")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="skip the gradient leg (cc-pVTZ size, FP64 and split plans)")
+    ap.add_argument("--with-batch", type=int, default=64, metavar="NMOL",
+                    help="molecules of the batch leg (uneven sizes, one call, against "
+                         "one-by-one FP64 plans); 0 skips it")
     ap.add_argument("--item-order", type=int, default=None, metavar="CODE",
                     help="fixed CCVV schedule code instead of autotuning it")
     ap.add_argument("--schedule-sweep", action="store_true",
@@ -503,9 +530,9 @@ def main():
         p64.close()
 
     extra = {}
-    if args.with_grad:
+    if not args.no_grad:
         extra["gradient"] = time_gradient(pk, torch)
-    if args.with_batch:
+    if args.with_batch > 0:
         extra["batch"] = time_batch(pk, torch, args.with_batch, prec)
 
     if rank == 0:

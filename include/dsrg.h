@@ -238,10 +238,43 @@ dsrg_status_t dsrg_plan_time_ccvv(dsrg_plan_t *plan, const double *B, const doub
  * call reads is written earlier in the same call, so nothing needs clearing.
  * All calls share the array: calls whose work overlaps on the GPU (other
  * streams, other host threads) race and must be serialised by the caller. The
- * first call on a device looks up the array's device address; make it before
- * any stream capture. */
+ * first call in each CUDA context of a device looks up the array's device
+ * address (the first call of the process on that device, and the first call
+ * after the device's context was destroyed and made again, e.g. by
+ * cudaDeviceReset, which loads the library's kernels anew at a new address);
+ * make that call before any stream capture. A CUDA error left pending by the
+ * caller's earlier work makes the call return DSRG_ERR_CUDA without queueing
+ * anything, and the error stays pending for the caller to read. */
 dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t *sz, const double *B, const double *eps,
                                        double s, double *out_dev, void *cuda_stream);
+
+/* Counters of the epilogue branches the split-precision kernels took (the
+ * paper has no counterpart; a diagnostic of which arithmetic evaluated the
+ * regulators of Eqs. (13), (15) and (23)). Counted since the plan was created
+ * or last reset; FP64 plans leave them at 0. Indices:
+ *   DSRG_COUNT_CCVV_FAR       CCVV work items (core pair x tile pair) whose every
+ *                             |Delta| is so large that exp(-2 s Delta^2) < 2^-63,
+ *                             evaluated as 1/Delta;
+ *   DSRG_COUNT_CCVV_FACTORED  items with every |Delta| >= 1/4 evaluated from the
+ *                             factorised exponentials;
+ *   DSRG_COUNT_CCVV_DIRECT    items with some |Delta| < 1/4 (or a pair whose
+ *                             factors could overflow), evaluated with expm1 per
+ *                             element (R(0) = 0) and the exchange combination in FP64;
+ *   DSRG_COUNT_CCVV_UNFACTORABLE items of pairs whose factors could overflow;
+ *   DSRG_COUNT_CAVV_NEAR      CAVV positions (core m, e, f) with some |Delta_u| < 1/4
+ *                             (or a non-factorisable (m, u)), evaluated in FP64 with
+ *                             expm1;
+ *   DSRG_COUNT_CAVV_UNFACTORABLE CAVV tiles with a non-factorisable (m, u).
+ * Waits for the plan's stream; reset != 0 clears the counters after reading. */
+#define DSRG_NCOUNTERS 8
+#define DSRG_COUNT_CCVV_FAR 0
+#define DSRG_COUNT_CCVV_FACTORED 1
+#define DSRG_COUNT_CCVV_DIRECT 2
+#define DSRG_COUNT_CCVV_UNFACTORABLE 3
+#define DSRG_COUNT_CAVV_NEAR 4
+#define DSRG_COUNT_CAVV_UNFACTORABLE 5
+dsrg_status_t dsrg_plan_branch_counts(dsrg_plan_t *plan, uint64_t counts[DSRG_NCOUNTERS],
+                                      int32_t reset);
 
 /* Wait for the plan's stream and report any device-side condition recorded
  * since the last call (DSRG_ERR_TIMEOUT), then clear it. */

@@ -166,6 +166,13 @@ class Plan:
     def sync(self):
         self._check(self.lib.dsrg_plan_sync(self.h), "dsrg_plan_sync")
 
+    def branch_counts(self, reset: bool = False) -> dict:
+        """Epilogue branch counters of the split kernels (``dsrg_plan_branch_counts``)."""
+        arr = (C.c_uint64 * _native.NCOUNTERS)()
+        self._check(self.lib.dsrg_plan_branch_counts(self.h, arr, 1 if reset else 0),
+                    "dsrg_plan_branch_counts")
+        return {k: int(arr[i]) for k, i in _native.COUNTERS.items()}
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.dsrg_plan_destroy(self.h)

@@ -26,8 +26,12 @@ EXPORTS = [
     "dsrg_batch_launch_count", "dsrg_batch_last_error", "dsrg_ccvv_energy_noalloc",
     "dsrg_plan_autotune", "dsrg_batch_autotune", "dsrg_plan_item_order", "dsrg_batch_item_order",
     "dsrg_plan_time_ccvv", "dsrg_plan_set_item_order", "dsrg_batch_set_item_order",
-    "dsrg_plan_selftest_wait_timeout",
+    "dsrg_plan_selftest_wait_timeout", "dsrg_plan_branch_counts",
 ]
+# indices of dsrg_plan_branch_counts
+NCOUNTERS = 8
+COUNTERS = {"ccvv_far": 0, "ccvv_factored": 1, "ccvv_direct": 2, "ccvv_unfactorable": 3,
+            "cavv_near": 4, "cavv_unfactorable": 5}
 
 
 class Sizes(C.Structure):
@@ -65,6 +69,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_plan_sync.restype = st
     lib.dsrg_plan_selftest_wait_timeout.argtypes = [vp]
     lib.dsrg_plan_selftest_wait_timeout.restype = st
+    lib.dsrg_plan_branch_counts.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int32]
+    lib.dsrg_plan_branch_counts.restype = st
     lib.dsrg_plan_last_launch_count.argtypes = [vp]
     lib.dsrg_plan_last_launch_count.restype = C.c_int32
     lib.dsrg_plan_workspace_bytes.argtypes = [vp]

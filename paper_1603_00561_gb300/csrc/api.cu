@@ -229,6 +229,7 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
   ok = ok && plan_alloc(p, (void**)&p->d_chunks, chunks.size() * sizeof(int2)) &&
        plan_alloc(p, (void**)&p->d_red, chunks.size() * 2 * sizeof(double));
   ok = ok && plan_alloc(p, (void**)&p->d_status, sizeof(int));
+  ok = ok && plan_alloc(p, (void**)&p->d_counts, DSRG_NCOUNTERS * sizeof(unsigned long long));
   ok = ok && active_alloc(p);
   if (ok && prec != DSRG_PREC_FP64)
     ok = share ? split_alloc_at(p, share->hi, share->lo, share->Qld, share->row_base, nullptr, nullptr)
@@ -277,6 +278,7 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
   if (e == cudaSuccess && !chunks.empty())
     e = cudaMemcpy(p->d_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_counts, 0, DSRG_NCOUNTERS * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(p->d_partials, 0, (size_t)np * sizeof(double));
   if (e != cudaSuccess) {
     free_all(p);
@@ -534,6 +536,18 @@ dsrg_status_t dsrg_plan_selftest_wait_timeout(dsrg_plan_t* p) {
   p->launches = 0;
   cudaError_t e = launch_wait_selftest(p);
   if (e != cudaSuccess) return cuda_fail(p, e, "wait self-test");
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_plan_branch_counts(dsrg_plan_t* p, uint64_t* counts, int32_t reset) {
+  if (!p || !counts) return DSRG_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  unsigned long long c[DSRG_NCOUNTERS] = {};
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c, p->d_counts, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(p->d_counts, 0, sizeof(c));
+  if (e != cudaSuccess) return cuda_fail(p, e, "branch counts");
+  for (int k = 0; k < DSRG_NCOUNTERS; ++k) counts[k] = (uint64_t)c[k];
   return DSRG_OK;
 }
 

@@ -108,6 +108,8 @@ struct dsrg_plan {
 
   // device status word (bounded waits)
   int* d_status = nullptr;
+  // counters of the epilogue branches taken by the split kernels (DSRG_COUNT_*)
+  unsigned long long* d_counts = nullptr;
 };
 
 namespace dsrg {

@@ -9,6 +9,8 @@
 // that the library holds for every GPU it is loaded on, until the process
 // exits. The arithmetic is that of the FP64 CCVV kernel (fp64_pairs.cu); only
 // where its scratch lives differs.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -35,7 +37,35 @@ static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
 constexpr int MAX_DEV = 64;
 std::mutex g_mu;
-double* g_addr[MAX_DEV] = {};
+// Per device: the address of the scratch array in the context it was looked up
+// in, keyed by that context's unique id. A context that is destroyed and made
+// again (cudaDeviceReset, a re-created primary context) loads the module anew
+// at a new address and gets a new id, so the address is looked up again.
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  double* addr = nullptr;
+};
+ScratchSlot g_slot[MAX_DEV];
+
+PFN_cuCtxGetCurrent_v4000 g_get_ctx = nullptr;
+PFN_cuCtxGetId_v12000 g_get_id = nullptr;
+
+bool driver_entry_points() {
+  if (g_get_ctx && g_get_id) return true;
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return false;
+  g_get_ctx = (PFN_cuCtxGetCurrent_v4000)f;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return false;
+  g_get_id = (PFN_cuCtxGetId_v12000)f;
+  return true;
+}
 
 __global__ void noalloc_lists_kernel(double* scratch, int nC, int nT, int n_pairs, int n_tp) {
   int2* pairs = (int2*)(scratch + NA_ITEMS);
@@ -87,20 +117,36 @@ __global__ void __launch_bounds__(256) noalloc_reduce_kernel(const double* scrat
   }
 }
 
-// Device address of the scratch array for the current device (looked up once per device).
+// Device address of the scratch array in the current device's current context.
+// Looked up with cudaGetSymbolAddress the first time a context is seen (this also
+// creates the device's primary context if the runtime has not done so yet), then
+// taken from the slot while the context id stays the same.
 cudaError_t scratch_address(double** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = (double*)p;
+  if (!driver_entry_points()) return cudaErrorNotSupported;
+  CUcontext ctx = nullptr;
+  if (g_get_ctx(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  void* p = nullptr;
+  if (!ctx) {
+    // no context current yet: the symbol lookup makes the primary context current
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+    if (g_get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
   }
-  *ptr = g_addr[dev];
+  unsigned long long id = 0;
+  if (g_get_id(ctx, &id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  ScratchSlot& sl = g_slot[dev];
+  if (sl.addr && sl.ctx_id == id) {
+    *ptr = sl.addr;
+    return cudaSuccess;
+  }
+  if (!p && (e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
+  sl.ctx_id = id;
+  sl.addr = (double*)p;
+  *ptr = sl.addr;
   return cudaSuccess;
 }
 
@@ -118,6 +164,9 @@ extern "C" dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t* sz, const 
   const long long n_pairs = nC * (nC + 1) / 2, n_tp = nT * (nT + 1) / 2;
   // sizes beyond the fixed scratch are rejected (no fallback allocation)
   if (n_pairs > NA_PAIRS || n_tp > NA_TPS || n_pairs * n_tp > NA_ITEMS) return DSRG_ERR_UNSUPPORTED;
+  // an error left pending by the caller's earlier work is reported, not consumed:
+  // it stays for the caller to read
+  if (cudaPeekAtLastError() != cudaSuccess) return DSRG_ERR_CUDA;
   double* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return DSRG_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -358,7 +358,9 @@ __global__ void cavv_tables_kernel(const double* __restrict__ eps, double s, Siz
     if (b == 0) {
       double vmax = 0.0;
       for (int v = 0; v < z.nV; ++v) vmax = fmax(vmax, fabs(eps[ve + v]));
-      const bool ok = (s * E * E <= 700.0) && (2.0 * s * fabs(E) * vmax <= 700.0) &&
+      // factors are multiplied left to right (pair, row, column, table); the partial
+      // products carry -sE^2 + 2sE e_e (+ 2sE e_f), bounded by the sum of magnitudes
+      const bool ok = (s * E * E + 4.0 * s * fabs(E) * vmax <= 700.0) &&
                       (4.0 * s * vmax * vmax <= 700.0);
       pinfo[4 * mu + 0] = E;
       pinfo[4 * mu + 1] = exp(-s * E * E);
@@ -396,7 +398,8 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
                                                       const double* __restrict__ alpha,
                                                       const double* __restrict__ pinfo,
                                                       const double* __restrict__ tau1,
-                                                      double* __restrict__ partials) {
+                                                      double* __restrict__ partials,
+                                                      unsigned long long* __restrict__ counts) {
   extern __shared__ float f2s[];
   float* sX = f2s;                              // [NA][32][33]   X_u[e,f]
   float* sXt = sX + NA * F2_T * (F2_T + 1);     // [NA][32][33]   X_u[f,e]
@@ -460,6 +463,8 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
   const int c = threadIdx.x & 31;
   const int f = F0 + c;
   double acc = 0.0;
+  unsigned long long near = 0;  // positions of this thread on the expm1 path
+  if (threadIdx.x == 0 && !fact) atomicAdd(&counts[DSRG_COUNT_CAVV_UNFACTORABLE], 1ull);
   if (f < z.nV) {
     for (int r = threadIdx.x >> 5; r < F2_T; r += 8) {
       const int e = E0 + r;
@@ -510,6 +515,7 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
       } else {
         // a D_u near 0 (or a pair whose factors could overflow): expm1 regulators
         // and the exchange combination in FP64
+        ++near;
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
           Rt[u] = reg_t(Dd[u], s);
@@ -532,6 +538,7 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
       }
     }
   }
+  if (near) atomicAdd(&counts[DSRG_COUNT_CAVV_NEAR], near);
   const double tot = block_sum<256>(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
@@ -798,7 +805,8 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     raise_smem_limit((const void*)cavv_f2_kernel<NA_>, sm); \
     cavv_f2_kernel<NA_><<<sg.count, 256, sm, stream>>>(st->Y, st->ldy, st->nVpad, eps, G, s, z,       \
                                                       st->d_tp, st->n_tp, st->alpha, st->pinfo,   \
-                                                      st->tau1, p->d_partials + sg.begin);        \
+                                                      st->tau1, p->d_partials + sg.begin,         \
+                                                      p->d_counts);                               \
     break;
     switch (z.nA) {
       F2_LAUNCH(1) F2_LAUNCH(2) F2_LAUNCH(3) F2_LAUNCH(4)

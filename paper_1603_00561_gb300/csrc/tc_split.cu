@@ -100,6 +100,7 @@ struct SplitArgs {
   const int4* items;
   const int* cta_begin;
   int* status;
+  unsigned long long* counts;  // epilogue branch counters (DSRG_COUNT_CCVV_*)
   int prefetch;  // K stages ahead to prefetch into L2 (0: off)
 };
 
@@ -481,6 +482,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       if (lane == 0) sRed[warp - 2] = acc;
       named_bar(1, 32 * EPI_WARPS);
       if (et == 0) {
+        atomicAdd(&a.counts[far ? DSRG_COUNT_CCVV_FAR
+                                : (fast ? DSRG_COUNT_CCVV_FACTORED : DSRG_COUNT_CCVV_DIRECT)],
+                  1ull);
+        if (pi[2] == 0.0) atomicAdd(&a.counts[DSRG_COUNT_CCVV_UNFACTORABLE], 1ull);
         const double w = (ip.two ? 2.0 : 1.0) * (ip.A < ip.Bt ? 2.0 : 1.0);
         double t = 0.0;
         for (int k = 0; k < EPI_WARPS; ++k) t += sRed[k];
@@ -584,7 +589,8 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
 
 // Per-pair factors of exp(-2 s D^2) with D = E - e_a - e_b:
 //   exp(-2 s E^2) * exp(4 s E e_a) * exp(4 s E e_b) * exp(-2 s (e_a + e_b)^2).
-// A pair is factorisable when every exponent stays within +-700.
+// A pair is factorisable when every partial product of these factors, taken in
+// the epilogue's order, stays within exp(+-700).
 __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Sizes z,
                                     const int2* __restrict__ pairs, int n_pairs, int nVpad,
                                     double* __restrict__ alpha, double* __restrict__ pinfo,
@@ -600,7 +606,10 @@ __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Si
     if (b == 0) {
       double vmax = 0.0;
       for (int v = 0; v < z.nV; ++v) vmax = fmax(vmax, fabs(eps[ve + v]));
-      const bool ok = (2.0 * s * E * E <= 700.0) && (4.0 * s * fabs(E) * vmax <= 700.0) &&
+      // the epilogue multiplies left to right, exp(-2sE^2) * alpha_a * alpha_b * tau:
+      // the partial products carry the exponents -2sE^2 + 4sE e_a (+ 4sE e_b), which
+      // for E e > 0 grow past each single factor's, so their sum of magnitudes is bounded
+      const bool ok = (2.0 * s * E * E + 8.0 * s * fabs(E) * vmax <= 700.0) &&
                       (8.0 * s * vmax * vmax <= 700.0);
       pinfo[4 * p + 0] = E;
       pinfo[4 * p + 1] = exp(-2.0 * s * E * E);
@@ -1081,6 +1090,7 @@ cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtenso
   a.items = d_items;
   a.cta_begin = d_begin;
   a.status = p->d_status;
+  a.counts = p->d_counts;
   a.prefetch = prefetch;
   const size_t sm = split_smem_bytes();
   if (bf16) {

@@ -58,7 +58,9 @@ def test_batch_graph_replay_and_recapture(pk):
     c = batch.energy(dev, s2).cpu().numpy()
     for m, p in enumerate(mols):
         ref = odsrg.energy(p.B, p.eps, p.gamma1, p.lambda2, 0.25, p.ncore, p.nactive, p.nvirt)
-        assert abs(c[m][4] - ref["total"]) / abs(ref["total"]) < 1e-4
+        # the split bound of the total (see test_batch_uneven_recipe_against_oracle)
+        tol = 2.0 * 2.0 * (3 * -(-p.naux // 16) * 2.0 ** -23 + 2.0 ** -18)
+        assert abs(c[m][4] - ref["total"]) / abs(ref["total"]) <= tol
 
 
 def test_batch_uneven_recipe_against_oracle(pk):

@@ -87,6 +87,9 @@ def test_split_blocks_small(pk, prec, nC, nA, nV, Q, s, seed):
         rel = abs(gpu[k] - ref[k]) / max(abs(ref[k]), 1e-300)
         print(f"{prec} {nC}/{nA}/{nV}/{Q} {k:7s} gpu={gpu[k]:+.12e} oracle={ref[k]:+.12e} rel={rel:.2e}")
         bar = split_tol(prec, Q, k)
+        if Q >= 200:
+            # enough auxiliary functions for the 1e-7 target of the split path
+            bar = min(bar, SPLIT_BAR)
         if ref[k] == 0.0:
             assert gpu[k] == 0.0
         else:
