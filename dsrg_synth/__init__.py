@@ -22,6 +22,16 @@ active A, virtual V; hole space H = C+A, particle space P = A+V; orbital order
 * ``lambda2`` -- the opposite-spin active two-body cumulant
   ``lambda2[u, v, x, y]`` (u, x alpha; v, y beta), entries ~ U(-0.05, 0.05),
   averaged over the 8 index permutations of a real (ux|vy)-type tensor.
+* optional ``lambda3`` (``with_lambda3=True``) -- a spin-orbital three-body
+  cumulant over the active spin orbitals ``2u + sigma``,
+  ``lambda3[U,V,W,X,Y,Z]`` for lambda_{UVW}^{XYZ}: entries ~ U(-0.02, 0.02),
+  zero unless the lower and upper triples hold the same number of alpha spin
+  orbitals, antisymmetrised over the lower triple and over the upper triple,
+  and symmetrised under the exchange of the two triples (a real Hermitian
+  cumulant).
+* optional ``f1`` (``with_f1=True``) -- the off-diagonal Fock block,
+  ``f1[i, a]`` for hole i and particle a, entries ~ U(-0.05, 0.05), zero on the
+  active x active sub-block (which belongs to the diagonal block).
 
 Random streams come from numpy's PCG64 seeded with ``SeedSequence(seed)``,
 one child stream per tensor, so each tensor is independent of the others'
@@ -47,6 +57,8 @@ class Problem:
     eps: np.ndarray      # [n] float64, order [core | active | virtual]
     gamma1: np.ndarray   # [nA, nA] float64
     lambda2: np.ndarray  # [nA, nA, nA, nA] float64
+    lambda3: np.ndarray | None = None  # [2nA]^6 float64, spin orbitals
+    f1: np.ndarray | None = None       # [nH, nP] float64
 
     @property
     def nhole(self) -> int:
@@ -83,9 +95,34 @@ def _haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
 DEGENERATE = dict(core=(-0.5, -0.25), active=(0.125,), virt=(-0.5, -0.25, 0.125, -0.875))
 
 
+def _antisym3(t: np.ndarray, axes) -> np.ndarray:
+    """Antisymmetrise a tensor over three of its axes (sum over the 6 orders with signs, / 6)."""
+    a, b, c = axes
+    out = np.zeros_like(t)
+    for perm, sign in (((a, b, c), 1), ((b, c, a), 1), ((c, a, b), 1),
+                       ((b, a, c), -1), ((a, c, b), -1), ((c, b, a), -1)):
+        order = list(range(t.ndim))
+        order[a], order[b], order[c] = perm
+        out += sign * t.transpose(order)
+    return out / 6.0
+
+
+def make_lambda3(nactive: int, rng: np.random.Generator, scale: float = 0.02) -> np.ndarray:
+    """Random real Hermitian spin-orbital three-body cumulant (see module docstring)."""
+    n2 = 2 * nactive
+    R = rng.uniform(-scale, scale, (n2,) * 6)
+    alpha = (np.arange(n2) % 2 == 0).astype(int)
+    na_low = alpha[:, None, None] + alpha[None, :, None] + alpha[None, None, :]
+    mask = na_low[:, :, :, None, None, None] == na_low[None, None, None, :, :, :]
+    R = R * mask
+    R = _antisym3(_antisym3(R, (0, 1, 2)), (3, 4, 5))
+    return 0.5 * (R + R.transpose(3, 4, 5, 0, 1, 2))
+
+
 def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5,
                  seed: int = 0, b_scale: float = 0.3, b_decay: float = 0.02,
-                 occupation: str = "random", spectrum: str = "sorted") -> Problem:
+                 occupation: str = "random", spectrum: str = "sorted",
+                 with_lambda3: bool = False, with_f1: bool = False) -> Problem:
     """Draw one synthetic problem.
 
     ``occupation`` selects gamma1: ``"random"`` (the recipe above), ``"full"``
@@ -107,7 +144,7 @@ def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5
         raise ValueError("sizes must be >= 0 and naux >= 1")
     ss = np.random.SeedSequence(seed)
     kids = ss.spawn(5)
-    rB, re, rg, rl, _ = (np.random.Generator(np.random.PCG64(k)) for k in kids)
+    rB, re, rg, rl, rx = (np.random.Generator(np.random.PCG64(k)) for k in kids)
     nH, nP = ncore + nactive, nactive + nvirt
 
     B = rB.standard_normal((naux, nH, nP))
@@ -168,7 +205,12 @@ def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5
             perms.append(t2.transpose(1, 0, 3, 2))      # (u,x)<->(v,y)
     lambda2 = sum(perms) / 8.0
 
-    return Problem(ncore, nactive, nvirt, naux, float(s), B, eps, gamma1, lambda2)
+    lambda3 = make_lambda3(nactive, rx) if with_lambda3 else None
+    f1 = None
+    if with_f1:
+        f1 = rx.uniform(-0.05, 0.05, (nH, nP))
+        f1[ncore:, :nactive] = 0.0
+    return Problem(ncore, nactive, nvirt, naux, float(s), B, eps, gamma1, lambda2, lambda3, f1)
 
 
 # The synthetic workloads, by what they stand for (sizes nC/nA/nV/naux, s).

@@ -12,15 +12,22 @@ Inputs (Sec. II.A, Eq. (19)):
   lambda2  [nA]^4          L[u,v,x,y] = lambda_{u alpha, v beta}^{x alpha, y beta}
   s        flow parameter (Eh^-2)
 
+Optional inputs:
+  lambda3  [2nA]^6         spin-orbital three-body cumulant lam3[U,V,W,X,Y,Z] =
+                           lambda_{UVW}^{XYZ} over the active spin orbitals 2u + sigma
+                           (terms J and K of Table 1); absent: 0
+  f1       [nH, nP]        off-diagonal Fock block f^(1) (Eqs. (12), (14)), spatial,
+                           the same for both spins; its active x active entries are
+                           not read (they belong to the diagonal block); absent: 0
+
 Blocks reported (Table 2): ``ccvv`` = F1, ``cavv`` = F2, ``ccav`` = F3,
-``active`` = A-E + G-I + F4-F8 (J = K = 0: the three-body cumulant is not an
-input), ``total`` = their sum.
+``active`` = A-E + G-K + F4-F8, ``total`` = their sum.
 
 Readings shared with tier 0 (restated here so this file stands alone):
-Delta = hole energies minus particle energies; the off-diagonal Fock block
-f^(1) is 0; Table 1's ft_j^b is the Hermitian element ft_b^j; internal (all
-active) amplitudes are zero; in Eq. (12) D_u^x = eps_x - eps_u; the regulated
-denominators use -expm1 and vanish at D = 0.
+Delta = hole energies minus particle energies; Table 1's ft_j^b is the
+Hermitian element ft_b^j; internal (all active) amplitudes are zero; in
+Eq. (12) D_u^x = eps_x - eps_u; the regulated denominators use -expm1 and
+vanish at D = 0.
 
 Spin adaptation of F1-F3 (closed-shell spin sums of the spin-orbital Table 2
 expressions, since every regulator depends only on spatial energies):
@@ -237,13 +244,21 @@ def _lambda_so(L, nA):
     return lam
 
 
-def active_block(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, return_terms=False):
-    """Terms A-E, G-I (Table 1) and F4-F8 (Table 2), spin-orbital, f^(1) = 0."""
+def active_block(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, return_terms=False,
+                 lambda3=None, f1=None):
+    """Terms A-E, G-K (Table 1) and F4-F8 (Table 2), spin-orbital."""
     B, eps, G, L, s = _t(B), _t(eps), _t(gamma1), _t(lambda2), _t(s)
     nC, nA, nV = ncore, nactive, nvirt
     if nA == 0:
-        z = torch.zeros((), dtype=DT)
-        return (z, {}) if return_terms else z
+        # no active orbitals: only term A survives, from f^(1) (gamma = 1 on the
+        # core, eta = 1 on the virtuals, the sum over u x of Eq. (12) is empty)
+        if f1 is None:
+            z = torch.zeros((), dtype=DT)
+            return (z, {}) if return_terms else z
+        D1 = eps[:nC, None] - eps[None, nC:]
+        F = _t(f1)
+        termA = 2.0 * torch.sum(F * (1.0 + torch.exp(-s * D1 * D1)) * F * reg_t(D1, s))
+        return (termA, {"A": termA}) if return_terms else termA
     sb = _SpinBlocks(B, eps, s, nC, nA, nV)
     nH2, nP2, nA2, nC2 = 2 * (nC + nA), 2 * (nA + nV), 2 * nA, 2 * nC
     gA = torch.kron(G / 2.0, torch.eye(2, dtype=DT))          # gamma on active spin orbitals
@@ -276,8 +291,15 @@ def active_block(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, return_terms
     actI = torch.arange(nH2) >= nC2
     actA = torch.arange(nP2) < nA2
     internal1 = actI[:, None] & actA[None, :]
-    t1 = torch.where(internal1, torch.zeros_like(S), S * reg_t(D1, s))
-    ft = S * torch.exp(-s * D1 * D1)
+    if f1 is None:
+        F1 = torch.zeros_like(S)
+    else:
+        same = (sb.sH[:, None] == sb.sP[None, :]).to(DT)
+        F1 = _t(f1)[sb.hsp][:, sb.psp] * same
+        F1 = torch.where(internal1, torch.zeros_like(F1), F1)
+    t1 = torch.where(internal1, torch.zeros_like(S), (F1 + S) * reg_t(D1, s))
+    g1 = torch.exp(-s * D1 * D1)
+    ft = F1 * (1.0 + g1) + S * g1
 
     terms = {}
     # A: ft_j^b t_a^i gamma_i^j eta_b^a
@@ -314,19 +336,27 @@ def active_block(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, return_terms
     # F8: 1/2 vt_{mw}^{vy} t_{ux}^{mz} gamma_z^w eta_v^u eta_y^x   [W1: m in C | A A]
     terms["F8"] = 0.5 * torch.einsum("mwvy,mzux,wz,uv,xy->", W1["Vt"][c, :, ap, :],
                                      W1["T"][c, :, ap, :], gA, eA, eA)
+    if lambda3 is not None:
+        l3 = _t(lambda3)
+        # J: 1/4 vt_{mz}^{uv} t_{xy}^{mw} lambda_{uvw}^{xyz}   [W1: m in C, z | u in A, v]
+        terms["J"] = 0.25 * torch.einsum("mzuv,mwxy,uvwxyz->", W1["Vt"][c, :, ap, :],
+                                         W1["T"][c, :, ap, :], l3)
+        # K: 1/4 vt_{xy}^{we} t_{ez}^{uv} lambda_{uvw}^{xyz}   [W3: w in A, e in V]
+        terms["K"] = 0.25 * torch.einsum("xywe,uvez,uvwxyz->", W3["Vt"][:, :, ap, vv],
+                                         W3["T"][:, :, vv, ap], l3)
     tot = sum(terms.values())
     return (tot, terms) if return_terms else tot
 
 
 def energy(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, with_pairs=False,
-           with_terms=False) -> dict:
+           with_terms=False, lambda3=None, f1=None) -> dict:
     """All four blocks and the total, as Python floats (pair energies as numpy)."""
     with torch.no_grad():
         e = ccvv_pair_energies(B, eps, s, ncore, nactive, nvirt)
         f2 = cavv(B, eps, gamma1, s, ncore, nactive, nvirt)
         f3 = ccav(B, eps, gamma1, s, ncore, nactive, nvirt)
         act, terms = active_block(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt,
-                                  return_terms=True)
+                                  return_terms=True, lambda3=lambda3, f1=f1)
     out = dict(ccvv=float(e.sum()), cavv=float(f2), ccav=float(f3), active=float(act))
     out["total"] = out["ccvv"] + out["cavv"] + out["ccav"] + out["active"]
     if with_pairs:
@@ -336,7 +366,8 @@ def energy(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, with_pairs=False,
     return out
 
 
-def energy_and_grad(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt) -> dict:
+def energy_and_grad(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, lambda3=None,
+                    f1=None) -> dict:
     """Energy blocks plus dE_total/dB, dE_total/deps and dE_total/ds by autograd."""
     Bt = _t(B).clone().requires_grad_(True)
     et = _t(eps).clone().requires_grad_(True)
@@ -344,7 +375,7 @@ def energy_and_grad(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt) -> dict:
     e = ccvv_pair_energies(Bt, et, st, ncore, nactive, nvirt).sum()
     f2 = cavv(Bt, et, gamma1, st, ncore, nactive, nvirt)
     f3 = ccav(Bt, et, gamma1, st, ncore, nactive, nvirt)
-    act = active_block(Bt, et, gamma1, lambda2, st, ncore, nactive, nvirt)
+    act = active_block(Bt, et, gamma1, lambda2, st, ncore, nactive, nvirt, lambda3=lambda3, f1=f1)
     tot = e + f2 + f3 + act
     dB, de, ds = torch.autograd.grad(tot, (Bt, et, st))
     return dict(ccvv=float(e), cavv=float(f2), ccav=float(f3), active=float(act),

@@ -14,16 +14,23 @@ Conventions (Sec. II):
 * T2 amplitude, Eq. (13): ``t_{ab}^{ij} = v (1 - exp(-s D^2)) / D``, zero when
   all four indices are active (internal amplitudes are excluded, Sec. II.A);
 * modified integrals, Eq. (15): ``vt = v (1 + exp(-s D^2))``;
-* T1 amplitude, Eq. (12), with the off-diagonal Fock block f^(1) read as 0:
-  ``t_a^i = [sum_{ux} D_u^x t_{ax}^{iu} gamma_u^x] (1 - exp(-s D_a^i^2)) / D_a^i``
-  with ``D_u^x = eps_x - eps_u``; zero when i and a are both active;
-* modified Fock, Eq. (14), same reading: ``ft_a^i = [sum ...] exp(-s D_a^i^2)``;
+* T1 amplitude, Eq. (12):
+  ``t_a^i = [f_a^i + sum_{ux} D_u^x t_{ax}^{iu} gamma_u^x] (1 - exp(-s D_a^i^2)) / D_a^i``
+  with ``D_u^x = eps_x - eps_u``; zero when i and a are both active. The
+  off-diagonal Fock block f^(1) is an optional spatial input ``f1[i, a]``
+  (hole i, particle a; the same for both spins, none between spins; its
+  active x active entries belong to the diagonal block F^(0) and are not
+  read); absent, it is 0;
+* modified Fock, Eq. (14): ``ft_a^i = f_a^i (1 + exp(-s D_a^i^2)) + [sum ...] exp(-s D_a^i^2)``;
   Table 1's ``ft_j^b`` is read as the same (Hermitian) element ``ft_b^j``;
 * densities (Fig. 1): gamma = 1 on core, G/2 per spin on the active block
   (G = spin-summed input), 0 on virtuals; eta = 1 - gamma;
 * cumulant: input ``L[u,v,x,y] = lambda_{u a, v b}^{x a, y b}`` (alpha, beta);
   same-spin blocks ``L[u,v,x,y] - L[u,v,y,x]``; the other opposite-spin
-  orderings follow from antisymmetry.
+  orderings follow from antisymmetry;
+* three-body cumulant (terms J and K): optional spin-orbital input
+  ``lam3[U,V,W,X,Y,Z] = lambda_{UVW}^{XYZ}`` over the active spin orbitals
+  (index ``2u + sigma``); absent, it is 0 and so are J and K.
 * the regulated denominators use ``-expm1(-x)`` for ``1 - exp(-x)`` and are 0
   when D == 0 (the limit of Sec. II.B's Maclaurin expansion).
 """
@@ -43,7 +50,7 @@ def _reg_t(D, s):
 class SpinOrbitalSystem:
     """Spin-orbital tensors over the full hole and particle spaces."""
 
-    def __init__(self, B, eps, gamma1, lambda2, s, ncore, nactive, nvirt):
+    def __init__(self, B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, lambda3=None, f1=None):
         nC, nA, nV = ncore, nactive, nvirt
         nH, nP = nC + nA, nA + nV
         B = np.asarray(B, dtype=float)
@@ -105,10 +112,17 @@ class SpinOrbitalSystem:
         # sum_{ux} D_u^x t_{ax}^{iu} gamma_u^x ; t_{ax}^{iu} = T2[i, u, a, x]
         T2_iuax = self.T2[:, aH][:, :, :, aP]                 # [i, u, a, x]
         S = np.einsum("ux,iuax,ux->ia", DUX, T2_iuax, gA)
-        self.T1 = S * _reg_t(D1, self.s)
         internal1 = self.actH[:, None] & self.actP[None, :]
+        F1 = np.zeros_like(S)
+        if f1 is not None:
+            F1 = np.asarray(f1, dtype=float)[hsp][:, psp] * (sH[:, None] == sP[None, :])
+            F1[internal1] = 0.0
+        self.F1 = F1
+        self.T1 = (F1 + S) * _reg_t(D1, self.s)
         self.T1[internal1] = 0.0
-        self.Ft = S * np.exp(-self.s * D1 ** 2)
+        g1 = np.exp(-self.s * D1 ** 2)
+        self.Ft = F1 * (1.0 + g1) + S * g1
+        self.lam3 = None if lambda3 is None else np.asarray(lambda3, dtype=float)
 
     @staticmethod
     def _lambda_so(L, nA):
@@ -167,9 +181,17 @@ class SpinOrbitalSystem:
         # I: + vt_{jx}^{bu} t_{ay}^{iv} gamma_i^j eta_b^a lambda_{uv}^{xy}
         out["I"] = np.einsum("jxbu,ivay,ji,ab,uvxy->", Vt[:, aH, :, aP], T[:, aH, :, aP],
                              g, et, lam, optimize="optimal")
-        # J and K need the three-body cumulant, which is not an input: 0.
-        out["J"] = 0.0
-        out["K"] = 0.0
+        # J: + 1/4 vt_{mz}^{uv} t_{xy}^{mw} lambda_{uvw}^{xyz}
+        # K: + 1/4 vt_{xy}^{we} t_{ez}^{uv} lambda_{uvw}^{xyz}
+        if self.lam3 is None:
+            out["J"] = 0.0
+            out["K"] = 0.0
+        else:
+            l3 = self.lam3
+            out["J"] = 0.25 * np.einsum("mzuv,mwxy,uvwxyz->", Vt[cH, aH, aP, aP],
+                                        T[cH, aH, aP, aP], l3, optimize="optimal")
+            out["K"] = 0.25 * np.einsum("xywe,uvez,uvwxyz->", Vt[aH, aH, aP, vP],
+                                        T[aH, aH, vP, aP], l3, optimize="optimal")
         return out
 
     # ----- Table 2: the eight pieces of term F -----
@@ -198,14 +220,14 @@ class SpinOrbitalSystem:
         return out
 
 
-def energy(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt) -> dict:
+def energy(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, lambda3=None, f1=None) -> dict:
     """Literal Table 1 energy and its Table 2 split.
 
     Returns the terms A-K, F1-F8, and the four reported blocks: ``ccvv`` = F1,
     ``cavv`` = F2, ``ccav`` = F3, ``active`` = everything else (total minus
     F1-F3), plus ``total``.
     """
-    so = SpinOrbitalSystem(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt)
+    so = SpinOrbitalSystem(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, lambda3, f1)
     t = so.terms()
     f = so.f_pieces()
     total = sum(t.values())

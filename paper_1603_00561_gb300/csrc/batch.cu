@@ -25,7 +25,7 @@ struct dsrg_batch {
   void* hi = nullptr;
   void* lo = nullptr;
   float* ybuf = nullptr;  // GEMM output of the CAVV/CCAV/active stage, reused molecule by molecule
-  CUtensorMap map_hi, map_lo;
+  dsrg::CcvvMaps maps;
   void* d_mols = nullptr;
   int4* d_items = nullptr;
   int* d_begin = nullptr;
@@ -140,8 +140,7 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
       return DSRG_ERR_OOM;
     }
     if (cudaMemset(b->hi, 0, plane) != cudaSuccess || cudaMemset(b->lo, 0, plane) != cudaSuccess ||
-        !dsrg::split_make_map(&b->map_hi, b->hi, bf16, rows, Qld, dsrg::split_kb_elems(bf16)) ||
-        !dsrg::split_make_map(&b->map_lo, b->lo, bf16, rows, Qld, dsrg::split_kb_elems(bf16))) {
+        !dsrg::split_make_ccvv_maps(&b->maps, b->hi, b->lo, bf16, rows, Qld)) {
       bfree(b);
       delete b;
       return DSRG_ERR_CUDA;
@@ -252,7 +251,7 @@ dsrg_status_t dsrg_batch_autotune(dsrg_batch_t* b, const double* const* B, const
     for (int r = 0; e == cudaSuccess && r <= reps; ++r) {
       if (r == 1) e = cudaEventRecord(e0, st);
       if (e == cudaSuccess)
-        e = dsrg::split_launch_ccvv(p0, b->map_hi, b->map_lo, b->d_mols, b->d_items, b->d_begin,
+        e = dsrg::split_launch_ccvv(p0, b->maps, b->d_mols, b->d_items, b->d_begin,
                                     b->grid, bf16, b->order >> 16);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -354,7 +353,7 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
       dsrg_plan* p0 = b->plans[0];
       e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
       if (e == cudaSuccess)
-        e = dsrg::split_launch_ccvv(p0, b->map_hi, b->map_lo, b->d_mols, b->d_items, b->d_begin,
+        e = dsrg::split_launch_ccvv(p0, b->maps, b->d_mols, b->d_items, b->d_begin,
                                     b->grid, b->prec == DSRG_PREC_BF16X3, b->order >> 16);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }

@@ -169,7 +169,16 @@ dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const d
 // Split planes shared by several molecules (tc_split.cu).
 bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
                     const CUtensorMap* shared_hi, const CUtensorMap* shared_lo);
-bool split_make_map(CUtensorMap* m, void* ptr, bool bf16, long long rows, int Qld, int kb_elems);
+// Tensor map of a plane buffer [rows][Qld]: boxes of kb_bytes of K by box_rows
+// rows, with the swizzle of the same span (32 or 64 bytes).
+bool split_make_map(CUtensorMap* m, void* ptr, bool bf16, long long rows, int Qld, int kb_bytes,
+                    int box_rows);
+// Maps of the CCVV kernel over one pair of planes: 128-row boxes, and 64-row
+// boxes for the B operand of a last virtual tile of at most 64 columns.
+struct CcvvMaps {
+  CUtensorMap hi, lo, hi64, lo64;
+};
+bool split_make_ccvv_maps(CcvvMaps* m, void* hi, void* lo, bool bf16, long long rows, int Qld);
 int split_plane_rows(const Sizes& z);
 int split_plane_qpad(const Sizes& z);
 int split_kb_elems(bool bf16);
@@ -187,9 +196,9 @@ void split_group_rows(const dsrg_plan* p, int g, int* h0, int* h1);
 cudaError_t split_launch_group(dsrg_plan* p, int g);
 cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols, int first, int n,
                              const double* const* eps, const double* s);
-cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,
-                              const void* d_mols, const int4* d_items, const int* d_begin,
-                              int grid, bool bf16, int prefetch);
+cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_mols,
+                              const int4* d_items, const int* d_begin, int grid, bool bf16,
+                              int prefetch);
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
                      std::vector<double>& cost, int order);
 extern const int SPLIT_ORDERS[];

@@ -169,6 +169,23 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   d |= (uint64_t)4 << 61;           // 64-byte swizzle
   return d;
 }
+// Shared-memory matrix descriptor: K-major operand, 32-byte swizzle, rows at a
+// 32-byte pitch (8-row groups 256 bytes apart); one MMA K step per row.
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;  // stride byte offset: 8 rows x 32 B
+  d |= (uint64_t)1 << 46;           // descriptor version of tcgen05
+  d |= (uint64_t)6 << 61;           // 32-byte swizzle
+  return d;
+}
+// Instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), both K-major, M = 128, N given
+// (a multiple of 16, 16..256).
+template <bool BF16>
+__host__ __device__ constexpr uint32_t idesc_128xn(uint32_t n) {
+  return (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) | ((n >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
 // Instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), both K-major, M = N = 128.
 template <bool BF16>
 __host__ __device__ constexpr uint32_t idesc_128x128() {

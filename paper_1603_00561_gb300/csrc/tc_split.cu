@@ -25,8 +25,12 @@
 //   warp 1      TMEM allocator and MMA issuer (one elected thread)
 //   warps 2-9   epilogue: 256 threads; warp w reads TMEM lanes 32*(w%4).. and
 //               columns 64*((w-2)/4).. of the tile (two warps per lane quarter)
-// Shared memory: 3 stages x 4 operand slots x 2 planes x (128 rows x 64 B),
-// 64-byte swizzle. TMEM: 2 buffers x (x, y) x 128 columns = 512 columns.
+// Shared memory: 6 stages x 4 operand slots x 2 planes x (128 rows x 32 B),
+// 32-byte swizzle: one MMA K step per stage, so that the buffer the MMAs hold
+// at any moment is small and 5 of the 6 stages can be in flight from L2. The
+// last virtual tile is as wide as the virtual space leaves it (N = its width
+// rounded up to 16); when that is at most 64, the slots read only as B operands
+// load 64 rows. TMEM: 2 buffers x (x, y) x 128 columns = 512 columns.
 // Every wait is bounded (about 2 s); on expiry the CTA records a status word,
 // drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -42,13 +46,15 @@
 namespace dsrg {
 
 constexpr int TT = 128;                      // tile edge (rows = TMEM lanes, columns)
-constexpr int KB_BYTES = 64;                 // K bytes per row per stage (64-byte swizzle span)
-constexpr int STAGES = 3;
-constexpr int SLOT_BYTES = TT * KB_BYTES;    // one operand tile of one plane: 8 KB
+constexpr int KB_BYTES = 32;                 // K bytes per row per stage: one MMA K step (32-byte swizzle span)
+constexpr int STAGES = 6;
+constexpr int SLOT_BYTES = TT * KB_BYTES;    // one operand tile of one plane: 4 KB
 constexpr int STAGE_BYTES = 4 * 2 * SLOT_BYTES;
+constexpr int GEMM_KB_BYTES = 64;            // K bytes per box of the tc_rest GEMM's maps (64-byte swizzle)
 constexpr int SPLIT_THREADS = 320;  // warps 0-1 roles, warps 2-9 epilogue
 constexpr int EPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
+constexpr int T_PITCH = TT + 1;  // row pitch (floats) of the transpose buffer: no bank conflicts
 
 struct SplitWs {
   int elt = 4, kb_elems = 16;
@@ -57,7 +63,8 @@ struct SplitWs {
   void* hi = nullptr;
   void* lo = nullptr;
   float* tail = nullptr;    // [rows + TAIL_PAD][TAIL_Q]  fl32(B) of the first TAIL_Q auxiliary functions
-  CUtensorMap map_hi, map_lo;
+  CUtensorMap map_hi, map_lo;  // 64-byte swizzled maps of the tc_rest GEMM
+  CcvvMaps cmaps;              // 32-byte swizzled maps of the CCVV kernel
   double* alpha = nullptr;  // [n_pairs][nVpad]  exp(4 s E_p e_b)
   double* pinfo = nullptr;  // [n_pairs][4]      E_p, exp(-2 s E_p^2), factorisable flag
   double* tau = nullptr;    // [nVpad][nVpad]    exp(-2 s (e_a + e_b)^2)
@@ -113,6 +120,10 @@ struct ItemPlan {
   int nload;            // slots to load: 0 .. nload-1 of the list `load`
   int load[4];          // slot ids to load
   int g1a, g1b, g2a, g2b;
+  int nB;               // MMA N: the columns of virtual tile Bt rounded up to 16
+  bool narrow;          // B-only slots (1, 3) of this item load 64 rows (nB <= 64, A != Bt)
+  bool ymma;            // y formed by its own MMAs (i != j, A != Bt)
+  bool ytr;             // y = x^T taken from x through shared memory (i != j, A == Bt)
 };
 
 __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const MolDesc** mdp) {
@@ -129,6 +140,15 @@ __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const
   ip.p = it.w / md->n_tp;
   ip.two = ip.i != ip.j;
   const bool dt = ip.A == ip.Bt;
+  const int nb = min(TT, md->nV - ip.Bt * TT);
+  ip.nB = (nb + 15) & ~15;
+  // slots 1 = (j, B) and 3 = (i, B) of an off-diagonal tile pair are read only as
+  // B operands (N rows); on a diagonal tile pair every slot is also an A operand
+  ip.narrow = !dt && ip.nB <= 64;
+  // on a diagonal tile pair y = v^{ji}[A,A] = (v^{ij}[A,A])^T: the epilogue
+  // transposes x instead of the tensor cores forming y
+  ip.ymma = ip.two && !dt;
+  ip.ytr = ip.two && dt;
   if (ip.two && !dt) {
     ip.nload = 4;
     ip.load[0] = 0; ip.load[1] = 1; ip.load[2] = 2; ip.load[3] = 3;
@@ -158,44 +178,42 @@ __device__ __forceinline__ int slot_row(const ItemPlan& ip, int slot, int nVpad)
   }
 }
 
-// The MMAs of one K stage of one item (two K steps of 16 BF16 / 8 TF32 values).
+// The MMAs of one K stage of one item (one K step of 16 BF16 / 8 TF32 values).
 // K runs from the last auxiliary function to the first and the small cross
 // products go before hi*hi: the accumulator truncates toward zero at every
 // instruction, and with the factors' magnitudes decreasing along Q this keeps
 // the accumulator small until the largest terms arrive, so few truncations act
 // on the full-size sum. hi*lo and hi*hi share their A operand, which the second
-// takes from the collector buffer.
+// takes from the collector buffer. N is the item's tile width (nB).
 template <bool BF16>
 __device__ __forceinline__ void ccvv_stage_mmas(uint32_t dx, uint32_t dy, uint32_t sb,
                                                 const ItemPlan& ip, int kb) {
-  constexpr uint32_t idesc = idesc_128x128<BF16>();
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const uint32_t off = (uint32_t)((1 - k) * 32);
-    const uint64_t a1h = desc_sw64(sb + (ip.g1a * 2 + 0) * SLOT_BYTES + off);
-    const uint64_t a1l = desc_sw64(sb + (ip.g1a * 2 + 1) * SLOT_BYTES + off);
-    const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + off);
-    const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + off);
-    const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-    tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
-    tc_mma<BF16, 1>(dx, a1h, b1l, idesc, 1u);
-    tc_mma<BF16, 2>(dx, a1h, b1h, idesc, 1u);
-    if (ip.two) {
-      const uint64_t a2h = desc_sw64(sb + (ip.g2a * 2 + 0) * SLOT_BYTES + off);
-      const uint64_t a2l = desc_sw64(sb + (ip.g2a * 2 + 1) * SLOT_BYTES + off);
-      const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + off);
-      const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + off);
-      tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
-      tc_mma<BF16, 1>(dy, a2h, b2l, idesc, 1u);
-      tc_mma<BF16, 2>(dy, a2h, b2h, idesc, 1u);
-    }
+  const uint32_t idesc = idesc_128xn<BF16>((uint32_t)ip.nB);
+  const uint64_t a1h = desc_sw32(sb + (ip.g1a * 2 + 0) * SLOT_BYTES);
+  const uint64_t a1l = desc_sw32(sb + (ip.g1a * 2 + 1) * SLOT_BYTES);
+  const uint64_t b1h = desc_sw32(sb + (ip.g1b * 2 + 0) * SLOT_BYTES);
+  const uint64_t b1l = desc_sw32(sb + (ip.g1b * 2 + 1) * SLOT_BYTES);
+  const uint32_t acc0 = kb > 0 ? 1u : 0u;
+  tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
+  tc_mma<BF16, 1>(dx, a1h, b1l, idesc, 1u);
+  tc_mma<BF16, 2>(dx, a1h, b1h, idesc, 1u);
+  if (ip.ymma) {
+    const uint64_t a2h = desc_sw32(sb + (ip.g2a * 2 + 0) * SLOT_BYTES);
+    const uint64_t a2l = desc_sw32(sb + (ip.g2a * 2 + 1) * SLOT_BYTES);
+    const uint64_t b2h = desc_sw32(sb + (ip.g2b * 2 + 0) * SLOT_BYTES);
+    const uint64_t b2l = desc_sw32(sb + (ip.g2b * 2 + 1) * SLOT_BYTES);
+    tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
+    tc_mma<BF16, 1>(dy, a2h, b2l, idesc, 1u);
+    tc_mma<BF16, 2>(dy, a2h, b2h, idesc, 1u);
   }
 }
 
 template <bool BF16>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     ccvv_split_kernel(const __grid_constant__ CUtensorMap map_hi,
-                      const __grid_constant__ CUtensorMap map_lo, const SplitArgs a) {
+                      const __grid_constant__ CUtensorMap map_lo,
+                      const __grid_constant__ CUtensorMap map_hi64,
+                      const __grid_constant__ CUtensorMap map_lo64, const SplitArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* tiles = smem;
@@ -210,6 +228,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
   double* sAlpha = sEps + TT;
   double* sRed = sAlpha + TT;
   float* sEpsF = (float*)(sRed + EPI_WARPS);
+  float* sT = sEpsF + TT;  // [32][T_PITCH]: 32 rows of x, transposed by the epilogue
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int it0 = a.cta_begin[blockIdx.x], it1 = a.cta_begin[blockIdx.x + 1];
@@ -244,6 +263,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&map_hi) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&map_lo) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&map_hi64) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)&map_lo64) : "memory");
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -263,13 +284,20 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
             break;
           }
           uint8_t* st = tiles + stage * STAGE_BYTES;
-          mbar_expect_tx(&full[stage], (uint32_t)(ip.nload * 2 * SLOT_BYTES));
+          uint32_t bytes = 0;
+          for (int l = 0; l < ip.nload; ++l)
+            bytes += (ip.narrow && (ip.load[l] & 1)) ? SLOT_BYTES : 2 * SLOT_BYTES;
+          mbar_expect_tx(&full[stage], bytes);
           const int kq = md->kq0 + (kblocks - 1 - kb) * KE;
           for (int l = 0; l < ip.nload; ++l) {
             const int sl = ip.load[l];
             const int row = row0 + slot_row(ip, sl, nVpad);
-            tma_load_2d(st + (sl * 2 + 0) * SLOT_BYTES, &map_hi, &full[stage], kq, row);
-            tma_load_2d(st + (sl * 2 + 1) * SLOT_BYTES, &map_lo, &full[stage], kq, row);
+            // B-only slots (odd ids) of a narrow last tile: the first 64 rows
+            const bool half = ip.narrow && (sl & 1);
+            tma_load_2d(st + (sl * 2 + 0) * SLOT_BYTES, half ? &map_hi64 : &map_hi, &full[stage], kq,
+                        row);
+            tma_load_2d(st + (sl * 2 + 1) * SLOT_BYTES, half ? &map_lo64 : &map_lo, &full[stage], kq,
+                        row);
           }
           if (a.prefetch > 0) {
             // L2 prefetch of the stage `prefetch` ahead (in this item or the next)
@@ -411,62 +439,97 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       bool ok = mbar_wait(&tfull[tbuf], tphase, abort_flag, a.status);
       tc_fence_after();
       double acc = 0.0;
-      if (ok) {
-        const uint32_t tx = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * 256);
-        const uint32_t ty = tx + 128;
-        for (int c0 = cbeg; c0 < cend; c0 += 16) {
-          uint32_t xr[16], yr[16];
-          tmem_ld16(tx + c0, xr);
-          if (ip.two) tmem_ld16(ty + c0, yr);
-          tmem_ld_wait();
-          if (!rok) continue;
-          // the first TAIL_Q auxiliary functions, the largest terms, in FP32
-          // round-to-nearest (the tensor cores took the rest)
-          tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
-          if (ip.two)
-            tail_add16(tail_ja, md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
-          if (far) {
+      // x_ab (and y_ab) of the 16 columns from c0: the FP32 terms of the first
+      // auxiliary functions, then the regulated exchange combination in FP64
+      auto chunk = [&](int c0, uint32_t (&xr)[16], uint32_t (&yr)[16]) {
+        // the first TAIL_Q auxiliary functions, the largest terms, in FP32
+        // round-to-nearest (the tensor cores took the rest)
+        tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
+        if (ip.two)
+          tail_add16(tail_ja, md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
+        if (far) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int cb = c0 + k;
-              if (cb >= cend) break;
-              const float xf = __uint_as_float(xr[k]);
-              const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
-              const double D = ca - sEps[cb];
-              float r0f;
-              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
-              const double r0 = (double)r0f;
-              const double R = fma(r0, fma(-D, r0, 1.0), r0);   // 1/D, one Newton step
-              acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
-            }
-          } else if (fast) {
+          for (int k = 0; k < 16; ++k) {
+            const int cb = c0 + k;
+            if (cb >= cend) break;
+            const float xf = __uint_as_float(xr[k]);
+            const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+            const double D = ca - sEps[cb];
+            float r0f;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
+            const double r0 = (double)r0f;
+            const double R = fma(r0, fma(-D, r0, 1.0), r0);   // 1/D, one Newton step
+            acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
+          }
+        } else if (fast) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int cb = c0 + k;
-              if (cb >= cend) break;
-              const float xf = __uint_as_float(xr[k]);
-              const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
-              const double D = ca - sEps[cb];
-              const double g = ha * sAlpha[cb] * taucol[(size_t)cb * nVpad];
-              float r0f;
-              asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
-              const double r0 = (double)r0f;             // 1/D to ~2^-22
-              const double e = fma(-D, r0, 1.0);         // Newton-Raphson residual
-              const double R0 = fma(-g, r0, r0);         // (1 - g) / D, seed accuracy
-              const double R = fma(R0, e, R0);           // one Newton step: ~2^-44
-              acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
-            }
-          } else {
+          for (int k = 0; k < 16; ++k) {
+            const int cb = c0 + k;
+            if (cb >= cend) break;
+            const float xf = __uint_as_float(xr[k]);
+            const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+            const double D = ca - sEps[cb];
+            const double g = ha * sAlpha[cb] * taucol[(size_t)cb * nVpad];
+            float r0f;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
+            const double r0 = (double)r0f;             // 1/D to ~2^-22
+            const double e = fma(-D, r0, 1.0);         // Newton-Raphson residual
+            const double R0 = fma(-g, r0, r0);         // (1 - g) / D, seed accuracy
+            const double R = fma(R0, e, R0);           // one Newton step: ~2^-44
+            acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
+          }
+        } else {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int cb = c0 + k;
-              if (cb >= cend) break;
-              const double xd = __uint_as_float(xr[k]);
-              const double yd = ip.two ? (double)__uint_as_float(yr[k]) : xd;
-              const double D = ca - sEps[cb];
-              acc = fma(fma(xd, xd - yd, yd * yd), reg_f1(D, s), acc);
+          for (int k = 0; k < 16; ++k) {
+            const int cb = c0 + k;
+            if (cb >= cend) break;
+            const double xd = __uint_as_float(xr[k]);
+            const double yd = ip.two ? (double)__uint_as_float(yr[k]) : xd;
+            const double D = ca - sEps[cb];
+            acc = fma(fma(xd, xd - yd, yd * yd), reg_f1(D, s), acc);
+          }
+        }
+      };
+      const uint32_t tx = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * 256);
+      const uint32_t ty = tx + 128;
+      if (!ip.ytr) {
+        if (ok) {
+          for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            uint32_t xr[16], yr[16];
+            tmem_ld16(tx + c0, xr);
+            if (ip.two) tmem_ld16(ty + c0, yr);
+            tmem_ld_wait();
+            if (rok) chunk(c0, xr, yr);
+          }
+        }
+      } else {
+        // y = x^T in four passes of 32 rows of x: the two warps holding TMEM
+        // lanes 32p..32p+31 store their rows to shared memory, then the warps
+        // whose columns are 32p..32p+31 read them back transposed. Every pass
+        // meets both barriers whatever `ok` is.
+        for (int pass = 0; pass < 4; ++pass) {
+          if (ok && quarter == pass) {
+            for (int c = cbeg; c < cbeg + 64; c += 16) {
+              uint32_t xr[16];
+              tmem_ld16(tx + c, xr);
+              tmem_ld_wait();
+#pragma unroll
+              for (int k = 0; k < 16; ++k) sT[lane * T_PITCH + c + k] = __uint_as_float(xr[k]);
             }
           }
+          named_bar(1, 32 * EPI_WARPS);
+          if (ok && (cbeg >> 6) == (pass >> 1)) {
+            for (int c0 = 32 * pass; c0 < 32 * pass + 32 && c0 < cend; c0 += 16) {
+              uint32_t xr[16], yr[16];
+              tmem_ld16(tx + c0, xr);
+              tmem_ld_wait();
+#pragma unroll
+              for (int k = 0; k < 16; ++k)
+                yr[k] = __float_as_uint(sT[(c0 - 32 * pass + k) * T_PITCH + row]);
+              if (rok) chunk(c0, xr, yr);
+            }
+          }
+          named_bar(1, 32 * EPI_WARPS);
         }
       }
       // release this TMEM buffer to the MMA issuer
@@ -675,19 +738,28 @@ bool split_supported(const dsrg_plan* p, std::string* why) {
   return true;
 }
 
-bool split_make_map(CUtensorMap* m, void* ptr, bool bf16, long long rows, int Qld, int kb_elems) {
+bool split_make_map(CUtensorMap* m, void* ptr, bool bf16, long long rows, int Qld, int kb_bytes,
+                    int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   const int elt = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)Qld, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Qld * elt};
-  cuuint32_t box[2] = {(cuuint32_t)kb_elems, (cuuint32_t)TT};
+  cuuint32_t box[2] = {(cuuint32_t)(kb_bytes / elt), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw =
+      kb_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
   CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                  ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+bool split_make_ccvv_maps(CcvvMaps* m, void* hi, void* lo, bool bf16, long long rows, int Qld) {
+  return split_make_map(&m->hi, hi, bf16, rows, Qld, KB_BYTES, TT) &&
+         split_make_map(&m->lo, lo, bf16, rows, Qld, KB_BYTES, TT) &&
+         split_make_map(&m->hi64, hi, bf16, rows, Qld, KB_BYTES, TT / 2) &&
+         split_make_map(&m->lo64, lo, bf16, rows, Qld, KB_BYTES, TT / 2);
 }
 
 int split_ccvv_blocks(const dsrg_plan* p) {
@@ -710,7 +782,8 @@ size_t split_tail_bytes(const Sizes& z) {
 // dealt to the CTA with the least accumulated cost (ties: lowest index), which
 // is round-robin for uniform costs (operand tiles of one pair stay close in
 // time, so they are re-read from L2) and balances uneven molecules. Cost of an
-// item: its K blocks times its GEMM count, plus a fixed epilogue share.
+// item: its K stages times its GEMM count times its tile width, plus a fixed
+// epilogue share.
 void split_schedule(const std::vector<int4>& items, const std::vector<double>& cost, int ncta,
                     std::vector<int4>& out, std::vector<int>& begin) {
   std::vector<double> load(ncta, 0.0);
@@ -747,7 +820,11 @@ void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& it
   auto tp_index = [&](int A, int B) { return A * nT - A * (A - 1) / 2 + (B - A); };
   auto push = [&](int i, int j, int A, int B) {
     items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, pair_index(i, j) * n_tp + tp_index(A, B)));
-    cost.push_back((double)kblocks * (i == j ? 1.0 : 2.0) + 24.0);
+    // MMA work: one GEMM for i = j or a diagonal tile pair (y = x^T), else two,
+    // each as wide as tile B; plus a fixed share for the epilogue
+    const int nb = z.nV - B * TT < TT ? z.nV - B * TT : TT;
+    const double width = (double)((nb + 15) & ~15) / TT;
+    cost.push_back((double)kblocks * (i == j || A == B ? 1.0 : 2.0) * width + 48.0);
   };
   const int G = order >> 1;
   if (G <= 0) {
@@ -817,9 +894,10 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
   if (cudaMemset(w->tail, 0, split_tail_bytes(z)) != cudaSuccess) return false;
   if (!hi && (cudaMemset(w->hi, 0, plane) != cudaSuccess || cudaMemset(w->lo, 0, plane) != cudaSuccess))
     return false;
-  // this molecule's own maps (CAVV kernel, single-molecule CCVV)
-  if (!split_make_map(&w->map_hi, w->hi, bf16, w->rows, Qld, w->kb_elems)) return false;
-  if (!split_make_map(&w->map_lo, w->lo, bf16, w->rows, Qld, w->kb_elems)) return false;
+  // this molecule's own maps: the tc_rest GEMM's, and the single-molecule CCVV kernel's
+  if (!split_make_map(&w->map_hi, w->hi, bf16, w->rows, Qld, GEMM_KB_BYTES, TT)) return false;
+  if (!split_make_map(&w->map_lo, w->lo, bf16, w->rows, Qld, GEMM_KB_BYTES, TT)) return false;
+  if (!split_make_ccvv_maps(&w->cmaps, w->hi, w->lo, bf16, w->rows, Qld)) return false;
   (void)shared_hi;
   (void)shared_lo;
   // descriptor (eps and s are filled per call)
@@ -929,7 +1007,7 @@ cudaError_t split_launch_group(dsrg_plan* p, int g) {
   SplitWs* w = p->split;
   const SplitWs::Group& G = w->groups[g];
   if (G.n == 0) return cudaSuccess;
-  return split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, G.d_items, G.d_begin, G.grid,
+  return split_launch_ccvv(p, w->cmaps, w->d_mol, G.d_items, G.d_begin, G.grid,
                            p->prec == DSRG_PREC_BF16X3, w->order >> 16);
 }
 
@@ -949,7 +1027,7 @@ cudaError_t split_time_ccvv(dsrg_plan* p, int reps, float* ms) {
   const bool bf16 = p->prec == DSRG_PREC_BF16X3;
   e = cudaEventRecord(e0, p->stream);
   for (int r = 0; e == cudaSuccess && r < reps; ++r)
-    e = split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, w->d_items, w->d_begin, w->grid, bf16,
+    e = split_launch_ccvv(p, w->cmaps, w->d_mol, w->d_items, w->d_begin, w->grid, bf16,
                           w->order >> 16);
   if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -982,7 +1060,8 @@ void split_free(dsrg_plan* p) {
 }
 
 static size_t split_smem_bytes() {
-  return (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (2 * TT + EPI_WARPS) * 8 + TT * 4 + 64;
+  return (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (2 * TT + EPI_WARPS) * 8 + TT * 4 +
+         32 * T_PITCH * 4 + 64;
 }
 
 // Planes (and FP32 tail rows) of the hole rows h0 <= h < h1 of B.
@@ -1082,9 +1161,9 @@ cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols_v, int first, int n,
   return cudaSuccess;
 }
 
-cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtensorMap& ml,
-                              const void* d_mols, const int4* d_items, const int* d_begin,
-                              int grid, bool bf16, int prefetch) {
+cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_mols,
+                              const int4* d_items, const int* d_begin, int grid, bool bf16,
+                              int prefetch) {
   SplitArgs a;
   a.mols = (const MolDesc*)d_mols;
   a.items = d_items;
@@ -1095,10 +1174,12 @@ cudaError_t split_launch_ccvv(dsrg_plan* p, const CUtensorMap& mh, const CUtenso
   const size_t sm = split_smem_bytes();
   if (bf16) {
     raise_smem_limit((const void*)ccvv_split_kernel<true>, sm);
-    ccvv_split_kernel<true><<<grid, SPLIT_THREADS, sm, p->stream>>>(mh, ml, a);
+    ccvv_split_kernel<true><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo, maps.hi64,
+                                                                    maps.lo64, a);
   } else {
     raise_smem_limit((const void*)ccvv_split_kernel<false>, sm);
-    ccvv_split_kernel<false><<<grid, SPLIT_THREADS, sm, p->stream>>>(mh, ml, a);
+    ccvv_split_kernel<false><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo, maps.hi64,
+                                                                     maps.lo64, a);
   }
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
@@ -1114,7 +1195,7 @@ cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, 
   cudaError_t e = split_stage(p, B, eps, s);
   if (e != cudaSuccess) return e;
   if ((e = split_prepare_single(p, eps, s)) != cudaSuccess) return e;
-  return split_launch_ccvv(p, w->map_hi, w->map_lo, w->d_mol, w->d_items,
+  return split_launch_ccvv(p, w->cmaps, w->d_mol, w->d_items,
                            w->d_begin, w->grid, p->prec == DSRG_PREC_BF16X3, w->order >> 16);
 }
 
