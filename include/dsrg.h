@@ -7,16 +7,16 @@
  *   E2(s) = <[H~(1)(s), T(1)(s)]>                      (Sec. II.B, Eq. (11))
  *
  * with the first-order amplitudes of Eqs. (12)-(13), the modified Fock and
- * integrals of Eqs. (14)-(15), the terms of Table 1 (A-I; J and K need the
- * three-body cumulant, which is not an input, and are 0), and the split of
- * term F into the diagrams F1-F8 of Table 2. The energy is reported per
- * block:
+ * integrals of Eqs. (14)-(15), the terms of Table 1 (A-K; J and K need the
+ * three-body cumulant, an optional input of dsrg_mrpt2_energy_ext, and are 0
+ * without it), and the split of term F into the diagrams F1-F8 of Table 2.
+ * The energy is reported per block:
  *
  *   out[0] = E_CCVV   diagram F1, Eq. (23): sum over core pairs (m,n) and
  *                     virtual pairs (e,f) of |v_mn^ef|^2 (1-exp(-2sD^2))/D
  *   out[1] = E_CAVV   diagram F2 (Table 2)
  *   out[2] = E_CCAV   diagram F3 (Table 2)
- *   out[3] = E_active terms A-E, G-I (Table 1) and F4-F8 (Table 2)
+ *   out[3] = E_active terms A-E, G-K (Table 1) and F4-F8 (Table 2)
  *   out[4] = E_total  the sum of the four blocks
  *
  * Problem statement (Sec. II.A, II.B, II.C):
@@ -24,7 +24,8 @@
  *     V (nV), ordered [core | active | virtual]; holes H = C+A (nH = nC+nA),
  *     particles P = A+V (nP = nA+nV);
  *   - orbitals are semicanonical: eps[p] is the diagonal of the generalized
- *     Fock matrix (Eq. (8)); the off-diagonal block f^(1) is taken as 0;
+ *     Fock matrix (Eq. (8)); the off-diagonal block f^(1) is an optional input
+ *     of the _ext entry points (0 otherwise);
  *   - two-electron integrals are factorised, (pq|rs) = sum_Q B^Q_pq B^Q_rs
  *     (Eq. (19)); every term reads B only on hole x particle index pairs, so
  *     the caller passes that block;
@@ -122,6 +123,27 @@ dsrg_status_t dsrg_mrpt2_energy(dsrg_plan_t *plan, const double *B, const double
                                 const double *gamma1, const double *lambda2, double s,
                                 double *out_dev);
 
+/* Energy as dsrg_mrpt2_energy with the two optional inputs of the full
+ * Table 1 (either may be NULL, read as 0):
+ *   lambda3 [2nA]^6  the three-body cumulant of the reference (Sec. II.A) in
+ *                    spin orbitals, lambda3[((((U*n2+V)*n2+W)*n2+X)*n2+Y)*n2+Z] =
+ *                    lambda_{UVW}^{XYZ}, n2 = 2 nA, active spin orbital
+ *                    U = 2u + sigma (sigma 0 = alpha, 1 = beta); it enters
+ *                    terms J (1/4 vt_{mz}^{uv} t_{xy}^{mw} lambda_{uvw}^{xyz}) and
+ *                    K (1/4 vt_{xy}^{we} t_{ez}^{uv} lambda_{uvw}^{xyz}) of Table 1,
+ *                    reported in out[3]; ignored when nA == 0;
+ *   f1 [nH][nP]      the off-diagonal block f^(1) of the generalized Fock matrix
+ *                    (Eq. (8)) in the semicanonical basis, f1[i*nP + a] = f_a^i for
+ *                    hole i and particle a (the same for both spins); it enters
+ *                    the T1 amplitude (Eq. (12)) and the modified Fock matrix
+ *                    (Eq. (14)), hence terms A-E (out[3]); its active x active
+ *                    entries belong to the diagonal block F^(0) and are not read.
+ * Both are caller-owned device arrays, 8-byte aligned. */
+dsrg_status_t dsrg_mrpt2_energy_ext(dsrg_plan_t *plan, const double *B, const double *eps,
+                                    const double *gamma1, const double *lambda2,
+                                    const double *lambda3, const double *f1, double s,
+                                    double *out_dev);
+
 /* Pair energies of diagram F1 (Eq. (23)): pairs_dev[nC][nC] on the device,
  * e_mn = sum_ef v_ef (2 v_ef - v_fe) (1-exp(-2 s D^2))/D with v_ef = (me|nf);
  * their sum is out[0] of dsrg_mrpt2_energy. Same arguments and rules. */
@@ -140,6 +162,15 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t *plan, const double *B, const d
                                      const double *gamma1, const double *lambda2, double s,
                                      double *out_dev, double *dB_dev, double *deps_dev,
                                      double *ds_dev);
+
+/* Energy and gradient as dsrg_mrpt2_energy_grad with the optional lambda3
+ * and f1 of dsrg_mrpt2_energy_ext (treated as constants: no gradient with
+ * respect to them). */
+dsrg_status_t dsrg_mrpt2_energy_grad_ext(dsrg_plan_t *plan, const double *B, const double *eps,
+                                         const double *gamma1, const double *lambda2,
+                                         const double *lambda3, const double *f1, double s,
+                                         double *out_dev, double *dB_dev, double *deps_dev,
+                                         double *ds_dev);
 
 /* Same as dsrg_mrpt2_energy with HOST inputs and a HOST out[5]: copies the
  * inputs into plan-owned device staging (plan created with DSRG_PLAN_HOST_IO),
@@ -252,15 +283,17 @@ dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t *sz, const double *B, 
  * paper has no counterpart; a diagnostic of which arithmetic evaluated the
  * regulators of Eqs. (13), (15) and (23)). Counted since the plan was created
  * or last reset; FP64 plans leave them at 0. Indices:
- *   DSRG_COUNT_CCVV_FAR       CCVV work items (core pair x tile pair) whose every
- *                             |Delta| is so large that exp(-2 s Delta^2) < 2^-63,
- *                             evaluated as 1/Delta;
- *   DSRG_COUNT_CCVV_FACTORED  items with every |Delta| >= 1/4 evaluated from the
+ *   DSRG_COUNT_CCVV_FAR       CCVV epilogue blocks (32 virtual rows x 16 virtual
+ *                             columns of one core pair) whose every |Delta| is so
+ *                             large that exp(-2 s Delta^2) < 2^-63, evaluated as
+ *                             1/Delta;
+ *   DSRG_COUNT_CCVV_FACTORED  blocks with every |Delta| >= 1/4 evaluated from the
  *                             factorised exponentials;
- *   DSRG_COUNT_CCVV_DIRECT    items with some |Delta| < 1/4 (or a pair whose
+ *   DSRG_COUNT_CCVV_DIRECT    blocks with some |Delta| < 1/4 (or of a pair whose
  *                             factors could overflow), evaluated with expm1 per
  *                             element (R(0) = 0) and the exchange combination in FP64;
- *   DSRG_COUNT_CCVV_UNFACTORABLE items of pairs whose factors could overflow;
+ *   DSRG_COUNT_CCVV_UNFACTORABLE work items (core pair x tile pair) of pairs whose
+ *                             factors could overflow;
  *   DSRG_COUNT_CAVV_NEAR      CAVV positions (core m, e, f) with some |Delta_u| < 1/4
  *                             (or a non-factorisable (m, u)), evaluated in FP64 with
  *                             expm1;

@@ -378,8 +378,9 @@ def energy_and_grad(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt, lambda3=N
     act = active_block(Bt, et, gamma1, lambda2, st, ncore, nactive, nvirt, lambda3=lambda3, f1=f1)
     tot = e + f2 + f3 + act
     dB, de, ds = torch.autograd.grad(tot, (Bt, et, st))
-    return dict(ccvv=float(e), cavv=float(f2), ccav=float(f3), active=float(act),
-                total=float(tot), dB=dB.numpy(), deps=de.numpy(), ds=float(ds))
+    return dict(ccvv=float(e.detach()), cavv=float(f2.detach()), ccav=float(f3.detach()),
+                active=float(act.detach()), total=float(tot.detach()), dB=dB.numpy(),
+                deps=de.numpy(), ds=float(ds))
 
 
 def block_grads(B, eps, gamma1, lambda2, s, ncore, nactive, nvirt) -> dict:

@@ -82,14 +82,22 @@ class Plan:
         return int(self.lib.dsrg_plan_workspace_bytes(self.h))
 
     # -- entry points ------------------------------------------------------------------------
-    def energy(self, B, eps, gamma1, lambda2, s: float, out=None):
-        """Block energies [E_CCVV, E_CAVV, E_CCAV, E_active, E_total] as a device tensor."""
+    def energy(self, B, eps, gamma1, lambda2, s: float, out=None, lambda3=None, f1=None):
+        """Block energies [E_CCVV, E_CAVV, E_CCAV, E_active, E_total] as a device tensor.
+        ``lambda3`` (spin-orbital three-body cumulant, [2nA]^6) and ``f1`` (off-diagonal
+        Fock block, [nH, nP]) are optional (``dsrg_mrpt2_energy_ext``)."""
         if out is None:
             out = torch.empty(5, dtype=torch.float64, device=self.device)
         self._stream()
-        st = self.lib.dsrg_mrpt2_energy(self.h, _ptr(B), _ptr(eps), _ptr(gamma1), _ptr(lambda2),
-                                        float(s), _ptr(out))
-        self._check(st, "dsrg_mrpt2_energy")
+        if lambda3 is None and f1 is None:
+            st = self.lib.dsrg_mrpt2_energy(self.h, _ptr(B), _ptr(eps), _ptr(gamma1),
+                                            _ptr(lambda2), float(s), _ptr(out))
+            self._check(st, "dsrg_mrpt2_energy")
+        else:
+            st = self.lib.dsrg_mrpt2_energy_ext(self.h, _ptr(B), _ptr(eps), _ptr(gamma1),
+                                                _ptr(lambda2), _ptr(lambda3), _ptr(f1), float(s),
+                                                _ptr(out))
+            self._check(st, "dsrg_mrpt2_energy_ext")
         return out
 
     def pair_energies(self, B, eps, s: float, out=None):
@@ -102,17 +110,18 @@ class Plan:
         self._check(st, "dsrg_ccvv_pair_energies")
         return out
 
-    def energy_grad(self, B, eps, gamma1, lambda2, s: float):
-        """Energies plus dE_total/dB, dE_total/deps, dE_total/ds (device tensors)."""
+    def energy_grad(self, B, eps, gamma1, lambda2, s: float, lambda3=None, f1=None):
+        """Energies plus dE_total/dB, dE_total/deps, dE_total/ds (device tensors);
+        optional ``lambda3`` and ``f1`` as for ``energy``."""
         out = torch.empty(5, dtype=torch.float64, device=self.device)
         dB = torch.empty_like(B)
         de = torch.empty_like(eps)
         ds = torch.empty(1, dtype=torch.float64, device=self.device)
         self._stream()
-        st = self.lib.dsrg_mrpt2_energy_grad(self.h, _ptr(B), _ptr(eps), _ptr(gamma1),
-                                             _ptr(lambda2), float(s), _ptr(out), _ptr(dB),
-                                             _ptr(de), _ptr(ds))
-        self._check(st, "dsrg_mrpt2_energy_grad")
+        st = self.lib.dsrg_mrpt2_energy_grad_ext(self.h, _ptr(B), _ptr(eps), _ptr(gamma1),
+                                                 _ptr(lambda2), _ptr(lambda3), _ptr(f1), float(s),
+                                                 _ptr(out), _ptr(dB), _ptr(de), _ptr(ds))
+        self._check(st, "dsrg_mrpt2_energy_grad_ext")
         return out, dB, de, ds
 
     def energy_host(self, B, eps, gamma1, lambda2, s: float, out=None):
@@ -290,6 +299,12 @@ def energy_total(plan, B, eps, s, gamma1=None, lambda2=None):
     if not isinstance(s, torch.Tensor):
         s = torch.tensor(float(s), dtype=torch.float64, device=B.device)
     return DSRGEnergy.apply(B, eps, s, gamma1, lambda2, plan)
+
+
+def extra_to_device(problem, device="cuda"):
+    """The optional (lambda3, f1) of a ``dsrg_synth.Problem`` as FP64 device tensors (or None)."""
+    f = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64).contiguous().to(device)
+    return f(problem.lambda3), f(problem.f1)
 
 
 def to_device(problem, device="cuda"):

@@ -26,7 +26,8 @@ EXPORTS = [
     "dsrg_batch_launch_count", "dsrg_batch_last_error", "dsrg_ccvv_energy_noalloc",
     "dsrg_plan_autotune", "dsrg_batch_autotune", "dsrg_plan_item_order", "dsrg_batch_item_order",
     "dsrg_plan_time_ccvv", "dsrg_plan_set_item_order", "dsrg_batch_set_item_order",
-    "dsrg_plan_selftest_wait_timeout", "dsrg_plan_branch_counts",
+    "dsrg_plan_selftest_wait_timeout", "dsrg_plan_branch_counts", "dsrg_mrpt2_energy_ext",
+    "dsrg_mrpt2_energy_grad_ext",
 ]
 # indices of dsrg_plan_branch_counts
 NCOUNTERS = 8
@@ -63,6 +64,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_ccvv_pair_energies.restype = st
     lib.dsrg_mrpt2_energy_grad.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp, vp, vp, vp]
     lib.dsrg_mrpt2_energy_grad.restype = st
+    lib.dsrg_mrpt2_energy_ext.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_double, vp]
+    lib.dsrg_mrpt2_energy_ext.restype = st
+    lib.dsrg_mrpt2_energy_grad_ext.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp, vp,
+                                               vp]
+    lib.dsrg_mrpt2_energy_grad_ext.restype = st
     lib.dsrg_mrpt2_energy_host.argtypes = [vp, vp, vp, vp, vp, C.c_double, vp]
     lib.dsrg_mrpt2_energy_host.restype = st
     lib.dsrg_plan_sync.argtypes = [vp]

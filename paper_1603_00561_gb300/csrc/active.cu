@@ -253,10 +253,13 @@ __global__ void build_tables_kernel(const double* __restrict__ eps, const double
   }
 }
 
-// T1 amplitudes and modified Fock elements over spin orbitals [2nH][2nP].
+// T1 amplitudes and modified Fock elements over spin orbitals [2nH][2nP]
+// (Eqs. (12), (14)); f1 is the optional off-diagonal Fock block [nH][nP]
+// (spatial, spin-diagonal; its active x active entries are not read).
 __global__ void t1_kernel(const double* __restrict__ eps, double s, Sizes z,
                           const double* __restrict__ W1T, const double* __restrict__ gA,
-                          double* __restrict__ t1, double* __restrict__ ft) {
+                          const double* __restrict__ f1, double* __restrict__ t1,
+                          double* __restrict__ ft) {
   const ActDims d = act_dims(z);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.nH2 * d.nP2) return;
@@ -271,8 +274,31 @@ __global__ void t1_kernel(const double* __restrict__ eps, double s, Sizes z,
     }
   const double D1 = eps[I >> 1] - eps[z.nC + (A >> 1)];
   const bool internal = (I >= d.nC2) && (A < d.nA2);
-  t1[k] = internal ? 0.0 : S * reg_t(D1, s);
-  ft[k] = S * exp(-s * D1 * D1);
+  const double F = (f1 && !internal && (I & 1) == (A & 1)) ? f1[(size_t)(I >> 1) * z.nP + (A >> 1)]
+                                                           : 0.0;
+  const double g = exp(-s * D1 * D1);
+  t1[k] = internal ? 0.0 : (F + S) * reg_t(D1, s);
+  ft[k] = fma(F, 1.0 + g, S * g);
+}
+
+// Term A with no active orbitals (the only term then, from f^(1)): per core
+// orbital m, 2 sum_e f_me^2 (1 + exp(-s D^2)) (1 - exp(-s D^2)) / D, D = e_m - e_e
+// (the factor 2 is the spin sum). f1 == null: 0.
+__global__ void __launch_bounds__(128) singles_kernel(const double* __restrict__ eps, double s,
+                                                      Sizes z, const double* __restrict__ f1,
+                                                      double* __restrict__ partials) {
+  __shared__ double red[4];
+  const int m = blockIdx.x;
+  double acc = 0.0;
+  if (f1) {
+    for (int e = threadIdx.x; e < z.nP; e += 128) {
+      const double D = eps[m] - eps[z.nC + e];
+      const double f = f1[(size_t)m * z.nP + e];
+      acc = fma(f * f * (1.0 + exp(-s * D * D)), reg_t(D, s), acc);
+    }
+  }
+  const double tot = block_sum<128>(acc, red);
+  if (threadIdx.x == 0) partials[m] = 2.0 * tot;
 }
 
 // gamma (over holes) and eta (over particles) as sparse row lookups.
@@ -589,12 +615,19 @@ __global__ void actvv_reduce_kernel(int nA4, int nblk, const double* __restrict_
 // Active block: one kernel, one term per blockIdx.y, one outer index per thread.
 // ---------------------------------------------------------------------------
 enum Term {
-  T_A = 0, T_B, T_C, T_D, T_E, T_GVA, T_GVV, T_H, T_I, T_F4, T_F5, T_F6, T_F7, T_F8, N_TERMS
+  T_A = 0, T_B, T_C, T_D, T_E, T_GVA, T_GVV, T_H, T_I, T_F4, T_F5, T_F6, T_F7, T_F8, T_J, T_K,
+  N_TERMS
 };
 
 struct TermArgs {
   const double *W1V, *W1T, *W1Vt, *W2V, *W2T, *W2Vt, *Ti, *lam, *gA, *t1, *ft, *P12;
+  const double* lam3;  // [2nA]^6 spin-orbital three-body cumulant, or null (J = K = 0)
 };
+
+// Index of lambda_{UVW}^{XYZ} in the spin-orbital three-body cumulant.
+__device__ __forceinline__ size_t lam3i(int n2, int U, int V, int W, int X, int Y, int Z) {
+  return (((((size_t)U * n2 + V) * n2 + W) * n2 + X) * n2 + Y) * n2 + Z;
+}
 
 __device__ __forceinline__ double ga(const ActDims& d, const double* gA, int U, int V) {
   return gA[U * d.nA2 + V];
@@ -636,6 +669,8 @@ __device__ __forceinline__ long term_count(int term, const ActDims& d) {
     case T_F6: return (long)d.nC2 * d.nV2 * a2;
     case T_F7: return (long)d.nV2 * a2 * d.nA2;
     case T_F8: return (long)d.nC2 * a2 * d.nA2;
+    case T_J: return (long)d.nC2 * a2 * d.nA2;
+    case T_K: return (long)d.nV2 * a2 * d.nA2;
   }
   return 0;
 }
@@ -777,6 +812,46 @@ __device__ double term_value(int term, long o, const Sizes& z, const ActDims& d,
         }
       }
       return vt * c;
+    }
+    case T_J: {  // 1/4 vt_{mz}^{uv} t_{xy}^{mw} lambda_{uvw}^{xyz}, outer (M, W, X, Y)
+      if (!t.lam3) return 0.0;
+      const int Y = (int)(o % nA2), X = (int)((o / nA2) % nA2), W = (int)((o / (nA2 * nA2)) % nA2);
+      const int M = (int)(o / ((long)nA2 * nA2 * nA2));
+      const double tt = t.W1T[w1i(d, M, W, X, Y)];
+      if (tt == 0.0) return 0.0;
+      for (int Z = 0; Z < nA2; ++Z)
+        for (int U = 0; U < nA2; ++U) {
+          // <M Z||U V> conserves spin: s_V = s_M + s_Z - s_U
+          const int sv = (M & 1) + (Z & 1) - (U & 1);
+          if (sv < 0 || sv > 1) continue;
+          // the cumulant conserves spin: s_U + s_V + s_W = s_X + s_Y + s_Z
+          if ((U & 1) + sv + (W & 1) != (X & 1) + (Y & 1) + (Z & 1)) continue;
+          for (int v = 0; v < nA; ++v) {
+            const int V = 2 * v + sv;
+            acc = fma(t.W1Vt[w1i(d, M, Z, U, V)], t.lam3[lam3i(nA2, U, V, W, X, Y, Z)], acc);
+          }
+        }
+      return 0.25 * tt * acc;
+    }
+    case T_K: {  // 1/4 vt_{xy}^{we} t_{ez}^{uv} lambda_{uvw}^{xyz}, outer (E, U, V, Z)
+      // vt_{xy}^{we} = <xy||we> = -<xy||ew> = -W1Vt[x, y, e, w]; t_{ez}^{uv} = W1T[u, v, e, z]
+      if (!t.lam3) return 0.0;
+      const int Z = (int)(o % nA2), V = (int)((o / nA2) % nA2), U = (int)((o / (nA2 * nA2)) % nA2);
+      const int Ap = nA2 + (int)(o / ((long)nA2 * nA2 * nA2));
+      const double tt = t.W1T[w1i(d, C2 + U, V, Ap, Z)];
+      if (tt == 0.0) return 0.0;
+      for (int X = 0; X < nA2; ++X)
+        for (int Y = 0; Y < nA2; ++Y) {
+          // <X Y||E W> conserves spin: s_W = s_X + s_Y - s_E
+          const int sw = (X & 1) + (Y & 1) - (Ap & 1);
+          if (sw < 0 || sw > 1) continue;
+          if ((U & 1) + (V & 1) + sw != (X & 1) + (Y & 1) + (Z & 1)) continue;
+          for (int w = 0; w < nA; ++w) {
+            const int W = 2 * w + sw;
+            acc = fma(t.W1Vt[w1i(d, C2 + X, Y, Ap, W)], t.lam3[lam3i(nA2, U, V, W, X, Y, Z)], acc);
+          }
+        }
+      return -0.25 * tt * acc;
     }
     case T_F4: {  // 1/4 vt_{xu}^{ef} t_{ef}^{yv} gamma_y^x gamma_v^u, outer (X, U, Y, V)
       const int V = (int)(o % nA2), Y = (int)((o / nA2) % nA2), U = (int)((o / (nA2 * nA2)) % nA2),
@@ -1109,7 +1184,12 @@ bool active_alloc(dsrg_plan* p) {
 }
 
 int active_plan(dsrg_plan* p, int first_partial) {
-  if (p->z.nA == 0) return 0;
+  if (p->z.nA == 0) {
+    // no active orbitals: one partial per core orbital for the f^(1) singles
+    p->segs.push_back(Segment{first_partial, p->z.nC, BLK_ACTIVE});
+    p->seg_active.push_back((int)p->segs.size() - 1);
+    return p->z.nC;
+  }
   const int nb = term_blocks(p->z) * N_TERMS;
   p->segs.push_back(Segment{first_partial, nb, BLK_ACTIVE});
   p->seg_active.push_back((int)p->segs.size() - 1);
@@ -1126,9 +1206,15 @@ cudaError_t launch_gram_aavv_fp64(dsrg_plan* p, const double* B) {
 }
 
 cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                          const double* L, double s, bool ints_ready) {
+                          const double* L, const double* L3, const double* F1, double s,
+                          bool ints_ready) {
   const Sizes& z = p->z;
-  if (z.nA == 0) return cudaSuccess;
+  if (z.nA == 0) {
+    const Segment& sg = p->segs[p->seg_active[0]];
+    singles_kernel<<<z.nC, 128, 0, p->stream>>>(eps, s, z, F1, p->d_partials + sg.begin);
+    DSRG_LAUNCH_CHECK(p);
+    return cudaSuccess;
+  }
   ActiveWs& w = p->act;
   const ActDims d = act_dims(z);
   cudaStream_t st = p->stream;
@@ -1146,7 +1232,7 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
   }
   {
     const int n = d.nH2 * d.nP2;
-    t1_kernel<<<(n + 255) / 256, 256, 0, st>>>(eps, s, z, w.W1 + w.w1n, w.gA, w.t1, w.ft);
+    t1_kernel<<<(n + 255) / 256, 256, 0, st>>>(eps, s, z, w.W1 + w.w1n, w.gA, F1, w.t1, w.ft);
     DSRG_LAUNCH_CHECK(p);
   }
   {
@@ -1205,6 +1291,7 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     ta.t1 = w.t1;
     ta.ft = w.ft;
     ta.P12 = w.P12;
+    ta.lam3 = L3;
     const Segment& sg = p->segs[p->seg_active[0]];
     dim3 grid(term_blocks(z), N_TERMS);
     terms_kernel<<<grid, TERM_NT, 0, st>>>(z, ta, p->d_partials + sg.begin);

@@ -330,7 +330,7 @@ static dsrg_status_t check_common(dsrg_plan* p, const double* B, const double* e
 namespace dsrg {
 // Everything after the CCVV launch: CAVV, CCAV, active block, final reduction.
 dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                       const double* L, double s, double* out) {
+                       const double* L, const double* L3, const double* F1, double s, double* out) {
   cudaError_t e;
   if (p->rest_tc) {
     // one tensor-core GEMM feeds CAVV, CCAV and the active-block integrals
@@ -339,7 +339,7 @@ dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const d
     if ((e = launch_cavv_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv");
     if ((e = launch_ccav_fp64(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "ccav");
   }
-  if ((e = launch_active(p, B, eps, G, L, s, p->rest_tc)) != cudaSuccess)
+  if ((e = launch_active(p, B, eps, G, L, L3, F1, s, p->rest_tc)) != cudaSuccess)
     return cuda_fail(p, e, "active");
   if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
   return DSRG_OK;
@@ -347,26 +347,37 @@ dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const d
 }  // namespace dsrg
 
 static dsrg_status_t run_energy(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                                const double* L, double s, double* out) {
+                                const double* L, const double* L3, const double* F1, double s,
+                                double* out) {
   cudaError_t e;
   if (p->prec == DSRG_PREC_FP64)
     e = launch_ccvv_fp64(p, B, eps, s);
   else
     e = launch_split_ccvv(p, B, eps, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
-  return run_rest(p, B, eps, G, L, s, out);
+  return run_rest(p, B, eps, G, L, L3, F1, s, out);
 }
 
 extern "C" {
 
-dsrg_status_t dsrg_mrpt2_energy(dsrg_plan_t* p, const double* B, const double* eps,
-                                const double* gamma1, const double* lambda2, double s,
-                                double* out_dev) {
+dsrg_status_t dsrg_mrpt2_energy_ext(dsrg_plan_t* p, const double* B, const double* eps,
+                                    const double* gamma1, const double* lambda2,
+                                    const double* lambda3, const double* f1, double s,
+                                    double* out_dev) {
   dsrg_status_t st = check_common(p, B, eps, gamma1, lambda2, s, true);
   if (st != DSRG_OK) return st;
   if (!out_dev || ((uintptr_t)out_dev & 7u)) return fail(p, DSRG_ERR_INVALID_ARG, "bad out pointer");
+  if (((uintptr_t)lambda3 | (uintptr_t)f1) & 7u)
+    return fail(p, DSRG_ERR_INVALID_ARG, "lambda3 and f1 must be 8-byte aligned");
+  if (p->z.nA == 0) lambda3 = nullptr;
   p->launches = 0;
-  return run_energy(p, B, eps, gamma1, lambda2, s, out_dev);
+  return run_energy(p, B, eps, gamma1, lambda2, lambda3, f1, s, out_dev);
+}
+
+dsrg_status_t dsrg_mrpt2_energy(dsrg_plan_t* p, const double* B, const double* eps,
+                                const double* gamma1, const double* lambda2, double s,
+                                double* out_dev) {
+  return dsrg_mrpt2_energy_ext(p, B, eps, gamma1, lambda2, nullptr, nullptr, s, out_dev);
 }
 
 dsrg_status_t dsrg_ccvv_pair_energies(dsrg_plan_t* p, const double* B, const double* eps, double s,
@@ -386,11 +397,15 @@ dsrg_status_t dsrg_ccvv_pair_energies(dsrg_plan_t* p, const double* B, const dou
   return DSRG_OK;
 }
 
-dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const double* eps,
-                                     const double* gamma1, const double* lambda2, double s,
-                                     double* out_dev, double* dB_dev, double* deps_dev,
-                                     double* ds_dev) {
+dsrg_status_t dsrg_mrpt2_energy_grad_ext(dsrg_plan_t* p, const double* B, const double* eps,
+                                         const double* gamma1, const double* lambda2,
+                                         const double* lambda3, const double* f1, double s,
+                                         double* out_dev, double* dB_dev, double* deps_dev,
+                                         double* ds_dev) {
   dsrg_status_t st = check_common(p, B, eps, gamma1, lambda2, s, true);
+  if (((uintptr_t)lambda3 | (uintptr_t)f1) & 7u)
+    return fail(p, DSRG_ERR_INVALID_ARG, "lambda3 and f1 must be 8-byte aligned");
+  if (p && p->z.nA == 0) lambda3 = nullptr;
   if (st != DSRG_OK) return st;
   if (!p->grad) return fail(p, DSRG_ERR_INVALID_ARG, "plan was created without DSRG_PLAN_GRAD");
   if (!out_dev || !dB_dev || !deps_dev || !ds_dev)
@@ -398,16 +413,25 @@ dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const doub
   if (((uintptr_t)out_dev | (uintptr_t)dB_dev | (uintptr_t)deps_dev | (uintptr_t)ds_dev) & 7u)
     return fail(p, DSRG_ERR_INVALID_ARG, "outputs must be 8-byte aligned");
   p->launches = 0;
-  st = run_energy(p, B, eps, gamma1, lambda2, s, out_dev);
+  st = run_energy(p, B, eps, gamma1, lambda2, lambda3, f1, s, out_dev);
   if (st != DSRG_OK) return st;
   if (p->rest_tc) {
     // the adjoint reads FP64 active-block integrals: re-form them in FP64
-    cudaError_t e0 = launch_active(p, B, eps, gamma1, lambda2, s, false);
+    cudaError_t e0 = launch_active(p, B, eps, gamma1, lambda2, lambda3, f1, s, false);
     if (e0 != cudaSuccess) return cuda_fail(p, e0, "active (fp64 tables)");
   }
-  cudaError_t e = launch_grad(p, B, eps, gamma1, lambda2, s, dB_dev, deps_dev, ds_dev);
+  cudaError_t e = launch_grad(p, B, eps, gamma1, lambda2, lambda3, f1, s, dB_dev, deps_dev,
+                              ds_dev);
   if (e != cudaSuccess) return cuda_fail(p, e, "gradient");
   return DSRG_OK;
+}
+
+dsrg_status_t dsrg_mrpt2_energy_grad(dsrg_plan_t* p, const double* B, const double* eps,
+                                     const double* gamma1, const double* lambda2, double s,
+                                     double* out_dev, double* dB_dev, double* deps_dev,
+                                     double* ds_dev) {
+  return dsrg_mrpt2_energy_grad_ext(p, B, eps, gamma1, lambda2, nullptr, nullptr, s, out_dev,
+                                    dB_dev, deps_dev, ds_dev);
 }
 
 dsrg_status_t dsrg_plan_time_ccvv(dsrg_plan_t* p, const double* B, const double* eps, double s,
@@ -518,11 +542,11 @@ dsrg_status_t dsrg_mrpt2_energy_host(dsrg_plan_t* p, const double* B_host, const
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->st_ev[G], 0);
     if (e == cudaSuccess) e = split_stage_rows(p, p->st_B, z.nC, z.nH);
     if (e != cudaSuccess) return cuda_fail(p, e, "ccvv");
-    st = run_rest(p, p->st_B, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+    st = run_rest(p, p->st_B, p->st_eps, p->st_g, p->st_l, nullptr, nullptr, s, p->st_out);
   } else {
     e = cudaMemcpyAsync(p->st_B, B_host, nb * 8, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "host to device copy");
-    st = run_energy(p, p->st_B, p->st_eps, p->st_g, p->st_l, s, p->st_out);
+    st = run_energy(p, p->st_B, p->st_eps, p->st_g, p->st_l, nullptr, nullptr, s, p->st_out);
   }
   if (st != DSRG_OK) return st;
   e = cudaMemcpyAsync(out_host, p->st_out, 5 * 8, cudaMemcpyDeviceToHost, p->stream);

@@ -360,7 +360,7 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
     for (int m = 0; m < n && st == DSRG_OK; ++m) {
       dsrg_plan* p = b->plans[m];
       st = dsrg::run_rest(p, B[m], eps[m], gamma1 ? gamma1[m] : nullptr,
-                          lambda2 ? lambda2[m] : nullptr, s[m], out_dev + 5 * m);
+                          lambda2 ? lambda2[m] : nullptr, nullptr, nullptr, s[m], out_dev + 5 * m);
     }
     for (int m = 0; m < n; ++m) b->launches += b->plans[m]->launches;
     cudaGraph_t graph = nullptr;

@@ -804,7 +804,13 @@ struct ActAdjArgs {
       *dM;
   double *deps, *ds;
   size_t w1n, w2n;
+  const double* lam3;  // [2nA]^6 spin-orbital three-body cumulant (terms J, K), or null
+  const double* f1;    // [nH][nP] off-diagonal Fock block (Eqs. (12), (14)), or null
 };
+
+__device__ __forceinline__ size_t L3I(int n2, int U, int V, int W, int X, int Y, int Z) {
+  return (((((size_t)U * n2 + V) * n2 + W) * n2 + X) * n2 + Y) * n2 + Z;
+}
 
 // (A1) term adjoints landing on W1-shaped tables: d(vt), d(t) direct, d(Ti).
 __global__ void adj_w1_terms_kernel(ActAdjArgs a) {
@@ -894,6 +900,54 @@ __global__ void adj_w1_terms_kernel(ActAdjArgs a) {
         for (int Y = 0; Y < d.nA2; ++Y)
           dt = fma(0.5 * g * eAA(d, gA, A, V) * eAA(d, gA, X, Y), a.W1Vt[W1(d, I, W, V, Y)], dt);
     }
+  }
+  if (a.lam3 && !Iact && !Avir) {
+    // J = 1/4 vt[M,Z,U',V] t[M,W,X',Y] lam3[U',V,W,X',Y,Z]
+    //  -> d(vt) at (M=I, Z=U, U'=A, V=X); d(t) at (M=I, W=U, X'=A, Y=X)
+    const int n2 = d.nA2;
+    for (int W = 0; W < n2; ++W)
+      for (int Xx = 0; Xx < n2; ++Xx) {
+        const int sy = (I & 1) + (W & 1) - (Xx & 1);  // <I W||X' Y> conserves spin
+        if (sy < 0 || sy > 1) continue;
+        for (int y = 0; y < d.nA2 / 2; ++y) {
+          const int Y = 2 * y + sy;
+          dvt = fma(0.25 * a.W1T[W1(d, I, W, Xx, Y)], a.lam3[L3I(n2, A, X, W, Xx, Y, U)], dvt);
+        }
+      }
+    for (int Z = 0; Z < n2; ++Z)
+      for (int Up = 0; Up < n2; ++Up) {
+        const int sv = (I & 1) + (Z & 1) - (Up & 1);  // <I Z||U' V> conserves spin
+        if (sv < 0 || sv > 1) continue;
+        for (int v = 0; v < d.nA2 / 2; ++v) {
+          const int V = 2 * v + sv;
+          dt = fma(0.25 * a.W1Vt[W1(d, I, Z, Up, V)], a.lam3[L3I(n2, Up, V, U, A, X, Z)], dt);
+        }
+      }
+  }
+  if (a.lam3 && Iact && Avir) {
+    // K = -1/4 vt[C2+X',Y,E,W] t[C2+U',V,E,Z] lam3[U',V,W,X',Y,Z]
+    //  -> d(vt) at (X'=Ia, Y=U, E=A, W=X); d(t) at (U'=Ia, V=U, E=A, Z=X)
+    const int n2 = d.nA2, Ia = I - d.nC2;
+    for (int Up = 0; Up < n2; ++Up)
+      for (int Vv = 0; Vv < n2; ++Vv) {
+        const int sz = (Up & 1) + (Vv & 1) - (A & 1);  // <U' V||E Z> conserves spin
+        if (sz < 0 || sz > 1) continue;
+        for (int zz = 0; zz < d.nA2 / 2; ++zz) {
+          const int Z = 2 * zz + sz;
+          dvt = fma(-0.25 * a.W1T[W1(d, d.nC2 + Up, Vv, A, Z)], a.lam3[L3I(n2, Up, Vv, X, Ia, U, Z)],
+                    dvt);
+        }
+      }
+    for (int Xp = 0; Xp < n2; ++Xp)
+      for (int Yp = 0; Yp < n2; ++Yp) {
+        const int sw = (Xp & 1) + (Yp & 1) - (A & 1);  // <X' Y||E W> conserves spin
+        if (sw < 0 || sw > 1) continue;
+        for (int ww = 0; ww < d.nA2 / 2; ++ww) {
+          const int W = 2 * ww + sw;
+          dt = fma(-0.25 * a.W1Vt[W1(d, d.nC2 + Xp, Yp, A, W)], a.lam3[L3I(n2, Ia, U, W, Xp, Yp, X)],
+                   dt);
+        }
+      }
   }
   if (!Iact && Avir) {
     // F6: vt[M, X'=U, e, V'=X]: sum gA[X',Y] eta[U',V'] W1T[M, Y, e, U']
@@ -1072,8 +1126,14 @@ __global__ void adj_t1_chain_kernel(ActAdjArgs a) {
   const double dt1 = internal ? 0.0 : a.dt1[k];
   const double dft = a.dft[k];
   a.dS[k] = dt1 * rt.v + dft * ex;
-  const double dD = S * (dt1 * rt.dD + dft * (-2.0 * a.s * D1 * ex));
-  const double dss = S * (dt1 * rt.ds + dft * (-D1 * D1 * ex));
+  // t1 = (F + S) Rt(D1), ft = F (1 + e^{-s D1^2}) + S e^{-s D1^2}: both regulators
+  // multiply F + S
+  const double F = (a.f1 && !internal && (I & 1) == (A & 1))
+                       ? a.f1[(size_t)(I >> 1) * z.nP + (A >> 1)]
+                       : 0.0;
+  const double FS = F + S;
+  const double dD = FS * (dt1 * rt.dD + dft * (-2.0 * a.s * D1 * ex));
+  const double dss = FS * (dt1 * rt.ds + dft * (-D1 * D1 * ex));
   if (dD != 0.0) {
     atomicAdd(&a.deps[I >> 1], dD);
     atomicAdd(&a.deps[z.nC + (A >> 1)], -dD);
@@ -1432,8 +1492,32 @@ static size_t ccav_adj_smem(const Sizes& z) {
 
 // Gradient of E_total (the energy itself must have been computed on the same
 // stream just before: the active-block tables of the forward pass are reused).
+// Term A with no active orbitals (f^(1) singles): E = 2 sum_{m,e} f^2 (1 + g) Rt,
+// g = exp(-s D^2), D = e_m - e_e; its eps and s derivatives (f^(1) is an input
+// of its own, B does not enter).
+__global__ void singles_adj_kernel(const double* __restrict__ eps, double s, Sizes z,
+                                   const double* __restrict__ f1, double* __restrict__ deps,
+                                   double* __restrict__ ds) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= z.nC * z.nP) return;
+  const int m = k / z.nP, e = k % z.nP;
+  const double f = f1[k];
+  const double D = eps[m] - eps[z.nC + e];
+  const RegD rt = rt_d(D, s);
+  const double g = exp(-s * D * D);
+  const double w = 2.0 * f * f;
+  const double dD = w * ((-2.0 * s * D * g) * rt.v + (1.0 + g) * rt.dD);
+  const double dss = w * ((-D * D * g) * rt.v + (1.0 + g) * rt.ds);
+  if (dD != 0.0) {
+    atomicAdd(&deps[m], dD);
+    atomicAdd(&deps[z.nC + e], -dD);
+  }
+  if (dss != 0.0) atomicAdd(ds, dss);
+}
+
 cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                        const double* L, double s, double* dB, double* deps, double* ds) {
+                        const double* L, const double* L3, const double* F1, double s, double* dB,
+                        double* deps, double* ds) {
   (void)L;
   const Sizes& z = p->z;
   GradWs* w = p->grad;
@@ -1486,7 +1570,14 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     if (!fp64) gw.B32 = (const float*)w->Wk;
     if ((e = gemm(p, gw)) != cudaSuccess) return e;
   }
-  if (z.nA == 0) return cudaSuccess;
+  if (z.nA == 0) {
+    if (F1) {
+      const int n = z.nC * z.nP;
+      singles_adj_kernel<<<(n + 255) / 256, 256, 0, st>>>(eps, s, z, F1, deps, ds);
+      DSRG_LAUNCH_CHECK(p);
+    }
+    return cudaSuccess;
+  }
   const long long nV = z.nV, nV2 = nV * nV;
 
   // ---- F2
@@ -1555,6 +1646,8 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     a.ds = ds;
     a.w1n = A.w1n;
     a.w2n = A.w2n;
+    a.lam3 = L3;
+    a.f1 = F1;
     const int nHP2 = 4 * z.nH * z.nP;
     const int nA4 = z.nA * z.nA * z.nA * z.nA;
     auto blocks = [](size_t n) { return (unsigned)((n + 255) / 256); };

@@ -129,9 +129,11 @@ cudaError_t launch_cavv_fp64(dsrg_plan* p, const double* B, const double* eps, c
 cudaError_t launch_ccav_fp64(dsrg_plan* p, const double* B, const double* eps, const double* G,
                              double s);
 // ints_ready: K1, K2, K3 and M are already formed (split path); otherwise they
-// are formed here in FP64 from B.
+// are formed here in FP64 from B. L3 (spin-orbital three-body cumulant) and F1
+// (off-diagonal Fock block) may be null (read as 0).
 cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                          const double* L, double s, bool ints_ready);
+                          const double* L, const double* L3, const double* F1, double s,
+                          bool ints_ready);
 cudaError_t launch_gram_aavv_fp64(dsrg_plan* p, const double* B);
 cudaError_t launch_final_reduce(dsrg_plan* p, double* out);
 cudaError_t launch_pair_energies(dsrg_plan* p, double* pairs);
@@ -164,7 +166,7 @@ struct SplitShare {
 dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precision_t prec,
                           void* cuda_stream, uint32_t flags, const SplitShare* share);
 dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                       const double* L, double s, double* out);
+                       const double* L, const double* L3, const double* F1, double s, double* out);
 
 // Split planes shared by several molecules (tc_split.cu).
 bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
@@ -214,7 +216,8 @@ void split_schedule(const std::vector<int4>& items, const std::vector<double>& c
 bool grad_alloc(dsrg_plan* p);
 void grad_free(dsrg_plan* p);
 cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                        const double* L, double s, double* dB, double* deps, double* ds);
+                        const double* L, const double* L3, const double* F1, double s, double* dB,
+                        double* deps, double* ds);
 
 // Split-path CAVV, CCAV and active-block integrals (tc_rest.cu); needs the
 // planes staged by the CCVV launch of the same call.

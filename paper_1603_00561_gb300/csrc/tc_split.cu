@@ -25,12 +25,11 @@
 //   warp 1      TMEM allocator and MMA issuer (one elected thread)
 //   warps 2-9   epilogue: 256 threads; warp w reads TMEM lanes 32*(w%4).. and
 //               columns 64*((w-2)/4).. of the tile (two warps per lane quarter)
-// Shared memory: 6 stages x 4 operand slots x 2 planes x (128 rows x 32 B),
-// 32-byte swizzle: one MMA K step per stage, so that the buffer the MMAs hold
-// at any moment is small and 5 of the 6 stages can be in flight from L2. The
-// last virtual tile is as wide as the virtual space leaves it (N = its width
-// rounded up to 16); when that is at most 64, the slots read only as B operands
-// load 64 rows. TMEM: 2 buffers x (x, y) x 128 columns = 512 columns.
+// Shared memory: 3 stages x 4 operand slots x 2 planes x (128 rows x 64 B),
+// 64-byte swizzle (two MMA K steps per stage). The last virtual tile is as wide
+// as the virtual space leaves it (N = its width rounded up to 16); when that is
+// at most 64, the slots read only as B operands load 64 rows. TMEM: 2 buffers
+// x (x, y) x 128 columns = 512 columns.
 // Every wait is bounded (about 2 s); on expiry the CTA records a status word,
 // drains what it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -46,15 +45,14 @@
 namespace dsrg {
 
 constexpr int TT = 128;                      // tile edge (rows = TMEM lanes, columns)
-constexpr int KB_BYTES = 32;                 // K bytes per row per stage: one MMA K step (32-byte swizzle span)
-constexpr int STAGES = 6;
-constexpr int SLOT_BYTES = TT * KB_BYTES;    // one operand tile of one plane: 4 KB
+constexpr int KB_BYTES = 64;                 // K bytes per row per stage: two MMA K steps (64-byte swizzle span)
+constexpr int STAGES = 3;
+constexpr int SLOT_BYTES = TT * KB_BYTES;    // one operand tile of one plane: 8 KB
 constexpr int STAGE_BYTES = 4 * 2 * SLOT_BYTES;
 constexpr int GEMM_KB_BYTES = 64;            // K bytes per box of the tc_rest GEMM's maps (64-byte swizzle)
 constexpr int SPLIT_THREADS = 320;  // warps 0-1 roles, warps 2-9 epilogue
 constexpr int EPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
-constexpr int T_PITCH = TT + 1;  // row pitch (floats) of the transpose buffer: no bank conflicts
 
 struct SplitWs {
   int elt = 4, kb_elems = 16;
@@ -122,8 +120,6 @@ struct ItemPlan {
   int g1a, g1b, g2a, g2b;
   int nB;               // MMA N: the columns of virtual tile Bt rounded up to 16
   bool narrow;          // B-only slots (1, 3) of this item load 64 rows (nB <= 64, A != Bt)
-  bool ymma;            // y formed by its own MMAs (i != j, A != Bt)
-  bool ytr;             // y = x^T taken from x through shared memory (i != j, A == Bt)
 };
 
 __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const MolDesc** mdp) {
@@ -145,10 +141,6 @@ __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const
   // slots 1 = (j, B) and 3 = (i, B) of an off-diagonal tile pair are read only as
   // B operands (N rows); on a diagonal tile pair every slot is also an A operand
   ip.narrow = !dt && ip.nB <= 64;
-  // on a diagonal tile pair y = v^{ji}[A,A] = (v^{ij}[A,A])^T: the epilogue
-  // transposes x instead of the tensor cores forming y
-  ip.ymma = ip.two && !dt;
-  ip.ytr = ip.two && dt;
   if (ip.two && !dt) {
     ip.nload = 4;
     ip.load[0] = 0; ip.load[1] = 1; ip.load[2] = 2; ip.load[3] = 3;
@@ -178,7 +170,7 @@ __device__ __forceinline__ int slot_row(const ItemPlan& ip, int slot, int nVpad)
   }
 }
 
-// The MMAs of one K stage of one item (one K step of 16 BF16 / 8 TF32 values).
+// The MMAs of one K stage of one item (two K steps of 16 BF16 / 8 TF32 values).
 // K runs from the last auxiliary function to the first and the small cross
 // products go before hi*hi: the accumulator truncates toward zero at every
 // instruction, and with the factors' magnitudes decreasing along Q this keeps
@@ -189,22 +181,26 @@ template <bool BF16>
 __device__ __forceinline__ void ccvv_stage_mmas(uint32_t dx, uint32_t dy, uint32_t sb,
                                                 const ItemPlan& ip, int kb) {
   const uint32_t idesc = idesc_128xn<BF16>((uint32_t)ip.nB);
-  const uint64_t a1h = desc_sw32(sb + (ip.g1a * 2 + 0) * SLOT_BYTES);
-  const uint64_t a1l = desc_sw32(sb + (ip.g1a * 2 + 1) * SLOT_BYTES);
-  const uint64_t b1h = desc_sw32(sb + (ip.g1b * 2 + 0) * SLOT_BYTES);
-  const uint64_t b1l = desc_sw32(sb + (ip.g1b * 2 + 1) * SLOT_BYTES);
-  const uint32_t acc0 = kb > 0 ? 1u : 0u;
-  tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
-  tc_mma<BF16, 1>(dx, a1h, b1l, idesc, 1u);
-  tc_mma<BF16, 2>(dx, a1h, b1h, idesc, 1u);
-  if (ip.ymma) {
-    const uint64_t a2h = desc_sw32(sb + (ip.g2a * 2 + 0) * SLOT_BYTES);
-    const uint64_t a2l = desc_sw32(sb + (ip.g2a * 2 + 1) * SLOT_BYTES);
-    const uint64_t b2h = desc_sw32(sb + (ip.g2b * 2 + 0) * SLOT_BYTES);
-    const uint64_t b2l = desc_sw32(sb + (ip.g2b * 2 + 1) * SLOT_BYTES);
-    tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
-    tc_mma<BF16, 1>(dy, a2h, b2l, idesc, 1u);
-    tc_mma<BF16, 2>(dy, a2h, b2h, idesc, 1u);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const uint32_t off = (uint32_t)((1 - k) * 32);
+    const uint64_t a1h = desc_sw64(sb + (ip.g1a * 2 + 0) * SLOT_BYTES + off);
+    const uint64_t a1l = desc_sw64(sb + (ip.g1a * 2 + 1) * SLOT_BYTES + off);
+    const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + off);
+    const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + off);
+    const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+    tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
+    tc_mma<BF16, 1>(dx, a1h, b1l, idesc, 1u);
+    tc_mma<BF16, 2>(dx, a1h, b1h, idesc, 1u);
+    if (ip.two) {
+      const uint64_t a2h = desc_sw64(sb + (ip.g2a * 2 + 0) * SLOT_BYTES + off);
+      const uint64_t a2l = desc_sw64(sb + (ip.g2a * 2 + 1) * SLOT_BYTES + off);
+      const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + off);
+      const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + off);
+      tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
+      tc_mma<BF16, 1>(dy, a2h, b2l, idesc, 1u);
+      tc_mma<BF16, 2>(dy, a2h, b2h, idesc, 1u);
+    }
   }
 }
 
@@ -228,7 +224,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
   double* sAlpha = sEps + TT;
   double* sRed = sAlpha + TT;
   float* sEpsF = (float*)(sRed + EPI_WARPS);
-  float* sT = sEpsF + TT;  // [32][T_PITCH]: 32 rows of x, transposed by the epilogue
+  float* sCr = sEpsF + TT;  // [TT/16][2]: min, max of e over the valid columns of each 16-column chunk
+  unsigned* sCnt = (unsigned*)(sCr + 2 * (TT / 16));  // [EPI_WARPS][3] epilogue blocks by regulator path
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int it0 = a.cta_begin[blockIdx.x], it1 = a.cta_begin[blockIdx.x + 1];
@@ -397,6 +394,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     const int cbeg = ((warp - 2) >> 2) * 64;   // this warp's half of the columns
     int tbuf = 0;
     uint32_t tphase = 0;
+    // 32-row x 16-column blocks of this warp by regulator path (lane 0 counts
+    // in shared memory; the first barrier of the item loop orders the clearing)
+    if (et < 3 * EPI_WARPS) sCnt[et] = 0u;
     for (int idx = it0; idx < it1; ++idx) {
       const MolDesc* md;
       const ItemPlan ip = plan_item(a, idx, &md);
@@ -406,14 +406,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       const double* pi = md->pinfo + 4 * ip.p;
       const double E = pi[0], beta = pi[1];
       const double* alpha = md->alpha + (size_t)ip.p * nVpad;
-      // every D of the tile pair is away from 0: no per-element guard needed
-      const double dmax = E - md->trange[2 * ip.A] - md->trange[2 * ip.Bt];
-      const double dmin = E - md->trange[2 * ip.A + 1] - md->trange[2 * ip.Bt + 1];
-      const bool fast = (pi[2] != 0.0) && (dmax <= -0.25 || dmin >= 0.25);
-      // every |D| of the tile pair so large that exp(-2 s D^2) < 2^-63: then
-      // (1 - exp(-2 s D^2)) / D equals 1/D to FP64 precision
-      const double dnear = dmax <= 0.0 ? dmax : (dmin >= 0.0 ? dmin : 0.0);
-      const bool far = (dmax <= -0.25 || dmin >= 0.25) && 2.0 * md->s * dnear * dnear > 44.0;
+      const bool factorisable = pi[2] != 0.0;
       named_bar(1, 32 * EPI_WARPS);
       if (et < TT) {
         const int b = ip.Bt * TT + et;
@@ -421,6 +414,17 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
         sEps[et] = eb;
         sEpsF[et] = (float)eb;
         sAlpha[et] = (b < nV) ? alpha[b] : 0.0;
+      }
+      named_bar(1, 32 * EPI_WARPS);
+      if (et < TT / 16) {
+        // range of e over the valid columns of chunk et (FP32: it only picks a path)
+        float lo = 3.0e38f, hi = -3.0e38f;
+        for (int c = 16 * et; c < 16 * et + 16 && ip.Bt * TT + c < nV; ++c) {
+          lo = fminf(lo, sEpsF[c]);
+          hi = fmaxf(hi, sEpsF[c]);
+        }
+        sCr[2 * et] = lo;
+        sCr[2 * et + 1] = hi;
       }
       named_bar(1, 32 * EPI_WARPS);
       const int arow = ip.A * TT + row;
@@ -435,101 +439,82 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       const double* taucol = md->tau + (size_t)(ip.Bt * TT) * nVpad + arow;
       const float* tail_ia = md->tail + (size_t)(ip.i * nVpad + arow) * TAIL_Q;
       const float* tail_ja = md->tail + (size_t)(ip.j * nVpad + arow) * TAIL_Q;
+      // range of E - e_a over this warp's valid rows (FP32)
+      float clo = rok ? caf : 3.0e38f, chi = rok ? caf : -3.0e38f;
+      for (int o = 16; o > 0; o >>= 1) {
+        clo = fminf(clo, __shfl_xor_sync(0xffffffffu, clo, o));
+        chi = fmaxf(chi, __shfl_xor_sync(0xffffffffu, chi, o));
+      }
+      // exp(-2 s D^2) < 2^-63 for every D of a block when 2 s D^2 > 44 (the FP32
+      // range carries a margin: 46)
+      const float far_d2 = 46.0f / (2.0f * (float)s);
 
       bool ok = mbar_wait(&tfull[tbuf], tphase, abort_flag, a.status);
       tc_fence_after();
       double acc = 0.0;
-      // x_ab (and y_ab) of the 16 columns from c0: the FP32 terms of the first
-      // auxiliary functions, then the regulated exchange combination in FP64
-      auto chunk = [&](int c0, uint32_t (&xr)[16], uint32_t (&yr)[16]) {
-        // the first TAIL_Q auxiliary functions, the largest terms, in FP32
-        // round-to-nearest (the tensor cores took the rest)
-        tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
-        if (ip.two)
-          tail_add16(tail_ja, md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
-        if (far) {
+      if (ok) {
+        const uint32_t tx = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * 256);
+        const uint32_t ty = tx + 128;
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+          uint32_t xr[16], yr[16];
+          tmem_ld16(tx + c0, xr);
+          if (ip.two) tmem_ld16(ty + c0, yr);
+          tmem_ld_wait();
+          // The regulator path of this warp's 32 rows and the 16 columns from c0
+          // (the same for the whole warp): every |D| so large that
+          // exp(-2 s D^2) < 2^-63 -> R = 1/D; every |D| >= 1/4 with factorisable
+          // exponentials -> the factor tables; else expm1 per element.
+          const float dlo = clo - sCr[2 * (c0 >> 4) + 1], dhi = chi - sCr[2 * (c0 >> 4)];
+          const bool away = dhi <= -0.25f || dlo >= 0.25f;
+          const float dn = dhi <= 0.0f ? dhi : dlo;
+          const int pth = !away ? 2 : (dn * dn > far_d2 ? 0 : (factorisable ? 1 : 2));
+          if (lane == 0) sCnt[3 * (warp - 2) + pth] += 1u;
+          if (!rok) continue;
+          // the first TAIL_Q auxiliary functions, the largest terms, in FP32
+          // round-to-nearest (the tensor cores took the rest)
+          tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
+          if (ip.two)
+            tail_add16(tail_ja, md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
+          if (pth == 0) {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int cb = c0 + k;
-            if (cb >= cend) break;
-            const float xf = __uint_as_float(xr[k]);
-            const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
-            const double D = ca - sEps[cb];
-            float r0f;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
-            const double r0 = (double)r0f;
-            const double R = fma(r0, fma(-D, r0, 1.0), r0);   // 1/D, one Newton step
-            acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
-          }
-        } else if (fast) {
+            for (int k = 0; k < 16; ++k) {
+              const int cb = c0 + k;
+              if (cb >= cend) break;
+              const float xf = __uint_as_float(xr[k]);
+              const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+              const double D = ca - sEps[cb];
+              double r0;
+              asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(D));  // 1/D, seed
+              const double R = fma(r0, fma(-D, r0, 1.0), r0);       // one Newton step
+              acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
+            }
+          } else if (pth == 1) {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int cb = c0 + k;
-            if (cb >= cend) break;
-            const float xf = __uint_as_float(xr[k]);
-            const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
-            const double D = ca - sEps[cb];
-            const double g = ha * sAlpha[cb] * taucol[(size_t)cb * nVpad];
-            float r0f;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(caf - sEpsF[cb]));
-            const double r0 = (double)r0f;             // 1/D to ~2^-22
-            const double e = fma(-D, r0, 1.0);         // Newton-Raphson residual
-            const double R0 = fma(-g, r0, r0);         // (1 - g) / D, seed accuracy
-            const double R = fma(R0, e, R0);           // one Newton step: ~2^-44
-            acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
-          }
-        } else {
+            for (int k = 0; k < 16; ++k) {
+              const int cb = c0 + k;
+              if (cb >= cend) break;
+              const float xf = __uint_as_float(xr[k]);
+              const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+              const double D = ca - sEps[cb];
+              const double g = ha * sAlpha[cb] * taucol[(size_t)cb * nVpad];
+              double r0;
+              asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(D));  // 1/D, seed
+              const double e = fma(-D, r0, 1.0);         // Newton-Raphson residual
+              const double R0 = fma(-g, r0, r0);         // (1 - g) / D, seed accuracy
+              const double R = fma(R0, e, R0);           // one Newton step
+              acc = fma((double)fmaf(xf, xf - yf, yf * yf), R, acc);
+            }
+          } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int cb = c0 + k;
-            if (cb >= cend) break;
-            const double xd = __uint_as_float(xr[k]);
-            const double yd = ip.two ? (double)__uint_as_float(yr[k]) : xd;
-            const double D = ca - sEps[cb];
-            acc = fma(fma(xd, xd - yd, yd * yd), reg_f1(D, s), acc);
-          }
-        }
-      };
-      const uint32_t tx = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tbuf * 256);
-      const uint32_t ty = tx + 128;
-      if (!ip.ytr) {
-        if (ok) {
-          for (int c0 = cbeg; c0 < cend; c0 += 16) {
-            uint32_t xr[16], yr[16];
-            tmem_ld16(tx + c0, xr);
-            if (ip.two) tmem_ld16(ty + c0, yr);
-            tmem_ld_wait();
-            if (rok) chunk(c0, xr, yr);
-          }
-        }
-      } else {
-        // y = x^T in four passes of 32 rows of x: the two warps holding TMEM
-        // lanes 32p..32p+31 store their rows to shared memory, then the warps
-        // whose columns are 32p..32p+31 read them back transposed. Every pass
-        // meets both barriers whatever `ok` is.
-        for (int pass = 0; pass < 4; ++pass) {
-          if (ok && quarter == pass) {
-            for (int c = cbeg; c < cbeg + 64; c += 16) {
-              uint32_t xr[16];
-              tmem_ld16(tx + c, xr);
-              tmem_ld_wait();
-#pragma unroll
-              for (int k = 0; k < 16; ++k) sT[lane * T_PITCH + c + k] = __uint_as_float(xr[k]);
+            for (int k = 0; k < 16; ++k) {
+              const int cb = c0 + k;
+              if (cb >= cend) break;
+              const double xd = __uint_as_float(xr[k]);
+              const double yd = ip.two ? (double)__uint_as_float(yr[k]) : xd;
+              const double D = ca - sEps[cb];
+              acc = fma(fma(xd, xd - yd, yd * yd), reg_f1(D, s), acc);
             }
           }
-          named_bar(1, 32 * EPI_WARPS);
-          if (ok && (cbeg >> 6) == (pass >> 1)) {
-            for (int c0 = 32 * pass; c0 < 32 * pass + 32 && c0 < cend; c0 += 16) {
-              uint32_t xr[16], yr[16];
-              tmem_ld16(tx + c0, xr);
-              tmem_ld_wait();
-#pragma unroll
-              for (int k = 0; k < 16; ++k)
-                yr[k] = __float_as_uint(sT[(c0 - 32 * pass + k) * T_PITCH + row]);
-              if (rok) chunk(c0, xr, yr);
-            }
-          }
-          named_bar(1, 32 * EPI_WARPS);
         }
       }
       // release this TMEM buffer to the MMA issuer
@@ -545,9 +530,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       if (lane == 0) sRed[warp - 2] = acc;
       named_bar(1, 32 * EPI_WARPS);
       if (et == 0) {
-        atomicAdd(&a.counts[far ? DSRG_COUNT_CCVV_FAR
-                                : (fast ? DSRG_COUNT_CCVV_FACTORED : DSRG_COUNT_CCVV_DIRECT)],
-                  1ull);
         if (pi[2] == 0.0) atomicAdd(&a.counts[DSRG_COUNT_CCVV_UNFACTORABLE], 1ull);
         const double w = (ip.two ? 2.0 : 1.0) * (ip.A < ip.Bt ? 2.0 : 1.0);
         double t = 0.0;
@@ -566,6 +548,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(TMEM_COLS)
                  : "memory");
+  }
+  if (threadIdx.x >= 64 && threadIdx.x < 64 + 3 * EPI_WARPS && it1 > it0) {
+    const unsigned c = sCnt[threadIdx.x - 64];
+    const int slot = (threadIdx.x - 64) % 3;
+    if (c)
+      atomicAdd(&a.counts[slot == 0 ? DSRG_COUNT_CCVV_FAR
+                                    : (slot == 1 ? DSRG_COUNT_CCVV_FACTORED : DSRG_COUNT_CCVV_DIRECT)],
+                (unsigned long long)c);
   }
 }
 
@@ -820,11 +810,11 @@ void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& it
   auto tp_index = [&](int A, int B) { return A * nT - A * (A - 1) / 2 + (B - A); };
   auto push = [&](int i, int j, int A, int B) {
     items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, pair_index(i, j) * n_tp + tp_index(A, B)));
-    // MMA work: one GEMM for i = j or a diagonal tile pair (y = x^T), else two,
-    // each as wide as tile B; plus a fixed share for the epilogue
+    // MMA work: one GEMM for i = j, else two, each as wide as tile B; plus a
+    // fixed share for the epilogue
     const int nb = z.nV - B * TT < TT ? z.nV - B * TT : TT;
     const double width = (double)((nb + 15) & ~15) / TT;
-    cost.push_back((double)kblocks * (i == j || A == B ? 1.0 : 2.0) * width + 48.0);
+    cost.push_back((double)kblocks * (i == j ? 1.0 : 2.0) * width + 24.0);
   };
   const int G = order >> 1;
   if (G <= 0) {
@@ -1061,7 +1051,7 @@ void split_free(dsrg_plan* p) {
 
 static size_t split_smem_bytes() {
   return (size_t)STAGES * STAGE_BYTES + 1024 + 256 + (2 * TT + EPI_WARPS) * 8 + TT * 4 +
-         32 * T_PITCH * 4 + 64;
+         2 * (TT / 16) * 4 + 3 * EPI_WARPS * 4 + 64;
 }
 
 // Planes (and FP32 tail rows) of the hole rows h0 <= h < h1 of B.

@@ -29,17 +29,26 @@ def _rel(a, b):
 TINY = [(3, 2, 4, 9, 0.37, 0), (2, 3, 3, 7, 0.8, 1), (3, 1, 5, 11, 0.1, 2), (1, 2, 2, 5, 1.3, 3)]
 
 
+def _extra(p):
+    return dict(lambda3=p.lambda3, f1=p.f1)
+
+
+@pytest.mark.parametrize("extra", [False, True], ids=["lam2", "lam3_f1"])
 @pytest.mark.parametrize("nC,nA,nV,Q,s,seed", TINY)
-def test_tiers_agree_per_block(nC, nA, nV, Q, s, seed):
+def test_tiers_agree_per_block(nC, nA, nV, Q, s, seed, extra):
     """Table 1 (literal, spin orbitals) == tier-1 (Table 2 split, Eq. (23) pair
-    loop, spin-adapted F1-F3), for every block and the total, lambda2 != 0."""
-    p = make_problem(nC, nA, nV, Q, s=s, seed=seed)
-    r0 = spinorb.energy(*_args(p))
-    r1 = dsrg.energy(*_args(p), with_terms=True)
+    loop, spin-adapted F1-F3), for every block and the total, lambda2 != 0;
+    with the three-body cumulant (terms J, K) and the off-diagonal Fock block
+    f^(1) (Eqs. (12), (14)) as well."""
+    p = make_problem(nC, nA, nV, Q, s=s, seed=seed, with_lambda3=extra, with_f1=extra)
+    r0 = spinorb.energy(*_args(p), **_extra(p))
+    r1 = dsrg.energy(*_args(p), with_terms=True, **_extra(p))
     for k in BLOCKS:
         assert _rel(r0[k], r1[k]) < 1e-12, (k, r0[k], r1[k])
     for k, v in r1["terms"].items():
         assert abs(v - r0[k]) <= 1e-12 * max(1.0, abs(r0[k])), k
+    if extra and nA >= 2:
+        assert r0["J"] != 0.0 and r0["K"] != 0.0
 
 
 @pytest.mark.parametrize("nC,nA,nV,Q,s,seed", TINY)
@@ -152,6 +161,25 @@ def test_size_consistency():
         assert abs(rab[k] - ra[k] - rb[k]) <= 1e-12 * max(1.0, abs(rab[k])), k
     r0 = spinorb.energy(B, eps, G, L, 0.5, nC, nA, nV)
     assert _rel(r0["total"], ra["total"] + rb["total"]) < 1e-12
+    # with three-body cumulants and off-diagonal Fock blocks of each fragment
+    # (nothing between the fragments)
+    pa = make_problem(2, 2, 3, 6, s=0.5, seed=11, with_lambda3=True, with_f1=True)
+    pb = make_problem(2, 1, 4, 5, s=0.5, seed=12, with_lambda3=True, with_f1=True)
+    F = np.zeros((nC + nA, nA + nV))
+    F[np.ix_(hA, pA)] = pa.f1
+    F[np.ix_(hB, pB)] = pb.f1
+    soA = [2 * u + sg for u in range(pa.nactive) for sg in (0, 1)]
+    soB = [2 * (pa.nactive + u) + sg for u in range(pb.nactive) for sg in (0, 1)]
+    L3 = np.zeros((2 * nA,) * 6)
+    L3[np.ix_(soA, soA, soA, soA, soA, soA)] = pa.lambda3
+    L3[np.ix_(soB, soB, soB, soB, soB, soB)] = pb.lambda3
+    rab = dsrg.energy(B, eps, G, L, 0.5, nC, nA, nV, lambda3=L3, f1=F)
+    ra = dsrg.energy(*_args(pa), **_extra(pa))
+    rb = dsrg.energy(*_args(pb), **_extra(pb))
+    for k in BLOCKS:
+        assert abs(rab[k] - ra[k] - rb[k]) <= 1e-12 * max(1.0, abs(rab[k])), k
+    r0 = spinorb.energy(B, eps, G, L, 0.5, nC, nA, nV, lambda3=L3, f1=F)
+    assert _rel(r0["total"], ra["total"] + rb["total"]) < 1e-12
 
 
 @pytest.mark.parametrize("spectrum,seed", [("overlap", 20), ("degenerate", 21), ("negative", 22)])
@@ -224,6 +252,47 @@ def test_orbital_permutation_invariance():
         assert _rel(r[k], rp[k]) < 1e-13, k
 
 
+def test_linear_in_lambda3():
+    """The three-body cumulant enters only terms J and K of Table 1, linearly:
+    E(2 L3) - E(0) = 2 (E(L3) - E(0)), and with L3 absent J = K = 0."""
+    p = make_problem(2, 3, 4, 8, s=0.5, seed=15, with_lambda3=True)
+    e = lambda l3: dsrg.energy(*_args(p), lambda3=l3)["total"]
+    e0, e1, e2 = e(None), e(p.lambda3), e(2.0 * p.lambda3)
+    assert e1 != e0
+    assert abs((e2 - e0) - 2.0 * (e1 - e0)) <= 1e-13 * abs(e1)
+    assert e(0.0 * p.lambda3) == e0
+
+
+@pytest.mark.parametrize("occ", ["full", "empty"])
+def test_singles_limit_is_mp2_with_singles(occ):
+    """One-determinant limits (lambda = 0, G = 2I or 0) with an off-diagonal
+    Fock block: T1 is f^(1) regulated (Eq. (12): the sum over u x vanishes),
+    the modified Fock is f (1 + e^{-sD^2}) (Eq. (14)), and term A becomes
+    sum_{ia} f_ia^2 (1 - e^{-2sD^2}) / D per spin. For s -> infinity the total is
+    the textbook spin-orbital MP2 energy with the non-Brillouin singles term,
+    1/4 sum |<ij||ab>|^2 / D_ij^ab + sum |f_ia|^2 / D_ia over the occupied (core,
+    and active when G = 2I) and unoccupied spin orbitals."""
+    p = make_problem(3, 2, 4, 10, s=1.0e6, seed=16, occupation=occ, with_f1=True)
+    p.lambda2[...] = 0.0
+    nC, nA, nV = p.ncore, p.nactive, p.nvirt
+    r1 = dsrg.energy(*_args(p), f1=p.f1)
+    r0 = spinorb.energy(*_args(p), f1=p.f1)
+    if occ == "full":
+        occ_idx, vir_idx = list(range(nC + nA)), list(range(nA, nA + nV))
+        Bp, e_occ = p.B[:, :, nA:], p.eps[: nC + nA]
+        mp2 = spinorb.mp2_spin_orbital(Bp, p.eps, nC + nA, nV, 0)
+    else:
+        occ_idx, vir_idx = list(range(nC)), list(range(nA + nV))
+        Bp, e_occ = p.B[:, :nC, :], p.eps[:nC]
+        mp2 = spinorb.mp2_spin_orbital(Bp, p.eps, nC, nA + nV, 0)
+    e_vir = p.eps[nC:][vir_idx]
+    f = p.f1[np.ix_(occ_idx, vir_idx)]
+    singles = 2.0 * np.sum(f ** 2 / (e_occ[:, None] - e_vir[None, :]))
+    assert singles != 0.0
+    assert _rel(r1["total"], mp2 + singles) < 1e-12
+    assert _rel(r0["total"], mp2 + singles) < 1e-12
+
+
 def test_affine_in_lambda2():
     """Every Table 1 term is linear in lambda2 or independent of it (J, K absent):
     E(2L) - E(0) = 2 (E(L) - E(0))."""
@@ -237,16 +306,19 @@ def test_affine_in_lambda2():
     assert abs((e2 - e0) - 2.0 * (e1 - e0)) <= 1e-13 * abs(e1)
 
 
-def test_gradient_matches_finite_differences_of_tier0():
+@pytest.mark.parametrize("extra", [False, True], ids=["lam2", "lam3_f1"])
+def test_gradient_matches_finite_differences_of_tier0(extra):
     """Autograd of tier 1 against central differences of the independent
-    literal Table 1 (tier 0), on B entries in every block, on eps and on s."""
-    p = make_problem(3, 2, 4, 7, s=0.45, seed=14)
-    g = dsrg.energy_and_grad(*_args(p))
+    literal Table 1 (tier 0), on B entries in every block, on eps and on s
+    (also with the three-body cumulant and f^(1))."""
+    p = make_problem(3, 2, 4, 7, s=0.45, seed=14, with_lambda3=extra, with_f1=extra)
+    g = dsrg.energy_and_grad(*_args(p), **_extra(p))
     rng = np.random.default_rng(1)
     h = 1e-5
 
     def e0(B=p.B, eps=p.eps, s=p.s):
-        return spinorb.energy(B, eps, p.gamma1, p.lambda2, s, p.ncore, p.nactive, p.nvirt)["total"]
+        return spinorb.energy(B, eps, p.gamma1, p.lambda2, s, p.ncore, p.nactive, p.nvirt,
+                              **_extra(p))["total"]
 
     idx = [tuple(rng.integers(0, n) for n in p.B.shape) for _ in range(12)]
     idx += [(0, 0, 0), (1, p.ncore, 0), (2, p.ncore + 1, p.nactive + 1), (3, 0, 1)]
