@@ -43,7 +43,8 @@ import dataclasses
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "CONFIGS", "batch_sizes"]
+__all__ = ["Problem", "make_problem", "CONFIGS", "batch_sizes", "FockProblem", "make_fock_problem",
+           "AOProblem", "make_ao_problem", "make_eri_factors"]
 
 
 @dataclasses.dataclass
@@ -211,6 +212,89 @@ def make_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5
         f1 = rx.uniform(-0.05, 0.05, (nH, nP))
         f1[ncore:, :nactive] = 0.0
     return Problem(ncore, nactive, nvirt, naux, float(s), B, eps, gamma1, lambda2, lambda3, f1)
+
+
+@dataclasses.dataclass
+class FockProblem:
+    """Inputs of the generalized Fock build and semicanonicalisation: the
+    one-electron integrals and the DF factors over ALL orbital pairs (not only
+    hole x particle), plus the active density and cumulants (non-semicanonical
+    orbitals: the Fock matrix has off-diagonal elements inside each block)."""
+    ncore: int
+    nactive: int
+    nvirt: int
+    naux: int
+    s: float
+    h: np.ndarray        # [n, n] symmetric
+    Bfull: np.ndarray    # [naux, n, n] symmetric in the orbital pair
+    gamma1: np.ndarray   # [nA, nA]
+    lambda2: np.ndarray  # [nA]^4
+    lambda3: np.ndarray | None = None
+
+
+def make_fock_problem(ncore: int, nactive: int, nvirt: int, naux: int, s: float = 0.5,
+                      seed: int = 0, b_scale: float = 0.05, b_decay: float = 0.02,
+                      with_lambda3: bool = False) -> FockProblem:
+    """Draw one problem for the Fock build: ``Bfull[Q, p, q]`` = b_scale *
+    N(0,1) * exp(-b_decay Q), symmetrised in (p, q) (b_scale 0.05 keeps the
+    two-electron part of the Fock matrix a perturbation of h at these sizes,
+    so that core, active and virtual orbital energies stay apart); ``h`` = diag(h0) + a
+    symmetric matrix with entries ~ U(-0.05, 0.05), h0 drawn like the orbital
+    energies of the recipe (core ~ U[-2.0, -0.3], active ~ U[-0.2, 0.1],
+    virtual ~ U[0.05, 5.0], unsorted); gamma1, lambda2 (and lambda3) as in
+    ``make_problem`` with the same seed."""
+    n = ncore + nactive + nvirt
+    base = make_problem(ncore, nactive, nvirt, 1, s=s, seed=seed, with_lambda3=with_lambda3)
+    ss = np.random.SeedSequence([seed, 4242])
+    rB, rh = (np.random.Generator(np.random.PCG64(k)) for k in ss.spawn(2))
+    B = rB.standard_normal((naux, n, n))
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    B *= b_scale * np.exp(-b_decay * np.arange(naux, dtype=np.float64))[:, None, None]
+    h0 = np.concatenate([rh.uniform(-2.0, -0.3, ncore), rh.uniform(-0.2, 0.1, nactive),
+                         rh.uniform(0.05, 5.0, nvirt)])
+    R = rh.uniform(-0.05, 0.05, (n, n))
+    h = np.diag(h0) + 0.5 * (R + R.T)
+    return FockProblem(ncore, nactive, nvirt, naux, float(s), h, B, base.gamma1, base.lambda2,
+                       base.lambda3)
+
+
+@dataclasses.dataclass
+class AOProblem:
+    """Inputs of the DF integral transformation (Sec. II.C): AO three-centre
+    integrals, the two-centre metric and MO coefficients."""
+    nbf: int
+    naux: int
+    ao3: np.ndarray    # [naux, nbf, nbf] (mu nu|P), symmetric in (mu, nu)
+    metric: np.ndarray  # [naux, naux] J_PQ, symmetric positive definite
+    C: np.ndarray      # [nbf, nmo] MO coefficients
+
+
+def make_ao_problem(nbf: int, nmo: int, naux: int, seed: int = 0) -> AOProblem:
+    """``ao3[P, mu, nu]`` = 0.3 N(0,1) exp(-0.02 P), symmetrised in (mu, nu);
+    ``metric`` = W diag(w) W^T with a Haar-random orthogonal W and w log-uniform
+    in [0.1, 10]; ``C`` = the first nmo columns of a Haar-random orthogonal matrix."""
+    ss = np.random.SeedSequence([seed, 1603])
+    ra, rm, rc = (np.random.Generator(np.random.PCG64(k)) for k in ss.spawn(3))
+    ao3 = ra.standard_normal((naux, nbf, nbf))
+    ao3 = 0.5 * (ao3 + ao3.transpose(0, 2, 1))
+    ao3 *= 0.3 * np.exp(-0.02 * np.arange(naux, dtype=np.float64))[:, None, None]
+    W = _haar_orthogonal(rm, naux)
+    w = np.exp(rm.uniform(np.log(0.1), np.log(10.0), naux))
+    metric = (W * w[None, :]) @ W.T
+    metric = 0.5 * (metric + metric.T)
+    C = _haar_orthogonal(rc, nbf)[:, :nmo]
+    return AOProblem(nbf, naux, ao3, metric, np.ascontiguousarray(C))
+
+
+def make_eri_factors(n: int, rank: int, seed: int = 0, scale: float = 0.3,
+                     decay: float = 0.02) -> np.ndarray:
+    """Exact low-rank factors of a synthetic two-electron integral matrix for
+    the Cholesky decomposition: ``F[k, p, q]`` = scale N(0,1) exp(-decay k),
+    symmetric in (p, q); the integrals are (pq|rs) = sum_k F[k,p,q] F[k,r,s]."""
+    r = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 315])))
+    F = r.standard_normal((rank, n, n))
+    F = 0.5 * (F + F.transpose(0, 2, 1))
+    return F * scale * np.exp(-decay * np.arange(rank, dtype=np.float64))[:, None, None]
 
 
 # The synthetic workloads, by what they stand for (sizes nC/nA/nV/naux, s).

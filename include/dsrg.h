@@ -309,6 +309,51 @@ dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t *sz, const double *B, 
 dsrg_status_t dsrg_plan_branch_counts(dsrg_plan_t *plan, uint64_t counts[DSRG_NCOUNTERS],
                                       int32_t reset);
 
+/* ---- Generalized Fock matrix and semicanonical orbitals (Sec. II.B, Eq. (8);
+ * Sec. III, steps 2-3 of the procedure) ----
+ * Inputs over ALL orbitals (not only the hole x particle block), ordered
+ * [core | active | virtual], n = nC + nA + nV:
+ *   h      [n][n]          one-electron integrals (symmetric);
+ *   Bfull  [naux][n][n]    DF/CD factors B^Q_pq (symmetric in p, q), Eq. (19);
+ *   gamma1 [nA][nA]        spin-summed active density (may be NULL if nA == 0).
+ * The Fock matrix is Eq. (8) for the reference's spin-free density D (2 on the
+ * core diagonal, gamma1 on the active block):
+ *   f_pq = h_pq + sum_rs D_rs [(pq|rs) - 1/2 (ps|rq)],
+ * in FP64 (the exchange part is one FP64 GEMM over the composite index (Q, r)).
+ * Semicanonicalisation diagonalises the core, active and virtual blocks of f
+ * separately (FP64 parallel cyclic Jacobi; eigenvalues ascending within each
+ * block, each eigenvector's largest component positive) and returns, for the
+ * orbitals U = blockdiag(U_C, U_A, U_V), the inputs of dsrg_mrpt2_energy_ext:
+ *   eps_out     [n]              diagonal of U^T f U;
+ *   B_out       [naux][nH][nP]   hole x particle block of U^T B^Q U;
+ *   f1_out      [nH][nP]         hole x particle block of U^T f U (f^(1); its
+ *                                active x active part, diagonal, set to 0);
+ *   gamma1_out  [nA][nA]         U_A^T gamma1 U_A;
+ *   lambda2_out [nA]^4           lambda2 rotated by U_A on every index;
+ *   lambda3_out [2nA]^6          the spin-orbital lambda3 rotated by U_A (x) 1
+ *                                on every index (only if lambda3 != NULL);
+ *   U_out       [n][n]           U (may be NULL).
+ * All arrays are caller-owned device arrays, 8-byte aligned. The plan owns its
+ * workspace (about naux*n*(nH+1) + 2*naux*nH*nP + 6 n^2 doubles). The
+ * semicanonicalisation synchronises the plan's stream (the Jacobi sweeps stop
+ * on a convergence test read by the host, ||offdiag||^2 <= 1e-30 ||A||^2, at
+ * most 30 sweeps) and is not meant to be captured in a graph. */
+typedef struct dsrg_sc_plan dsrg_sc_plan_t;
+/* sz->ncore, nactive, nvirt >= 0 (n >= 1), naux >= 1, nactive <= 8. */
+dsrg_status_t dsrg_sc_plan_create(dsrg_sc_plan_t **plan, const dsrg_sizes_t *sz, void *cuda_stream);
+dsrg_status_t dsrg_sc_plan_destroy(dsrg_sc_plan_t *plan);
+/* f_dev [n][n]: the generalized Fock matrix (asynchronous, on the plan's stream). */
+dsrg_status_t dsrg_generalized_fock(dsrg_sc_plan_t *plan, const double *h, const double *Bfull,
+                                    const double *gamma1, double *f_dev);
+dsrg_status_t dsrg_semicanonicalize(dsrg_sc_plan_t *plan, const double *h, const double *Bfull,
+                                    const double *gamma1, const double *lambda2,
+                                    const double *lambda3, double *eps_out, double *B_out,
+                                    double *f1_out, double *gamma1_out, double *lambda2_out,
+                                    double *lambda3_out, double *U_out);
+/* Jacobi sweeps of the slowest-converging block in the last call. */
+int32_t dsrg_sc_last_sweeps(const dsrg_sc_plan_t *plan);
+const char *dsrg_sc_last_error(const dsrg_sc_plan_t *plan);
+
 /* Wait for the plan's stream and report any device-side condition recorded
  * since the last call (DSRG_ERR_TIMEOUT), then clear it. */
 dsrg_status_t dsrg_plan_sync(dsrg_plan_t *plan);

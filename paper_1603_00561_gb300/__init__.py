@@ -15,7 +15,8 @@ import torch
 from . import _native
 from ._native import DSRGError, PREC
 
-__all__ = ["Plan", "Batch", "DSRGError", "PREC", "BLOCKS", "build", "DSRGEnergy", "energy_total"]
+__all__ = ["Plan", "Batch", "DSRGError", "PREC", "BLOCKS", "build", "DSRGEnergy", "energy_total",
+           "SemicanonicalPlan"]
 
 BLOCKS = ("ccvv", "cavv", "ccav", "active", "total")
 
@@ -263,6 +264,67 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.lib.dsrg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SemicanonicalPlan:
+    """Generalized Fock matrix (Eq. (8)) and the semicanonical basis
+    (``dsrg_sc_plan_create``, ``dsrg_generalized_fock``, ``dsrg_semicanonicalize``):
+    from h [n, n], the full DF factors Bfull [naux, n, n] and the active density,
+    the inputs of the energy in the semicanonical orbitals."""
+
+    def __init__(self, ncore: int, nactive: int, nvirt: int, naux: int, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the DSRG-MRPT2 library needs a CUDA GPU")
+        self.lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.sizes = (int(ncore), int(nactive), int(nvirt), int(naux))
+        sz = _native.Sizes(*self.sizes)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.dsrg_sc_plan_create(C.byref(h), C.byref(sz),
+                                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if st != _native.OK:
+            raise DSRGError(st, f"dsrg_sc_plan_create{self.sizes}")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != _native.OK:
+            raise DSRGError(st, f"{what}: {self.lib.dsrg_sc_last_error(self.h).decode()}")
+
+    def fock(self, h, Bfull, gamma1):
+        n = sum(self.sizes[:3])
+        f = torch.empty((n, n), dtype=torch.float64, device=self.device)
+        self._check(self.lib.dsrg_generalized_fock(self.h, _ptr(h), _ptr(Bfull), _ptr(gamma1), _ptr(f)),
+                    "dsrg_generalized_fock")
+        return f
+
+    def semicanonicalize(self, h, Bfull, gamma1, lambda2, lambda3=None) -> dict:
+        nC, nA, nV, Q = self.sizes
+        n, nH, nP = nC + nA + nV, nC + nA, nA + nV
+        z = lambda *shape: torch.empty(shape, dtype=torch.float64, device=self.device)
+        out = dict(eps=z(n), B=z(Q, nH, nP), f1=z(nH, nP), U=z(n, n),
+                   gamma1=z(nA, nA) if nA else None, lambda2=z(nA, nA, nA, nA) if nA else None,
+                   lambda3=z(*(2 * nA,) * 6) if (nA and lambda3 is not None) else None)
+        st = self.lib.dsrg_semicanonicalize(
+            self.h, _ptr(h), _ptr(Bfull), _ptr(gamma1), _ptr(lambda2), _ptr(lambda3),
+            _ptr(out["eps"]), _ptr(out["B"]), _ptr(out["f1"]), _ptr(out["gamma1"]),
+            _ptr(out["lambda2"]), _ptr(out["lambda3"]), _ptr(out["U"]))
+        self._check(st, "dsrg_semicanonicalize")
+        return out
+
+    def last_sweeps(self) -> int:
+        return int(self.lib.dsrg_sc_last_sweeps(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dsrg_sc_plan_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -27,7 +27,8 @@ EXPORTS = [
     "dsrg_plan_autotune", "dsrg_batch_autotune", "dsrg_plan_item_order", "dsrg_batch_item_order",
     "dsrg_plan_time_ccvv", "dsrg_plan_set_item_order", "dsrg_batch_set_item_order",
     "dsrg_plan_selftest_wait_timeout", "dsrg_plan_branch_counts", "dsrg_mrpt2_energy_ext",
-    "dsrg_mrpt2_energy_grad_ext",
+    "dsrg_mrpt2_energy_grad_ext", "dsrg_sc_plan_create", "dsrg_sc_plan_destroy", "dsrg_generalized_fock",
+    "dsrg_semicanonicalize", "dsrg_sc_last_sweeps", "dsrg_sc_last_error",
 ]
 # indices of dsrg_plan_branch_counts
 NCOUNTERS = 8
@@ -75,6 +76,18 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_plan_sync.restype = st
     lib.dsrg_plan_selftest_wait_timeout.argtypes = [vp]
     lib.dsrg_plan_selftest_wait_timeout.restype = st
+    lib.dsrg_sc_plan_create.argtypes = [C.POINTER(vp), C.POINTER(Sizes), vp]
+    lib.dsrg_sc_plan_create.restype = st
+    lib.dsrg_sc_plan_destroy.argtypes = [vp]
+    lib.dsrg_sc_plan_destroy.restype = st
+    lib.dsrg_generalized_fock.argtypes = [vp, vp, vp, vp, vp]
+    lib.dsrg_generalized_fock.restype = st
+    lib.dsrg_semicanonicalize.argtypes = [vp] + [vp] * 12
+    lib.dsrg_semicanonicalize.restype = st
+    lib.dsrg_sc_last_sweeps.argtypes = [vp]
+    lib.dsrg_sc_last_sweeps.restype = C.c_int32
+    lib.dsrg_sc_last_error.argtypes = [vp]
+    lib.dsrg_sc_last_error.restype = C.c_char_p
     lib.dsrg_plan_branch_counts.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int32]
     lib.dsrg_plan_branch_counts.restype = st
     lib.dsrg_plan_last_launch_count.argtypes = [vp]

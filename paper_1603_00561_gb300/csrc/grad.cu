@@ -72,23 +72,6 @@ __device__ __forceinline__ RegD rf1_d(double D, double s) {
 //   C[i*ci + j*cj] (+)= alpha * sum_{l1<L1, l2<L2} A[i*ai + l1*a1 + l2*a2] * Bm[l1*b1 + l2*b2 + j*bj]
 // 64 x 64 tiles, 256 threads, K chunks of 16 over l = l1*L2 + l2.
 // ---------------------------------------------------------------------------
-struct GemmArgs {
-  int M, N, L1, L2;
-  const double* A;
-  long long ai, a1, a2;
-  const double* Bm;
-  long long b1, b2, bj;
-  double* C;
-  long long ci, cj;
-  double alpha;
-  int accumulate;
-  int nb;                // independent problems in one launch (blockIdx.z);
-  long long sa, sb, sc;  // their offsets of A, Bm, C
-  // FP32 copies of A and Bm (same element offsets) for the FP32 GEMM, or null
-  const float* A32;
-  const float* B32;
-};
-
 __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
   __shared__ double sA[16][65], sB[16][65];
   g.A += blockIdx.z * g.sa;
@@ -297,6 +280,13 @@ struct GradWs {
 __global__ void to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, size_t n) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) y[k] = (float)x[k];
+}
+
+cudaError_t launch_gemm_fp64(cudaStream_t st, const GemmArgs& g) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.nb);
+  gemm_fp64_kernel<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
 }
 
 // FP64 plans: FP64 GEMM; split-precision plans: FP32 GEMM.
@@ -1461,7 +1451,7 @@ void grad_free(dsrg_plan* p) {
   p->grad = nullptr;
 }
 
-static GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, long long a1,
+GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, long long a1,
                    long long a2, const double* Bm, long long b1, long long b2, long long bj,
                    double* C, long long ci, long long cj, double alpha) {
   GemmArgs g;
@@ -1478,7 +1468,7 @@ static GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, 
 }
 
 // The same GEMM for nb problems whose A, Bm, C start sa, sb, sc elements apart.
-static GemmArgs batched(GemmArgs g, int nb, long long sa, long long sb, long long sc) {
+GemmArgs batched(GemmArgs g, int nb, long long sa, long long sb, long long sc) {
   g.nb = nb;
   g.sa = sa;
   g.sb = sb;

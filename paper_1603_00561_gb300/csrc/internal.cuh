@@ -212,6 +212,32 @@ cudaError_t split_prepare_single(dsrg_plan* p, const double* eps, double s);
 void split_schedule(const std::vector<int4>& items, const std::vector<double>& cost, int ncta,
                     std::vector<int4>& out, std::vector<int>& begin);
 
+// Generic GEMM with a composite K index (grad.cu):
+//   C[i*ci + j*cj] (+)= alpha * sum_{l1<L1, l2<L2} A[i*ai + l1*a1 + l2*a2] * Bm[l1*b1 + l2*b2 + j*bj]
+// for nb problems whose A, Bm, C start sa, sb, sc elements apart.
+struct GemmArgs {
+  int M, N, L1, L2;
+  const double* A;
+  long long ai, a1, a2;
+  const double* Bm;
+  long long b1, b2, bj;
+  double* C;
+  long long ci, cj;
+  double alpha;
+  int accumulate;
+  int nb;                // independent problems in one launch (blockIdx.z);
+  long long sa, sb, sc;  // their offsets of A, Bm, C
+  // FP32 copies of A and Bm (same element offsets) for the FP32 GEMM, or null
+  const float* A32;
+  const float* B32;
+};
+GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, long long a1, long long a2,
+            const double* Bm, long long b1, long long b2, long long bj, double* C, long long ci,
+            long long cj, double alpha);
+GemmArgs batched(GemmArgs g, int nb, long long sa, long long sb, long long sc);
+// FP64 (64 x 64 tiles, FP64 FMA) on stream st; accumulate = 1 adds to C.
+cudaError_t launch_gemm_fp64(cudaStream_t st, const GemmArgs& g);
+
 // Gradient (grad.cu).
 bool grad_alloc(dsrg_plan* p);
 void grad_free(dsrg_plan* p);

@@ -48,7 +48,7 @@ constexpr uint32_t G_TMEM_COLS = 512;
 constexpr int XROW_ALIGN = 64;
 constexpr int F2_T = 32;                              // F2 epilogue tile edge
 
-struct GemmArgs {
+struct TcGemmArgs {
   int a_row0;        // row r of Y is plane row a_row0 + r
   int b_row0;        // column c of Y is plane row b_row0 + c
   int m_tiles, n_tiles;
@@ -94,7 +94,7 @@ __device__ __forceinline__ void gemm_stage_mmas(uint32_t d, uint32_t sa, uint32_
 template <bool BF16>
 __global__ void __launch_bounds__(G_THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap map_hi,
-                      const __grid_constant__ CUtensorMap map_lo, const GemmArgs a) {
+                      const __grid_constant__ CUtensorMap map_lo, const TcGemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* tiles = smem;
@@ -768,7 +768,7 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     DSRG_LAUNCH_CHECK(p);
   }
   {
-    GemmArgs a;
+    TcGemmArgs a;
     a.a_row0 = 0;
     a.b_row0 = z.nC * st->nVpad;
     a.m_tiles = st->m_tiles;
