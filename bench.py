@@ -156,6 +156,16 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
+def sum_over_ranks(t, world):
+    """Sum of a tensor over all ranks (the partial block energies of a sharded
+    molecule: one all-reduce of 5 doubles). One rank: t itself."""
+    if world <= 1:
+        return t
+    import torch.distributed as dist
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t
+
+
 def job_rate(world, units_per_rank, seconds):
     """Whole-job throughput under weak scaling: every rank processes the same
     units (its own molecule), so the job does world * units in `seconds`."""
@@ -335,6 +345,10 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: all ranks share ONE molecule (its core pairs dealt "
+                         "round-robin, one all-reduce of the 5 block energies per step; strong "
+                         "scaling) instead of one molecule per rank (weak scaling)")
     ap.add_argument("--no-grad", action="store_true",
                     help="skip the gradient leg (cc-pVTZ size, FP64 and split plans)")
     ap.add_argument("--with-batch", type=int, default=64, metavar="NMOL",
@@ -374,8 +388,10 @@ def main():
                   flush=True)
         return
     cfg = WORKLOADS[args.workload]
-    # weak scaling: each rank its own molecule of the same size
-    p = make_problem(seed=rank, **cfg)
+    shard = args.shard and world > 1
+    # weak scaling: each rank its own molecule of the same size; --shard: one
+    # molecule (seed 0) shared by all ranks
+    p = make_problem(seed=0 if shard else rank, **cfg)
     prec = args.precision
     try:
         plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, host_io=True)
@@ -408,8 +424,13 @@ def main():
     else:
         item_order = plan.autotune(B, eps, p.s, reps=2)
 
+    if shard:
+        plan.set_shard(rank, world)
+
     def step():
         plan.energy(B, eps, g, l, p.s, out=out)
+        if shard:
+            sum_over_ranks(out, world)   # the partial block energies of the ranks
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -436,7 +457,8 @@ def main():
     energies = out.cpu().numpy().tolist()
 
     flops = ccvv_flops(p.ncore, p.nvirt, p.naux)
-    value = job_rate(world, flops, t_step) / 1e12
+    # weak: every rank did a whole molecule; shard: the ranks did one together
+    value = (flops / t_step if shard else job_rate(world, flops, t_step)) / 1e12
 
     # dominant kernel: the CCVV pair contraction alone, timed with CUDA events on the
     # plan's stream inside the library (planes staged first, one untimed launch)
@@ -542,7 +564,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "scaling": "strong" if shard else "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, **cfg, "precision": prec,
                        "item_order": item_order,

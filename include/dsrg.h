@@ -354,6 +354,61 @@ dsrg_status_t dsrg_semicanonicalize(dsrg_sc_plan_t *plan, const double *h, const
 int32_t dsrg_sc_last_sweeps(const dsrg_sc_plan_t *plan);
 const char *dsrg_sc_last_error(const dsrg_sc_plan_t *plan);
 
+/* ---- Integral factorisations (Sec. II.C) ----
+ * Density fitting in the MO basis: the factors B^Q_pq = sum_P [W]_QP (pq|P) of
+ * the MO three-centre integrals (pq|P) = sum_{mu nu} C_{mu p} (mu nu|P) C_{nu q}
+ * for p in [p0, p0 + np), q in [q0, q0 + nq) (e.g. holes x particles, or all
+ * orbitals for the Fock build), with W W^T = J^{-1}. The paper writes
+ * W = J^{-1/2}; every such W gives the same integrals sum_Q B^Q_pq B^Q_rs and
+ * the same energy, and this call takes W = L^{-1} from the Cholesky factor
+ * J = L L^T (the factors differ from the J^{-1/2} ones by an orthogonal rotation
+ * of the auxiliary index). FP64 throughout.
+ *   ao3    [naux][nbf][nbf]  AO three-centre integrals (mu nu|P), symmetric in mu nu;
+ *   C      [nbf][nmo]        MO coefficients;
+ *   metric [naux][naux]      two-centre integrals J_PQ, symmetric positive definite;
+ *   B_out  [naux][np][nq];
+ *   work   caller-owned device scratch of dsrg_df_mo_transform_work_bytes() bytes.
+ * Synchronous (it reads back the positivity check of the metric):
+ * DSRG_ERR_INVALID_ARG if the metric is not positive definite. */
+size_t dsrg_df_mo_transform_work_bytes(int32_t nbf, int32_t naux, int32_t np, int32_t nq);
+dsrg_status_t dsrg_df_mo_transform(const double *ao3, const double *C, const double *metric,
+                                   int32_t nbf, int32_t nmo, int32_t naux, int32_t p0, int32_t np,
+                                   int32_t q0, int32_t nq, double *B_out, double *work,
+                                   size_t work_bytes, void *cuda_stream);
+
+/* Cholesky decomposition of the two-electron integrals: the pivoted incomplete
+ * Cholesky decomposition (outer-product form with diagonal pivoting) of the
+ * positive semi-definite matrix M[(pq),(rs)] = (pq|rs) over all n^2 orbital
+ * pairs, stopped when the largest remaining diagonal element is below tau (the
+ * paper's threshold is 1e-5 Eh) or after max_rank vectors. M is given by
+ * factors F [nfac][n][n] (M = sum_k F^k (F^k)^T, e.g. exact integrals of a
+ * small basis or a finer factorisation). Output: L_out [max_rank][n][n], of
+ * which the first *rank_out are the Cholesky vectors B^Q_pq; every integral
+ * of M - sum_Q B^Q (B^Q)^T is below tau in magnitude. FP64. work: caller-owned
+ * device scratch of dsrg_cd_factors_work_bytes(n) bytes. Synchronous (the rank
+ * is read back). */
+size_t dsrg_cd_factors_work_bytes(int32_t n);
+dsrg_status_t dsrg_cd_factors(const double *F, int32_t nfac, int32_t n, double tau,
+                              int32_t max_rank, double *L_out, int32_t *rank_out, double *work,
+                              size_t work_bytes, void *cuda_stream);
+
+/* ---- Several GPUs on one molecule (the paper's loop over core pairs, Sec. III,
+ * dealt to ranks instead of threads) ----
+ * After dsrg_plan_set_shard(plan, rank, world), the plan's energy and gradient
+ * calls compute only this rank's share: the CCVV (F1) core pairs i <= j whose
+ * index in row-major order is = rank (mod world), and, on rank 0 only, the
+ * other blocks (CAVV, CCAV, active). out[5] then holds this rank's partial
+ * block energies: their sum over the ranks is the energy (one reduction of 5
+ * doubles, e.g. an all-reduce). The gradient's F1 adjoint is dealt by groups of
+ * core rows (their dB rows are disjoint) and the other adjoints run on rank 0,
+ * so dB, deps and ds are partial too and sum over the ranks. Every rank needs
+ * the whole B. world = 1 restores the full computation. Waits for the plan's
+ * stream; do not call while the stream is being captured. */
+dsrg_status_t dsrg_plan_set_shard(dsrg_plan_t *plan, int32_t rank, int32_t world);
+/* Host-only: the (i, j) core pairs of a shard, pairs_out[2k] = i, [2k+1] = j
+ * (pairs_out may be NULL); returns their number, -1 for bad arguments. */
+int32_t dsrg_shard_pairs(int32_t ncore, int32_t rank, int32_t world, int32_t *pairs_out);
+
 /* Wait for the plan's stream and report any device-side condition recorded
  * since the last call (DSRG_ERR_TIMEOUT), then clear it. */
 dsrg_status_t dsrg_plan_sync(dsrg_plan_t *plan);

@@ -9,6 +9,7 @@ is no CPU path. Importing the package does not load the library; the first
 from __future__ import annotations
 
 import ctypes as C
+import ctypes as C_
 
 import torch
 
@@ -16,7 +17,7 @@ from . import _native
 from ._native import DSRGError, PREC
 
 __all__ = ["Plan", "Batch", "DSRGError", "PREC", "BLOCKS", "build", "DSRGEnergy", "energy_total",
-           "SemicanonicalPlan"]
+           "SemicanonicalPlan", "df_mo_transform", "cd_factors", "shard_pairs"]
 
 BLOCKS = ("ccvv", "cavv", "ccav", "active", "total")
 
@@ -176,6 +177,12 @@ class Plan:
     def sync(self):
         self._check(self.lib.dsrg_plan_sync(self.h), "dsrg_plan_sync")
 
+    def set_shard(self, rank: int, world: int):
+        """Compute only this rank's share of the molecule (``dsrg_plan_set_shard``):
+        energies and gradients become partial sums over ranks."""
+        self._check(self.lib.dsrg_plan_set_shard(self.h, int(rank), int(world)),
+                    "dsrg_plan_set_shard")
+
     def branch_counts(self, reset: bool = False) -> dict:
         """Epilogue branch counters of the split kernels (``dsrg_plan_branch_counts``)."""
         arr = (C.c_uint64 * _native.NCOUNTERS)()
@@ -332,6 +339,56 @@ class SemicanonicalPlan:
             self.close()
         except Exception:
             pass
+
+
+def shard_pairs(ncore: int, rank: int, world: int):
+    """The (i, j) core pairs of one rank's share (``dsrg_shard_pairs``; host only,
+    needs the library but no GPU)."""
+    lib = _native.load()
+    n = int(lib.dsrg_shard_pairs(int(ncore), int(rank), int(world), None))
+    if n < 0:
+        raise ValueError("bad shard arguments")
+    buf = (C_.c_int32 * (2 * max(n, 1)))()
+    lib.dsrg_shard_pairs(int(ncore), int(rank), int(world), buf)
+    return [(buf[2 * k], buf[2 * k + 1]) for k in range(n)]
+
+
+def df_mo_transform(ao3, C, metric, p0: int = 0, np_: int | None = None, q0: int = 0,
+                    nq: int | None = None):
+    """DF factors B^Q_pq of the MO three-centre integrals for p in [p0, p0+np_),
+    q in [q0, q0+nq) (``dsrg_df_mo_transform``; metric square root from its
+    Cholesky factor). Device tensors in, [naux, np_, nq] device tensor out."""
+    lib = _native.load()
+    naux, nbf, _ = ao3.shape
+    nmo = C.shape[1]
+    np_ = nmo - p0 if np_ is None else np_
+    nq = nmo - q0 if nq is None else nq
+    out = torch.empty((naux, np_, nq), dtype=torch.float64, device=ao3.device)
+    wb = int(lib.dsrg_df_mo_transform_work_bytes(nbf, naux, np_, nq))
+    work = torch.empty((wb + 7) // 8, dtype=torch.float64, device=ao3.device)
+    st = lib.dsrg_df_mo_transform(_ptr(ao3), _ptr(C), _ptr(metric), nbf, nmo, naux, p0, np_, q0, nq,
+                                  _ptr(out), _ptr(work), wb,
+                                  C_.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != _native.OK:
+        raise DSRGError(st, "dsrg_df_mo_transform")
+    return out
+
+
+def cd_factors(F, tau: float = 1e-5, max_rank: int | None = None):
+    """Pivoted Cholesky vectors of the integral matrix sum_k F^k (F^k)^T
+    (``dsrg_cd_factors``): F [nfac, n, n] device tensor; returns [rank, n, n]."""
+    lib = _native.load()
+    nfac, n, _ = F.shape
+    max_rank = n * n if max_rank is None else max_rank
+    L = torch.empty((max_rank, n, n), dtype=torch.float64, device=F.device)
+    wb = int(lib.dsrg_cd_factors_work_bytes(n))
+    work = torch.empty((wb + 7) // 8, dtype=torch.float64, device=F.device)
+    rank = C_.c_int32(0)
+    st = lib.dsrg_cd_factors(_ptr(F), nfac, n, float(tau), max_rank, _ptr(L), C_.byref(rank),
+                             _ptr(work), wb, C_.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != _native.OK:
+        raise DSRGError(st, "dsrg_cd_factors")
+    return L[: rank.value]
 
 
 class DSRGEnergy(torch.autograd.Function):

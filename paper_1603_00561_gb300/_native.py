@@ -29,6 +29,8 @@ EXPORTS = [
     "dsrg_plan_selftest_wait_timeout", "dsrg_plan_branch_counts", "dsrg_mrpt2_energy_ext",
     "dsrg_mrpt2_energy_grad_ext", "dsrg_sc_plan_create", "dsrg_sc_plan_destroy", "dsrg_generalized_fock",
     "dsrg_semicanonicalize", "dsrg_sc_last_sweeps", "dsrg_sc_last_error",
+    "dsrg_df_mo_transform_work_bytes", "dsrg_df_mo_transform", "dsrg_cd_factors_work_bytes",
+    "dsrg_cd_factors", "dsrg_plan_set_shard", "dsrg_shard_pairs",
 ]
 # indices of dsrg_plan_branch_counts
 NCOUNTERS = 8
@@ -86,6 +88,21 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_semicanonicalize.restype = st
     lib.dsrg_sc_last_sweeps.argtypes = [vp]
     lib.dsrg_sc_last_sweeps.restype = C.c_int32
+    i32 = C.c_int32
+    lib.dsrg_df_mo_transform_work_bytes.argtypes = [i32, i32, i32, i32]
+    lib.dsrg_df_mo_transform_work_bytes.restype = C.c_size_t
+    lib.dsrg_df_mo_transform.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp,
+                                         C.c_size_t, vp]
+    lib.dsrg_df_mo_transform.restype = st
+    lib.dsrg_cd_factors_work_bytes.argtypes = [i32]
+    lib.dsrg_cd_factors_work_bytes.restype = C.c_size_t
+    lib.dsrg_cd_factors.argtypes = [vp, i32, i32, C.c_double, i32, vp, C.POINTER(i32), vp,
+                                    C.c_size_t, vp]
+    lib.dsrg_cd_factors.restype = st
+    lib.dsrg_plan_set_shard.argtypes = [vp, i32, i32]
+    lib.dsrg_plan_set_shard.restype = st
+    lib.dsrg_shard_pairs.argtypes = [i32, i32, i32, C.POINTER(i32)]
+    lib.dsrg_shard_pairs.restype = i32
     lib.dsrg_sc_last_error.argtypes = [vp]
     lib.dsrg_sc_last_error.restype = C.c_char_p
     lib.dsrg_plan_branch_counts.argtypes = [vp, C.POINTER(C.c_uint64), C.c_int32]

@@ -332,6 +332,12 @@ namespace dsrg {
 dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
                        const double* L, const double* L3, const double* F1, double s, double* out) {
   cudaError_t e;
+  if (p->shard_rank != 0) {
+    // another rank's plan computes CAVV, CCAV and the active block; this
+    // rank's segments of them stay at the zeros set by dsrg_plan_set_shard
+    if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
+    return DSRG_OK;
+  }
   if (p->rest_tc) {
     // one tensor-core GEMM feeds CAVV, CCAV and the active-block integrals
     if ((e = launch_split_rest(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv/ccav");
@@ -560,6 +566,35 @@ dsrg_status_t dsrg_plan_selftest_wait_timeout(dsrg_plan_t* p) {
   p->launches = 0;
   cudaError_t e = launch_wait_selftest(p);
   if (e != cudaSuccess) return cuda_fail(p, e, "wait self-test");
+  return DSRG_OK;
+}
+
+int32_t dsrg_shard_pairs(int32_t ncore, int32_t rank, int32_t world, int32_t* pairs_out) {
+  if (ncore < 1 || world < 1 || rank < 0 || rank >= world) return -1;
+  int32_t n = 0, k = 0;
+  for (int i = 0; i < ncore; ++i)
+    for (int j = i; j < ncore; ++j, ++k)
+      if (pair_in_shard(k, rank, world)) {
+        if (pairs_out) {
+          pairs_out[2 * n] = i;
+          pairs_out[2 * n + 1] = j;
+        }
+        ++n;
+      }
+  return n;
+}
+
+dsrg_status_t dsrg_plan_set_shard(dsrg_plan_t* p, int32_t rank, int32_t world) {
+  if (!p || world < 1 || rank < 0 || rank >= world) return DSRG_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(p, e, "set shard");
+  p->shard_rank = rank;
+  p->shard_world = world;
+  // every partial slot starts at zero: the slots of another rank's work are
+  // never written again
+  e = cudaMemset(p->d_partials, 0, (size_t)p->n_partials * sizeof(double));
+  if (e == cudaSuccess && p->split) e = split_set_order(p, split_order(p));
+  if (e != cudaSuccess) return cuda_fail(p, e, "set shard");
   return DSRG_OK;
 }
 

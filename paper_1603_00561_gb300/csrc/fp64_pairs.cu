@@ -23,10 +23,14 @@ constexpr int T64 = 64, KC64 = 16;
 __global__ void __launch_bounds__(256) ccvv_fp64_kernel(
     const double* __restrict__ B, const double* __restrict__ eps, double s, Sizes z,
     const int2* __restrict__ pairs, const int2* __restrict__ tps, int n_tp,
-    double* __restrict__ partials) {
+    double* __restrict__ partials, int shard_rank, int shard_world) {
   __shared__ double sIA[KC64][T64], sJB[KC64][T64], sJA[KC64][T64], sIB[KC64][T64];
   __shared__ double red[8];
   const int item = blockIdx.x;
+  if (!pair_in_shard(item / n_tp, shard_rank, shard_world)) {
+    if (threadIdx.x == 0) partials[item] = 0.0;  // another rank's pair
+    return;
+  }
   const int2 ij = pairs[item / n_tp];
   const int2 ab = tps[item % n_tp];
   const int i = ij.x, j = ij.y;
@@ -103,7 +107,8 @@ int ccvv_fp64_blocks(const dsrg_plan* p) { return p->n_pairs * p->n_tp_ccvv; }
 cudaError_t launch_ccvv_fp64(dsrg_plan* p, const double* B, const double* eps, double s) {
   const Segment& sg = p->segs[p->seg_ccvv];
   ccvv_fp64_kernel<<<sg.count, 256, 0, p->stream>>>(B, eps, s, p->z, p->d_pairs, p->d_tp_ccvv,
-                                                    p->n_tp_ccvv, p->d_partials + sg.begin);
+                                                    p->n_tp_ccvv, p->d_partials + sg.begin,
+                                                    p->shard_rank, p->shard_world);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }

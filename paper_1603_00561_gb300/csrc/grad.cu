@@ -1530,8 +1530,10 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   const int n_tp = p->n_tp_ccvv;  // 64-wide tile pairs of the FP64 work list
   // rows k in groups of w->kgroup: W^{kj} of the group, then one batched GEMM
   const long long nVp = w->nVp, wstride = (long long)z.nC * nVp * nVp;
-  for (int k0 = 0; k0 < z.nC; k0 += w->kgroup) {
+  for (int k0 = 0, grp = 0; k0 < z.nC; k0 += w->kgroup, ++grp) {
     const int kg = (z.nC - k0) < w->kgroup ? (z.nC - k0) : w->kgroup;
+    // multi-GPU share: groups of core rows dealt round-robin (their dB rows are disjoint)
+    if (!pair_in_shard(grp, p->shard_rank, p->shard_world)) continue;
     if (fp64) {
       for (int k = k0; k < k0 + kg; ++k) {
         ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
@@ -1560,6 +1562,7 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     if (!fp64) gw.B32 = (const float*)w->Wk;
     if ((e = gemm(p, gw)) != cudaSuccess) return e;
   }
+  if (p->shard_rank != 0) return cudaSuccess;  // the other blocks' adjoints: rank 0
   if (z.nA == 0) {
     if (F1) {
       const int n = z.nC * z.nP;

@@ -106,6 +106,10 @@ struct dsrg_plan {
   cudaStream_t st_copy = nullptr;
   std::vector<cudaEvent_t> st_ev;
 
+  // multi-GPU share of this plan (dsrg_plan_set_shard): CCVV pairs with index
+  // = shard_rank (mod shard_world); the other blocks only on rank 0
+  int shard_rank = 0, shard_world = 1;
+
   // device status word (bounded waits)
   int* d_status = nullptr;
   // counters of the epilogue branches taken by the split kernels (DSRG_COUNT_*)
@@ -201,8 +205,13 @@ cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols, int first, int n,
 cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_mols,
                               const int4* d_items, const int* d_begin, int grid, bool bf16,
                               int prefetch);
+// items of pairs whose index is not = rank (mod world) are left out
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
-                     std::vector<double>& cost, int order);
+                     std::vector<double>& cost, int order, int rank = 0, int world = 1);
+// the shard of core pair index k (pairs i <= j in row-major order)
+__host__ __device__ inline bool pair_in_shard(int k, int rank, int world) {
+  return world <= 1 || k % world == rank;
+}
 extern const int SPLIT_ORDERS[];
 extern const int N_SPLIT_ORDERS;
 cudaError_t split_set_order(dsrg_plan* p, int order);

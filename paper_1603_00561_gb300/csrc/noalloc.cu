@@ -20,7 +20,7 @@ namespace dsrg {
 __global__ void ccvv_fp64_kernel(const double* __restrict__ B, const double* __restrict__ eps,
                                  double s, Sizes z, const int2* __restrict__ pairs,
                                  const int2* __restrict__ tps, int n_tp,
-                                 double* __restrict__ partials);
+                                 double* __restrict__ partials, int shard_rank, int shard_world);
 }  // namespace dsrg
 
 namespace {
@@ -185,7 +185,7 @@ extern "C" dsrg_status_t dsrg_ccvv_energy_noalloc(const dsrg_sizes_t* sz, const 
   const int2* pairs = (const int2*)(scratch + NA_ITEMS);
   const int2* tps = (const int2*)(scratch + NA_ITEMS + NA_PAIRS);
   dsrg::ccvv_fp64_kernel<<<(unsigned)(n_pairs * n_tp), 256, 0, st>>>(B, eps, s, z, pairs, tps,
-                                                                     (int)n_tp, scratch);
+                                                                     (int)n_tp, scratch, 0, 1);
   if (cudaGetLastError() != cudaSuccess) return DSRG_ERR_CUDA;
   noalloc_reduce_kernel<<<1, 256, 0, st>>>(scratch, (int)(n_pairs * n_tp), out_dev);
   if (cudaGetLastError() != cudaSuccess) return DSRG_ERR_CUDA;

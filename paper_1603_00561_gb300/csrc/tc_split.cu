@@ -802,12 +802,13 @@ void split_schedule(const std::vector<int4>& items, const std::vector<double>& c
 // Consecutive items run at the same time on different SMs, so the order sets
 // which operand tiles share the L2 at any moment.
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
-                     std::vector<double>& cost, int order) {
+                     std::vector<double>& cost, int order, int rank, int world) {
   const int nT = (z.nV + TT - 1) / TT, nC = z.nC;
   const int n_tp = nT * (nT + 1) / 2;
   auto pair_index = [&](int i, int j) { return i * nC - i * (i - 1) / 2 + (j - i); };
   auto tp_index = [&](int A, int B) { return A * nT - A * (A - 1) / 2 + (B - A); };
   auto push = [&](int i, int j, int A, int B) {
+    if (!pair_in_shard(pair_index(i, j), rank, world)) return;
     items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, pair_index(i, j) * n_tp + tp_index(A, B)));
     // MMA work: one GEMM for i = j, else two; plus a fixed share for the
     // epilogue. The narrower last tile is not weighted down: equal costs keep
@@ -928,7 +929,8 @@ cudaError_t split_set_order(dsrg_plan* p, int order) {
   std::vector<int4> items, sched;
   std::vector<double> cost;
   std::vector<int> begin;
-  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, order & 0xffff);
+  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, order & 0xffff, p->shard_rank,
+                  p->shard_world);
   split_schedule(items, cost, w->grid, sched, begin);
   cudaError_t e = cudaMemcpy(w->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
@@ -964,7 +966,7 @@ bool split_alloc_groups(dsrg_plan* p, const std::vector<int>& bounds) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
   std::vector<int4> items;
   std::vector<double> cost;
-  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, 0);
+  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, 0, p->shard_rank, p->shard_world);
   w->groups.resize(ngroups);
   for (int g = 0; g < ngroups; ++g) {
     SplitWs::Group& G = w->groups[g];
