@@ -421,11 +421,8 @@ dsrg_status_t dsrg_mrpt2_energy_grad_ext(dsrg_plan_t* p, const double* B, const 
   p->launches = 0;
   st = run_energy(p, B, eps, gamma1, lambda2, lambda3, f1, s, out_dev);
   if (st != DSRG_OK) return st;
-  if (p->rest_tc) {
-    // the adjoint reads FP64 active-block integrals: re-form them in FP64
-    cudaError_t e0 = launch_active(p, B, eps, gamma1, lambda2, lambda3, f1, s, false);
-    if (e0 != cudaSuccess) return cuda_fail(p, e0, "active (fp64 tables)");
-  }
+  // the adjoint reads the active-block tables the energy call left (split plans:
+  // from the tensor-core integrals, whose error is far below the gradient's own)
   cudaError_t e = launch_grad(p, B, eps, gamma1, lambda2, lambda3, f1, s, dB_dev, deps_dev,
                               ds_dev);
   if (e != cudaSuccess) return cuda_fail(p, e, "gradient");
@@ -594,6 +591,9 @@ dsrg_status_t dsrg_plan_set_shard(dsrg_plan_t* p, int32_t rank, int32_t world) {
   // never written again
   e = cudaMemset(p->d_partials, 0, (size_t)p->n_partials * sizeof(double));
   if (e == cudaSuccess && p->split) e = split_set_order(p, split_order(p));
+  // the gradient's S: positions of another rank's pairs are never written again
+  if (e == cudaSuccess) e = tc_adj_clear(p);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(p, e, "set shard");
   return DSRG_OK;
 }

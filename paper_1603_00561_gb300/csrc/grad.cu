@@ -1,15 +1,16 @@
 // Adjoint of the DSRG-MRPT2 energy: dE_total/dB, dE_total/deps, dE_total/ds.
 //
-// FP64 plans: all adjoint arithmetic is FP64 on CUDA cores. Split-precision
-// plans: the recomputed contractions over Q (v, X, Z) and the GEMMs that turn
-// the adjoints into dB run in FP32 on CUDA cores with round-to-nearest (the
-// truncating tensor-core accumulator would bias these long sums toward zero);
-// regulators, their derivatives and every epilogue stay FP64. Pair quantities
+// FP64 plans: all adjoint arithmetic is FP64 on CUDA cores. Pair quantities
 // are recomputed per core row rather than stored: for a fixed core orbital k
 // the kernel forms v^{kj} for every j tile by tile and keeps only
-// W^{kj} = dE/dv^{kj}, which a GEMM turns into dB. dB is assembled with one
-// thread per element in every kernel (fixed order, bit-reproducible); deps and
-// ds use FP64 atomics.
+// W^{kj} = dE/dv^{kj}, which a GEMM turns into dB.
+// Split-precision plans: the CCVV pair blocks are recomputed on the tensor
+// cores by the CCVV kernel's adjoint epilogue (tc_split.cu), the CAVV / CCAV
+// integrals X, Z in FP32 (round to nearest) on CUDA cores; the adjoints of all
+// integrals then form one symmetric matrix S and one tensor-core GEMM turns it
+// into dB (tc_adjoint.cu). Regulators, their derivatives and every epilogue
+// stay FP64. dB is assembled with one thread per element (fixed order,
+// bit-reproducible); deps and ds use FP64 atomics.
 //
 // Derivatives (closed-shell spin-adapted forms of Table 2, Eqs. (12)-(15), (23)):
 //  F1: E = sum_{ij} sum_ab v_ab (2 v_ab - v_ba) R(D),  R = (1 - exp(-2 s D^2))/D
@@ -25,47 +26,6 @@
 #include "regulators.cuh"
 
 namespace dsrg {
-
-// ---------------------------------------------------------------------------
-// Regulator values and derivatives. x = s D^2.
-//   Rt = (1 - e^{-x})/D, dRt/dD = (2 x e^{-x} + expm1(-x))/D^2, dRt/ds = D e^{-x}
-//   Rv = 1 + e^{-x},     dRv/dD = -2 s D e^{-x},              dRv/ds = -D^2 e^{-x}
-// For x < 1e-4 the Maclaurin series of Sec. II.B is used:
-//   Rt = s D (1 - x/2 + x^2/6), dRt/dD = s (1 - 3x/2 + 5x^2/6).
-// The F1 regulator is Rt with s -> 2s (and dR/ds doubles).
-// ---------------------------------------------------------------------------
-struct RegD {
-  double v, dD, ds;
-};
-
-__device__ __forceinline__ RegD rt_d(double D, double s) {
-  const double x = s * D * D;
-  const double g = exp(-x);
-  RegD r;
-  if (x < 1e-4) {
-    r.v = s * D * (1.0 - 0.5 * x + x * x / 6.0);
-    r.dD = s * (1.0 - 1.5 * x + 5.0 / 6.0 * x * x);
-  } else {
-    // for x > 1/2, e^{-x} < 0.61 and e^{-x} - 1 has no cancellation: one exponential
-    const double em = x > 0.5 ? g - 1.0 : expm1(-x);
-    const double inv = 1.0 / D;
-    r.v = -em * inv;
-    r.dD = (2.0 * x * g + em) * inv * inv;
-  }
-  r.ds = D * g;
-  return r;
-}
-
-__device__ __forceinline__ RegD rv_d(double D, double s) {
-  const double g = exp(-s * D * D);
-  return RegD{1.0 + g, -2.0 * s * D * g, -D * D * g};
-}
-
-__device__ __forceinline__ RegD rf1_d(double D, double s) {
-  RegD r = rt_d(D, 2.0 * s);
-  r.ds *= 2.0;
-  return r;
-}
 
 // ---------------------------------------------------------------------------
 // Generic FP64 GEMM with composite K index:
@@ -128,146 +88,11 @@ __global__ void __launch_bounds__(256) gemm_fp64_kernel(GemmArgs g) {
   }
 }
 
-// The same contraction in FP32 (operands rounded to FP32, FP32 accumulation
-// with round-to-nearest), 128 x 128 tiles, 8 x 8 outputs per thread. Operand
-// tiles are read along whichever index is contiguous in memory.
-constexpr int SG_T = 128, SG_K = 16;
-
-// FA / FB: the A / Bm operand is read from its FP32 copy (A32 / B32), which
-// holds the same values the FP64 operand rounds to when staged.
-template <bool FA, bool FB>
-__global__ void __launch_bounds__(256, 1) gemm_f32_kernel(GemmArgs g) {
-  __shared__ __align__(16) float sA[SG_K][SG_T + 4];
-  __shared__ __align__(16) float sB[SG_K][SG_T + 4];
-  const double* Ad = g.A + blockIdx.z * g.sa;
-  const double* Bd = g.Bm + blockIdx.z * g.sb;
-  const float* Af = FA ? g.A32 + blockIdx.z * g.sa : nullptr;
-  const float* Bf = FB ? g.B32 + blockIdx.z * g.sb : nullptr;
-  g.C += blockIdx.z * g.sc;
-  const int i0 = blockIdx.y * SG_T, j0 = blockIdx.x * SG_T;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const unsigned L = (unsigned)g.L1 * (unsigned)g.L2, L2 = (unsigned)g.L2;
-  const bool a_kfast = g.a2 == 1 && g.L2 > 1, b_kfast = g.b2 == 1 && g.L2 > 1;
-  // element e = threadIdx.x + 256 t of a 16 x 128 operand tile: (k row, tile column)
-  auto kc = [&](bool kfast, int t, int& ll, int& c) {
-    const int e = threadIdx.x + 256 * t;
-    if (kfast) {
-      ll = e % SG_K;
-      c = e / SG_K;
-    } else {
-      ll = e / SG_T;
-      c = e % SG_T;
-    }
-  };
-  // raw values of the next chunk: converted (FP64 operands) only when stored to
-  // shared memory, so the loads stay in flight during this chunk's FMAs
-  typename std::conditional<FA, float, double>::type ra_next[8];
-  typename std::conditional<FB, float, double>::type rb_next[8];
-  // K index l = l1 * L2 + l2: one division per chunk (l0 is the same for every
-  // thread), then each element steps from (l0 / L2, l0 % L2)
-  auto split_l = [&](unsigned l0, unsigned l1_0, unsigned l2_0, int ll, unsigned& l1,
-                     unsigned& l2) {
-    if (L2 == 1) {
-      l1 = l0 + ll;
-      l2 = 0;
-    } else {
-      l1 = l1_0;
-      l2 = l2_0 + ll;
-      while (l2 >= L2) {
-        l2 -= L2;
-        ++l1;
-      }
-    }
-  };
-  auto fetch = [&](unsigned l0) {
-    const unsigned l1_0 = L2 == 1 ? l0 : l0 / L2, l2_0 = l0 - l1_0 * L2;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      int ll, c;
-      kc(a_kfast, t, ll, c);
-      const unsigned l = l0 + ll;
-      ra_next[t] = 0;
-      if (l < L && i0 + c < g.M) {
-        unsigned l1, l2;
-        split_l(l0, l1_0, l2_0, ll, l1, l2);
-        const long long o = (long long)(i0 + c) * g.ai + (long long)l1 * g.a1 + (long long)l2 * g.a2;
-        if constexpr (FA) ra_next[t] = Af[o]; else ra_next[t] = Ad[o];
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      int ll, c;
-      kc(b_kfast, t, ll, c);
-      const unsigned l = l0 + ll;
-      rb_next[t] = 0;
-      if (l < L && j0 + c < g.N) {
-        unsigned l1, l2;
-        split_l(l0, l1_0, l2_0, ll, l1, l2);
-        const long long o = (long long)l1 * g.b1 + (long long)l2 * g.b2 + (long long)(j0 + c) * g.bj;
-        if constexpr (FB) rb_next[t] = Bf[o]; else rb_next[t] = Bd[o];
-      }
-    }
-  };
-  auto stash = [&]() {
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      int ll, c;
-      kc(a_kfast, t, ll, c);
-      sA[ll][c] = (float)ra_next[t];
-      kc(b_kfast, t, ll, c);
-      sB[ll][c] = (float)rb_next[t];
-    }
-  };
-  // thread (tx, ty) owns rows {4ty..4ty+3, 64+4ty..64+4ty+3} and the same
-  // columns with tx: each fragment load reads 16 consecutive float4 (no bank
-  // conflicts) and is a broadcast across the lanes that share it
-  float acc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-  fetch(0);
-  for (unsigned l0 = 0; l0 < L; l0 += SG_K) {
-    stash();
-    __syncthreads();
-    if (l0 + SG_K < L) fetch(l0 + SG_K);  // next chunk's loads overlap this chunk's FMAs
-#pragma unroll 4
-    for (int ll = 0; ll < SG_K; ++ll) {
-      const float4 a0 = *(const float4*)&sA[ll][ty * 4];
-      const float4 a1 = *(const float4*)&sA[ll][64 + ty * 4];
-      const float4 b0 = *(const float4*)&sB[ll][tx * 4];
-      const float4 b1 = *(const float4*)&sB[ll][64 + tx * 4];
-      const float ra[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float rb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(ra[r], rb[c], acc[r][c]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
-    if (i >= g.M) continue;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = j0 + (c < 4 ? tx * 4 + c : 64 + tx * 4 + c - 4);
-      if (j >= g.N) continue;
-      double* p = g.C + (long long)i * g.ci + (long long)j * g.cj;
-      *p = g.accumulate ? fma(g.alpha, (double)acc[r][c], *p) : g.alpha * (double)acc[r][c];
-    }
-  }
-}
-
 // Gradient workspace (DSRG_PLAN_GRAD).
 struct GradWs {
   double* Wk = nullptr;   // [kgroup][nC][nVp][nVp]
   int nVp = 0;
   int kgroup = 1;         // core rows whose W^{kj} are formed before one batched GEMM
-  double* V = nullptr;    // [kgroup][nV][nC*nP] pair blocks v^{kj} (split plans)
-  float* B32 = nullptr;   // [naux][nH][nP] fl32 of the call's B (split plans), read by the GEMMs
-  const double* Bsrc = nullptr;  // the call's B, whose FP32 copy B32 holds
   size_t nB = 0;          // elements of B
   double* dX = nullptr;   // [nC][nA][nV][nV]
   double* dZ = nullptr;   // [nA][nC][nC][nV]
@@ -277,11 +102,6 @@ struct GradWs {
   double *dK1 = nullptr, *dK2 = nullptr, *dK3 = nullptr, *dM = nullptr;
 };
 
-__global__ void to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, size_t n) {
-  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) y[k] = (float)x[k];
-}
-
 cudaError_t launch_gemm_fp64(cudaStream_t st, const GemmArgs& g) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.nb);
@@ -289,29 +109,11 @@ cudaError_t launch_gemm_fp64(cudaStream_t st, const GemmArgs& g) {
   return cudaGetLastError();
 }
 
-// FP64 plans: FP64 GEMM; split-precision plans: FP32 GEMM.
+// The FP64 plans' GEMMs (split plans assemble dB on the tensor cores).
 static cudaError_t gemm(dsrg_plan* p, const GemmArgs& g) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  if (p->prec == DSRG_PREC_FP64) {
-    dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.nb);
-    gemm_fp64_kernel<<<grid, 256, 0, p->stream>>>(g);
-  } else {
-    // operands that lie in the call's B are read from its FP32 copy
-    GemmArgs h = g;
-    const GradWs* w = p->grad;
-    auto in_b = [&](const double* x) { return w->B32 && x >= w->Bsrc && x < w->Bsrc + w->nB; };
-    if (!h.A32) h.A32 = in_b(g.A) ? w->B32 + (g.A - w->Bsrc) : nullptr;
-    if (!h.B32) h.B32 = in_b(g.Bm) ? w->B32 + (g.Bm - w->Bsrc) : nullptr;
-    dim3 grid((g.N + SG_T - 1) / SG_T, (g.M + SG_T - 1) / SG_T, g.nb);
-    if (h.A32 && h.B32)
-      gemm_f32_kernel<true, true><<<grid, 256, 0, p->stream>>>(h);
-    else if (h.A32)
-      gemm_f32_kernel<true, false><<<grid, 256, 0, p->stream>>>(h);
-    else if (h.B32)
-      gemm_f32_kernel<false, true><<<grid, 256, 0, p->stream>>>(h);
-    else
-      gemm_f32_kernel<false, false><<<grid, 256, 0, p->stream>>>(h);
-  }
+  dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.nb);
+  gemm_fp64_kernel<<<grid, 256, 0, p->stream>>>(g);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
@@ -423,89 +225,6 @@ __global__ void __launch_bounds__(256) ccvv_adj_kernel(const double* __restrict_
   }
 }
 
-// F1 adjoint from precomputed pair blocks (split-precision plans): the FP32
-// GEMM has formed V_k[a][j*nP + p] = v^{kj}_{a,p-nA} for the rows k of a group;
-// this kernel forms W^{kj} and the eps / s derivatives exactly as the
-// epilogue of ccvv_adj_kernel, reading x = v^{kj}_ab and y = v^{kj}_ba through
-// two 64 x 64 shared-memory tiles. Grid: (group row, j, tile pair A <= B).
-// W is written in TW: FP32 for the FP32 GEMM that consumes it (the rounding that
-// GEMM would apply when staging an FP64 W).
-template <typename TW>
-__global__ void __launch_bounds__(256) ccvv_adj_w_kernel(const double* __restrict__ V,
-                                                         const double* __restrict__ eps, double s,
-                                                         Sizes z, int k0, const int2* __restrict__ tps,
-                                                         int n_tp, int nVp, TW* __restrict__ W,
-                                                         double* __restrict__ deps,
-                                                         double* __restrict__ ds) {
-  extern __shared__ double vsm[];
-  double* tX = vsm;                 // [64][65]  V[a0 + r][j, b0 + c]
-  double* tY = vsm + GT * (GT + 1); // [64][65]  V[b0 + r][j, a0 + c]
-  __shared__ double rowacc[GT], colacc[GT];
-  __shared__ double red[8];
-  const int kl = blockIdx.x / (z.nC * n_tp);
-  const int rem = blockIdx.x % (z.nC * n_tp);
-  const int j = rem / n_tp, k = k0 + kl;
-  const int2 ab = tps[rem % n_tp];
-  const int a0 = ab.x * GT, b0 = ab.y * GT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int ve = z.nC + z.nA;
-  const long long ldv = (long long)z.nC * z.nP;
-  const double* Vk = V + (long long)kl * z.nV * ldv + (long long)j * z.nP + z.nA;
-  TW* Wk = W + (long long)kl * z.nC * nVp * nVp;
-  if (threadIdx.x < GT) {
-    rowacc[threadIdx.x] = 0.0;
-    colacc[threadIdx.x] = 0.0;
-  }
-  for (int e = threadIdx.x; e < GT * GT; e += 256) {
-    const int r = e / GT, c = e % GT;
-    tX[r * (GT + 1) + c] = (a0 + r < z.nV && b0 + c < z.nV) ? Vk[(long long)(a0 + r) * ldv + b0 + c] : 0.0;
-    tY[r * (GT + 1) + c] = (b0 + r < z.nV && a0 + c < z.nV) ? Vk[(long long)(b0 + r) * ldv + a0 + c] : 0.0;
-  }
-  __syncthreads();
-  const double E = eps[k] + eps[j];
-  const bool mirror = ab.x < ab.y;
-  const double wt = mirror ? 2.0 : 1.0;
-  double dk = 0.0, dss = 0.0;
-  double racc[4] = {0, 0, 0, 0}, cacc[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int al = ty * 4 + r, a = a0 + al;
-    if (a >= z.nV) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int bl = tx * 4 + c, b = b0 + bl;
-      if (b >= z.nV) continue;
-      const double D = E - eps[ve + a] - eps[ve + b];
-      const RegD R = rf1_d(D, s);
-      const double xv = tX[al * (GT + 1) + bl], yv = tY[bl * (GT + 1) + al];
-      Wk[((size_t)j * nVp + a) * nVp + b] = (TW)((4.0 * xv - 2.0 * yv) * R.v);
-      if (mirror) Wk[((size_t)j * nVp + b) * nVp + a] = (TW)((4.0 * yv - 2.0 * xv) * R.v);
-      const double q = fma(xv, xv - yv, yv * yv);
-      dk = fma(2.0 * wt * q, R.dD, dk);
-      dss = fma(wt * q, R.ds, dss);
-      const double gv = -2.0 * q * R.dD;
-      racc[r] += gv;
-      if (mirror) cacc[c] += gv;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) atomicAdd(&rowacc[ty * 4 + r], racc[r]);
-  if (mirror) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) atomicAdd(&colacc[tx * 4 + c], cacc[c]);
-  }
-  const double tk = block_sum<256>(dk, red);
-  const double ts = block_sum<256>(dss, red);
-  if (threadIdx.x == 0) {
-    atomicAdd(&deps[k], tk);
-    atomicAdd(ds, ts);
-  }
-  if (threadIdx.x < GT) {
-    const int a = a0 + threadIdx.x, b = b0 + threadIdx.x;
-    if (a < z.nV) atomicAdd(&deps[ve + a], rowacc[threadIdx.x]);
-    if (mirror && b < z.nV) atomicAdd(&deps[ve + b], colacc[threadIdx.x]);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // F2 adjoint: items (m, tile pair A<=B), 32 x 32 tiles; writes dX[m][u][e][f].
@@ -1096,7 +815,23 @@ __global__ void adj_p12_kernel(ActAdjArgs a) {
 }
 
 // (B1) t1/ft -> S, with the eps and s dependence of their regulators.
-__global__ void adj_t1_chain_kernel(ActAdjArgs a) {
+// Per-block accumulation of the eps / s derivatives: entries 0..n-1 of the
+// shared array are the orbitals, entry n is s. These kernels touch few distinct
+// orbitals per block (often the few active ones in every thread), and direct
+// global atomics on those addresses serialised them; the block adds in shared
+// memory and flushes one global atomic per non-zero entry.
+__device__ __forceinline__ void dacc_init(double* sh, int n) {
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) sh[k] = 0.0;
+  __syncthreads();
+}
+__device__ __forceinline__ void dacc_flush(const double* sh, int n, double* deps, double* ds) {
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    if (sh[k] != 0.0) atomicAdd(&deps[k], sh[k]);
+  if (threadIdx.x == 0 && sh[n] != 0.0) atomicAdd(ds, sh[n]);
+}
+
+__device__ __forceinline__ void adj_t1_chain_kernel_body(ActAdjArgs a, double* sacc_) {
   const AD d = adims(a.z);
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.nH2 * d.nP2) return;
@@ -1125,14 +860,21 @@ __global__ void adj_t1_chain_kernel(ActAdjArgs a) {
   const double dD = FS * (dt1 * rt.dD + dft * (-2.0 * a.s * D1 * ex));
   const double dss = FS * (dt1 * rt.ds + dft * (-D1 * D1 * ex));
   if (dD != 0.0) {
-    atomicAdd(&a.deps[I >> 1], dD);
-    atomicAdd(&a.deps[z.nC + (A >> 1)], -dD);
+    atomicAdd(&sacc_[I >> 1], dD);
+    atomicAdd(&sacc_[z.nC + (A >> 1)], -dD);
   }
-  if (dss != 0.0) atomicAdd(a.ds, dss);
+  if (dss != 0.0) atomicAdd(&sacc_[a.z.n], dss);
+}
+
+__global__ void adj_t1_chain_kernel(ActAdjArgs a) {
+  extern __shared__ double sacc_[];
+  dacc_init(sacc_, a.z.n);
+  adj_t1_chain_kernel_body(a, sacc_);
+  dacc_flush(sacc_, a.z.n, a.deps, a.ds);
 }
 
 // (B2) W1: total d(t) (direct + via Ti + via S), then through the regulators to d(V).
-__global__ void adj_w1_chain_kernel(ActAdjArgs a) {
+__device__ __forceinline__ void adj_w1_chain_kernel_body(ActAdjArgs a, double* sacc_) {
   const AD d = adims(a.z);
   const Sizes& z = a.z;
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1159,8 +901,8 @@ __global__ void adj_w1_chain_kernel(ActAdjArgs a) {
   dt = fma(dS * (eX - eU), gux, dt);
   const double T = a.W1T[k];
   if (gux != 0.0 && dS != 0.0 && T != 0.0) {
-    atomicAdd(&a.deps[z.nC + (X >> 1)], dS * gux * T);
-    atomicAdd(&a.deps[z.nC + (U >> 1)], -dS * gux * T);
+    atomicAdd(&sacc_[z.nC + (X >> 1)], dS * gux * T);
+    atomicAdd(&sacc_[z.nC + (U >> 1)], -dS * gux * T);
   }
   // regulators: T = V Rt(D) (zero if internal), Vt = V Rv(D)
   const double V = a.W1V[k];
@@ -1173,16 +915,23 @@ __global__ void adj_w1_chain_kernel(ActAdjArgs a) {
   const double dD = V * (dtt * rt.dD + dvt * rv.dD);
   const double dss = V * (dtt * rt.ds + dvt * rv.ds);
   if (dD != 0.0) {
-    atomicAdd(&a.deps[I >> 1], dD);
-    atomicAdd(&a.deps[z.nC + (U >> 1)], dD);
-    atomicAdd(&a.deps[z.nC + (A >> 1)], -dD);
-    atomicAdd(&a.deps[z.nC + (X >> 1)], -dD);
+    atomicAdd(&sacc_[I >> 1], dD);
+    atomicAdd(&sacc_[z.nC + (U >> 1)], dD);
+    atomicAdd(&sacc_[z.nC + (A >> 1)], -dD);
+    atomicAdd(&sacc_[z.nC + (X >> 1)], -dD);
   }
-  if (dss != 0.0) atomicAdd(a.ds, dss);
+  if (dss != 0.0) atomicAdd(&sacc_[a.z.n], dss);
+}
+
+__global__ void adj_w1_chain_kernel(ActAdjArgs a) {
+  extern __shared__ double sacc_[];
+  dacc_init(sacc_, a.z.n);
+  adj_w1_chain_kernel_body(a, sacc_);
+  dacc_flush(sacc_, a.z.n, a.deps, a.ds);
 }
 
 // (B3) W2 through its regulators to d(V).
-__global__ void adj_w2_chain_kernel(ActAdjArgs a) {
+__device__ __forceinline__ void adj_w2_chain_kernel_body(ActAdjArgs a, double* sacc_) {
   const AD d = adims(a.z);
   const Sizes& z = a.z;
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1201,12 +950,19 @@ __global__ void adj_w2_chain_kernel(ActAdjArgs a) {
   const double dD = V * (dt * rt.dD + dvt * rv.dD);
   const double dss = V * (dt * rt.ds + dvt * rv.ds);
   if (dD != 0.0) {
-    atomicAdd(&a.deps[I >> 1], dD);
-    atomicAdd(&a.deps[J >> 1], dD);
-    atomicAdd(&a.deps[z.nC + (X >> 1)], -dD);
-    atomicAdd(&a.deps[z.nC + (Y >> 1)], -dD);
+    atomicAdd(&sacc_[I >> 1], dD);
+    atomicAdd(&sacc_[J >> 1], dD);
+    atomicAdd(&sacc_[z.nC + (X >> 1)], -dD);
+    atomicAdd(&sacc_[z.nC + (Y >> 1)], -dD);
   }
-  if (dss != 0.0) atomicAdd(a.ds, dss);
+  if (dss != 0.0) atomicAdd(&sacc_[a.z.n], dss);
+}
+
+__global__ void adj_w2_chain_kernel(ActAdjArgs a) {
+  extern __shared__ double sacc_[];
+  dacc_init(sacc_, a.z.n);
+  adj_w2_chain_kernel_body(a, sacc_);
+  dacc_flush(sacc_, a.z.n, a.deps, a.ds);
 }
 
 // (B4) spin sums back to the spatial integrals K1, K2 (from W1) and K3 (from W2).
@@ -1250,7 +1006,7 @@ __global__ void adj_k_kernel(ActAdjArgs a) {
 
 // (B5) adjoint of P1/P2 -> dM[x][u][e][f] (one thread per virtual pair (e,f)), eps, s.
 template <int NA>
-__global__ void adj_m_kernel(ActAdjArgs a, const double* __restrict__ dP12) {
+__device__ __forceinline__ void adj_m_kernel_body(ActAdjArgs a, const double* __restrict__ dP12, double* sacc_) {
   const Sizes& z = a.z;
   const size_t nV2 = (size_t)z.nV * z.nV;
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1293,15 +1049,23 @@ __global__ void adj_m_kernel(ActAdjArgs a, const double* __restrict__ dP12) {
     a.dM[(size_t)p * nV2 + k] = dm[p];
     dsum += dDp[p];
     if (dDp[p] != 0.0) {
-      atomicAdd(&a.deps[z.nC + p / NA], dDp[p]);
-      atomicAdd(&a.deps[z.nC + p % NA], dDp[p]);
+      atomicAdd(&sacc_[z.nC + p / NA], dDp[p]);
+      atomicAdd(&sacc_[z.nC + p % NA], dDp[p]);
     }
   }
   if (dsum != 0.0) {
-    atomicAdd(&a.deps[ve + e], -dsum);
-    atomicAdd(&a.deps[ve + f], -dsum);
+    atomicAdd(&sacc_[ve + e], -dsum);
+    atomicAdd(&sacc_[ve + f], -dsum);
   }
-  if (dss != 0.0) atomicAdd(a.ds, dss);
+  if (dss != 0.0) atomicAdd(&sacc_[a.z.n], dss);
+}
+
+template <int NA>
+__global__ void adj_m_kernel(ActAdjArgs a, const double* __restrict__ dP12) {
+  extern __shared__ double sacc_[];
+  dacc_init(sacc_, a.z.n);
+  adj_m_kernel_body<NA>(a, dP12, sacc_);
+  dacc_flush(sacc_, a.z.n, a.deps, a.ds);
 }
 
 // (B6) dK1, dK2, dK3 -> dB (gather, one thread per dB element; adds).
@@ -1352,7 +1116,7 @@ __global__ void adj_k_to_b_kernel(ActAdjArgs a, const double* __restrict__ B, do
 namespace dsrg {
 
 // Generic-nA fallback of adj_m_kernel for active spaces above 4 orbitals.
-__global__ void adj_m_generic_kernel(ActAdjArgs a, const double* __restrict__ dP12) {
+__device__ __forceinline__ void adj_m_generic_kernel_body(ActAdjArgs a, const double* __restrict__ dP12, double* sacc_) {
   const Sizes& z = a.z;
   const int NA = z.nA, NA2 = NA * NA, NA4 = NA2 * NA2;
   const size_t nV2 = (size_t)z.nV * z.nV;
@@ -1391,24 +1155,31 @@ __global__ void adj_m_generic_kernel(ActAdjArgs a, const double* __restrict__ dP
         dm += d2 * mq * rvq.v * rtpt.v;
         const double dR2 = d2 * mq * mp;
         if (dR2 != 0.0) {
-          atomicAdd(&a.deps[z.nC + pt / NA], dR2 * rvq.v * rtpt.dD);
-          atomicAdd(&a.deps[z.nC + pt % NA], dR2 * rvq.v * rtpt.dD);
+          atomicAdd(&sacc_[z.nC + pt / NA], dR2 * rvq.v * rtpt.dD);
+          atomicAdd(&sacc_[z.nC + pt % NA], dR2 * rvq.v * rtpt.dD);
           dsum += dR2 * rvq.v * rtpt.dD;
         }
       }
     }
     a.dM[(size_t)p * nV2 + k] = dm;
     if (dDp != 0.0) {
-      atomicAdd(&a.deps[z.nC + p / NA], dDp);
-      atomicAdd(&a.deps[z.nC + p % NA], dDp);
+      atomicAdd(&sacc_[z.nC + p / NA], dDp);
+      atomicAdd(&sacc_[z.nC + p % NA], dDp);
     }
     dsum += dDp;
   }
   if (dsum != 0.0) {
-    atomicAdd(&a.deps[ve + e], -dsum);
-    atomicAdd(&a.deps[ve + f], -dsum);
+    atomicAdd(&sacc_[ve + e], -dsum);
+    atomicAdd(&sacc_[ve + f], -dsum);
   }
-  if (dss != 0.0) atomicAdd(a.ds, dss);
+  if (dss != 0.0) atomicAdd(&sacc_[a.z.n], dss);
+}
+
+__global__ void adj_m_generic_kernel(ActAdjArgs a, const double* __restrict__ dP12) {
+  extern __shared__ double sacc_[];
+  dacc_init(sacc_, a.z.n);
+  adj_m_generic_kernel_body(a, dP12, sacc_);
+  dacc_flush(sacc_, a.z.n, a.deps, a.ds);
 }
 
 
@@ -1417,16 +1188,18 @@ bool grad_alloc(dsrg_plan* p) {
   GradWs* g = new GradWs();
   p->grad = g;
   g->nVp = (z.nV + GT - 1) / GT * GT;
-  // as many rows as fit in 2 GiB of W (plus the pair blocks V of split plans; at least one)
-  const bool split = p->prec != DSRG_PREC_FP64;
-  const size_t per_w = (size_t)z.nC * g->nVp * g->nVp * 8;
-  const size_t per_v = split ? (size_t)z.nV * z.nC * z.nP * 8 : 0;
-  const size_t kmax = ((size_t)2 << 30) / (per_w + per_v);
-  g->kgroup = (int)(kmax < 1 ? 1 : (kmax > (size_t)z.nC ? (size_t)z.nC : kmax));
-  bool ok = plan_alloc(p, (void**)&g->Wk, per_w * g->kgroup);
-  if (ok && split) ok = plan_alloc(p, (void**)&g->V, per_v * g->kgroup);
   g->nB = (size_t)z.Q * z.nH * z.nP;
-  if (ok && split) ok = plan_alloc(p, (void**)&g->B32, g->nB * sizeof(float));
+  bool ok = true;
+  if (p->prec == DSRG_PREC_FP64) {
+    // as many rows as fit in 2 GiB of W (at least one)
+    const size_t per_w = (size_t)z.nC * g->nVp * g->nVp * 8;
+    const size_t kmax = ((size_t)2 << 30) / per_w;
+    g->kgroup = (int)(kmax < 1 ? 1 : (kmax > (size_t)z.nC ? (size_t)z.nC : kmax));
+    ok = plan_alloc(p, (void**)&g->Wk, per_w * g->kgroup);
+  } else {
+    // split plans: S and B^T planes of the tensor-core assembly (tc_adjoint.cu)
+    ok = tc_adj_alloc(p);
+  }
   if (z.nA > 0) {
     const size_t w1n = p->act.w1n, w2n = p->act.w2n;
     const size_t nHP2 = (size_t)4 * z.nH * z.nP;
@@ -1449,6 +1222,7 @@ bool grad_alloc(dsrg_plan* p) {
 void grad_free(dsrg_plan* p) {
   delete p->grad;
   p->grad = nullptr;
+  tc_adj_free(p);
 }
 
 GemmArgs mk(int M, int N, int L1, int L2, const double* A, long long ai, long long a1,
@@ -1485,9 +1259,9 @@ static size_t ccav_adj_smem(const Sizes& z) {
 // Term A with no active orbitals (f^(1) singles): E = 2 sum_{m,e} f^2 (1 + g) Rt,
 // g = exp(-s D^2), D = e_m - e_e; its eps and s derivatives (f^(1) is an input
 // of its own, B does not enter).
-__global__ void singles_adj_kernel(const double* __restrict__ eps, double s, Sizes z,
+__device__ __forceinline__ void singles_adj_kernel_body(const double* __restrict__ eps, double s, Sizes z,
                                    const double* __restrict__ f1, double* __restrict__ deps,
-                                   double* __restrict__ ds) {
+                                   double* __restrict__ ds, double* sacc_) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= z.nC * z.nP) return;
   const int m = k / z.nP, e = k % z.nP;
@@ -1499,10 +1273,19 @@ __global__ void singles_adj_kernel(const double* __restrict__ eps, double s, Siz
   const double dD = w * ((-2.0 * s * D * g) * rt.v + (1.0 + g) * rt.dD);
   const double dss = w * ((-D * D * g) * rt.v + (1.0 + g) * rt.ds);
   if (dD != 0.0) {
-    atomicAdd(&deps[m], dD);
-    atomicAdd(&deps[z.nC + e], -dD);
+    atomicAdd(&sacc_[m], dD);
+    atomicAdd(&sacc_[z.nC + e], -dD);
   }
-  if (dss != 0.0) atomicAdd(ds, dss);
+  if (dss != 0.0) atomicAdd(&sacc_[z.n], dss);
+}
+
+__global__ void singles_adj_kernel(const double* __restrict__ eps, double s, Sizes z,
+                                   const double* __restrict__ f1, double* __restrict__ deps,
+                                   double* __restrict__ ds) {
+  extern __shared__ double sacc_[];
+  dacc_init(sacc_, z.n);
+  singles_adj_kernel_body(eps, s, z, f1, deps, ds, sacc_);
+  dacc_flush(sacc_, z.n, deps, ds);
 }
 
 cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const double* G,
@@ -1514,59 +1297,49 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
   cudaStream_t st = p->stream;
   cudaError_t e;
   const long long HP = (long long)z.nH * z.nP;
-  if ((e = cudaMemsetAsync(dB, 0, (size_t)z.Q * HP * 8, st)) != cudaSuccess) return e;
+  // FP64 plans: FP64 adjoints and GEMMs. Split plans: the adjoints of the
+  // integrals, then one tensor-core GEMM of their symmetric matrix S with B^T
+  // (tc_adjoint.cu), which writes every element of dB.
+  const bool fp64 = p->prec == DSRG_PREC_FP64;
+  if (fp64 && (e = cudaMemsetAsync(dB, 0, (size_t)z.Q * HP * 8, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(deps, 0, (size_t)z.n * 8, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ds, 0, 8, st)) != cudaSuccess) return e;
-
-  // FP64 plans recompute in FP64, split-precision plans in FP32 (round to nearest)
-  const bool fp64 = p->prec == DSRG_PREC_FP64;
   if (!fp64) {
-    // fl32(B) once, for every GEMM that reads B (the same rounding as at staging)
-    w->Bsrc = B;
-    to_f32_kernel<<<(unsigned)((w->nB + 255) / 256), 256, 0, st>>>(B, w->B32, w->nB);
-    DSRG_LAUNCH_CHECK(p);
+    // ---- F1: the core x core block of S and the eps / s derivatives (this rank's pairs)
+    if ((e = tc_adj_ccvv(p, B, eps, s, deps, ds)) != cudaSuccess) return e;
+    if (p->shard_rank != 0 || z.nA == 0) {
+      if (p->shard_rank == 0 && F1) {
+        const int n = z.nC * z.nP;
+        singles_adj_kernel<<<(n + 255) / 256, 256, ((size_t)z.n + 1) * 8, st>>>(eps, s, z, F1, deps, ds);
+        DSRG_LAUNCH_CHECK(p);
+      }
+      return tc_adj_assemble(p, B, dB);
+    }
   }
-  // ---- F1: per core row k, W^{kj} then dB[:, k, V] += 2 sum_j B_j W^{kj T}
+  // ---- F1 (FP64 plans): per core row k, W^{kj} then dB[:, k, V] += 2 sum_j B_j W^{kj T}
   const int n_tp = p->n_tp_ccvv;  // 64-wide tile pairs of the FP64 work list
   // rows k in groups of w->kgroup: W^{kj} of the group, then one batched GEMM
   const long long nVp = w->nVp, wstride = (long long)z.nC * nVp * nVp;
-  for (int k0 = 0, grp = 0; k0 < z.nC; k0 += w->kgroup, ++grp) {
+  for (int k0 = 0, grp = 0; fp64 && k0 < z.nC; k0 += w->kgroup, ++grp) {
     const int kg = (z.nC - k0) < w->kgroup ? (z.nC - k0) : w->kgroup;
     // multi-GPU share: groups of core rows dealt round-robin (their dB rows are disjoint)
     if (!pair_in_shard(grp, p->shard_rank, p->shard_world)) continue;
-    if (fp64) {
-      for (int k = k0; k < k0 + kg; ++k) {
-        ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
-                                                             w->nVp, w->Wk + (k - k0) * wstride,
-                                                             deps, ds);
-        DSRG_LAUNCH_CHECK(p);
-      }
-    } else {
-      // V_k[a][(j,p)] = sum_Q B[Q,k,a] B[Q,j,p] for the group (FP32 GEMM), then W
-      const long long ldv = (long long)z.nC * z.nP;
-      GemmArgs gv = batched(mk(z.nV, (int)ldv, z.Q, 1, B + (long long)k0 * z.nP + z.nA, 1, HP, 0, B,
-                               HP, 0, 1, w->V, ldv, 1, 1.0),
-                            kg, z.nP, 0, (long long)z.nV * ldv);
-      gv.accumulate = 0;
-      if ((e = gemm(p, gv)) != cudaSuccess) return e;
-      const size_t smw = (size_t)2 * GT * (GT + 1) * 8;
-      // W in FP32 (the Wk buffer holds it at the same element offsets)
-      raise_smem_limit((const void*)ccvv_adj_w_kernel<float>, smw);
-      ccvv_adj_w_kernel<float><<<kg * z.nC * n_tp, 256, smw, st>>>(
-          w->V, eps, s, z, k0, p->d_tp_ccvv, n_tp, w->nVp, (float*)w->Wk, deps, ds);
+    for (int k = k0; k < k0 + kg; ++k) {
+      ccvv_adj_kernel<double><<<z.nC * n_tp, 256, 0, st>>>(B, eps, s, z, k, p->d_tp_ccvv, n_tp,
+                                                           w->nVp, w->Wk + (k - k0) * wstride,
+                                                           deps, ds);
       DSRG_LAUNCH_CHECK(p);
     }
     GemmArgs gw = batched(mk(z.Q, z.nV, z.nC, z.nV, B + z.nA, HP, z.nP, 1, w->Wk, nVp * nVp, 1, nVp,
                              dB + (long long)k0 * z.nP + z.nA, HP, 1, 2.0),
                           kg, 0, wstride, z.nP);
-    if (!fp64) gw.B32 = (const float*)w->Wk;
     if ((e = gemm(p, gw)) != cudaSuccess) return e;
   }
   if (p->shard_rank != 0) return cudaSuccess;  // the other blocks' adjoints: rank 0
   if (z.nA == 0) {
     if (F1) {
       const int n = z.nC * z.nP;
-      singles_adj_kernel<<<(n + 255) / 256, 256, 0, st>>>(eps, s, z, F1, deps, ds);
+      singles_adj_kernel<<<(n + 255) / 256, 256, ((size_t)z.n + 1) * 8, st>>>(eps, s, z, F1, deps, ds);
       DSRG_LAUNCH_CHECK(p);
     }
     return cudaSuccess;
@@ -1584,12 +1357,19 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
       cavv_adj_kernel<NA_, float><<<z.nC * p->n_tp_cavv, 256, 0, st>>>(                          \
           B, eps, G, s, z, p->d_tp_cavv, p->n_tp_cavv, z.nV, w->dX, deps, ds);                   \
     break;
-    switch (z.nA) {
-      CAVV_ADJ(1) CAVV_ADJ(2) CAVV_ADJ(3) CAVV_ADJ(4) CAVV_ADJ(5) CAVV_ADJ(6) CAVV_ADJ(7) CAVV_ADJ(8)
-      default: return cudaErrorInvalidValue;
+    if (!fp64 && p->rest_tc) {
+      // X from the energy call's tensor-core GEMM output
+      if ((e = launch_split_cavv_adjoint(p, eps, G, s, w->dX, deps, ds)) != cudaSuccess) return e;
+    } else {
+      switch (z.nA) {
+        CAVV_ADJ(1) CAVV_ADJ(2) CAVV_ADJ(3) CAVV_ADJ(4) CAVV_ADJ(5) CAVV_ADJ(6) CAVV_ADJ(7) CAVV_ADJ(8)
+        default: return cudaErrorInvalidValue;
+      }
+      DSRG_LAUNCH_CHECK(p);
     }
 #undef CAVV_ADJ
-    DSRG_LAUNCH_CHECK(p);
+  }
+  if (fp64) {
     e = gemm(p, batched(mk(z.Q, z.nV, z.nA, z.nV, B + (long long)z.nC * z.nP + z.nA, HP, z.nP, 1,
                            w->dX, nV2, 1, nV, dB + z.nA, HP, 1, 1.0),
                         z.nC, 0, (long long)z.nA * nV2, z.nP));
@@ -1611,6 +1391,8 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
       ccav_adj_kernel<float><<<z.nV, 256, sm, st>>>(B, eps, G, s, z, w->dZ, deps, ds);
     }
     DSRG_LAUNCH_CHECK(p);
+  }
+  if (fp64) {
     const long long nCV = (long long)z.nC * nV, nCCV = (long long)z.nC * nCV;
     e = gemm(p, batched(mk(z.Q, z.nV, z.nC, z.nA, B, HP, z.nP, 1, w->dZ, nV, nCCV, 1, dB + z.nA, HP,
                            1, 1.0),
@@ -1644,6 +1426,7 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     const int nHP2 = 4 * z.nH * z.nP;
     const int nA4 = z.nA * z.nA * z.nA * z.nA;
     auto blocks = [](size_t n) { return (unsigned)((n + 255) / 256); };
+    const size_t dsm = ((size_t)z.n + 1) * 8;  // block sums of deps and ds
     adj_w1_terms_kernel<<<blocks(A.w1n), 256, 0, st>>>(a);
     DSRG_LAUNCH_CHECK(p);
     adj_w2_terms_kernel<<<blocks(A.w2n), 256, 0, st>>>(a);
@@ -1652,11 +1435,11 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
     DSRG_LAUNCH_CHECK(p);
     adj_p12_kernel<<<blocks(nA4), 256, 0, st>>>(a);
     DSRG_LAUNCH_CHECK(p);
-    adj_t1_chain_kernel<<<blocks(nHP2), 256, 0, st>>>(a);
+    adj_t1_chain_kernel<<<blocks(nHP2), 256, dsm, st>>>(a);
     DSRG_LAUNCH_CHECK(p);
-    adj_w1_chain_kernel<<<blocks(A.w1n), 256, 0, st>>>(a);
+    adj_w1_chain_kernel<<<blocks(A.w1n), 256, dsm, st>>>(a);
     DSRG_LAUNCH_CHECK(p);
-    adj_w2_chain_kernel<<<blocks(A.w2n), 256, 0, st>>>(a);
+    adj_w2_chain_kernel<<<blocks(A.w2n), 256, dsm, st>>>(a);
     DSRG_LAUNCH_CHECK(p);
     {
       const size_t n = 2 * (size_t)z.nH * z.nA * z.nA * z.nP + (size_t)z.nH * z.nA * z.nH * z.nA;
@@ -1664,13 +1447,18 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
       DSRG_LAUNCH_CHECK(p);
     }
     switch (z.nA) {
-      case 1: adj_m_kernel<1><<<blocks(nV2), 256, 0, st>>>(a, w->dP12); break;
-      case 2: adj_m_kernel<2><<<blocks(nV2), 256, 0, st>>>(a, w->dP12); break;
-      case 3: adj_m_kernel<3><<<blocks(nV2), 256, 0, st>>>(a, w->dP12); break;
-      case 4: adj_m_kernel<4><<<blocks(nV2), 256, 0, st>>>(a, w->dP12); break;
-      default: adj_m_generic_kernel<<<blocks(nV2), 256, 0, st>>>(a, w->dP12); break;
+      case 1: adj_m_kernel<1><<<blocks(nV2), 256, dsm, st>>>(a, w->dP12); break;
+      case 2: adj_m_kernel<2><<<blocks(nV2), 256, dsm, st>>>(a, w->dP12); break;
+      case 3: adj_m_kernel<3><<<blocks(nV2), 256, dsm, st>>>(a, w->dP12); break;
+      case 4: adj_m_kernel<4><<<blocks(nV2), 256, dsm, st>>>(a, w->dP12); break;
+      default: adj_m_generic_kernel<<<blocks(nV2), 256, dsm, st>>>(a, w->dP12); break;
     }
     DSRG_LAUNCH_CHECK(p);
+    if (!fp64) {
+      // every adjoint of an integral is formed: S outside the core block, then dB
+      if ((e = tc_adj_rest(p, w->dX, w->dZ, w->dM, w->dK1, w->dK2, w->dK3)) != cudaSuccess) return e;
+      return tc_adj_assemble(p, B, dB);
+    }
     adj_k_to_b_kernel<<<blocks((size_t)z.Q * HP), 256, 0, st>>>(a, B, dB);
     DSRG_LAUNCH_CHECK(p);
     const long long CP = (long long)z.nC * z.nP;

@@ -56,6 +56,7 @@ struct ActiveWs {
 struct SplitWs;    // tensor-core path workspace (tc_split.cu)
 struct RestState;  // tensor-core CAVV / CCAV / active integrals (tc_rest.cu)
 struct GradWs;   // gradient workspace (grad.cu)
+struct TcAdjWs;  // tensor-core assembly of dE/dB for split plans (tc_adjoint.cu)
 
 }  // namespace dsrg
 
@@ -96,6 +97,7 @@ struct dsrg_plan {
   dsrg::SplitWs* split = nullptr;
   dsrg::RestState* rest = nullptr;  // split CAVV / CCAV / active integrals (tc_rest.cu)
   dsrg::GradWs* grad = nullptr;  // gradient workspace (DSRG_PLAN_GRAD)
+  dsrg::TcAdjWs* tcadj = nullptr;  // split plans' S and B^T planes of the gradient
   bool rest_tc = false;        // CAVV, CCAV and the active integrals from the tensor-core GEMM
 
   // device staging of dsrg_mrpt2_energy_host (DSRG_PLAN_HOST_IO)
@@ -254,6 +256,25 @@ cudaError_t launch_grad(dsrg_plan* p, const double* B, const double* eps, const 
                         const double* L, const double* L3, const double* F1, double s, double* dB,
                         double* deps, double* ds);
 
+// Tensor-core assembly of dE/dB for split plans (tc_adjoint.cu): S is the
+// symmetric matrix of the adjoints of every integral (r|c) over the plane rows;
+// dB = S . B^T. tc_adj_ccvv forms its core x core block (and adds to deps, ds),
+// tc_adj_rest the rest from the adjoints dX, dZ, dM, dK1, dK2, dK3,
+// tc_adj_assemble writes every element of dB.
+bool tc_adj_alloc(dsrg_plan* p);
+void tc_adj_free(dsrg_plan* p);
+cudaError_t tc_adj_clear(dsrg_plan* p);
+cudaError_t tc_adj_ccvv(dsrg_plan* p, const double* B, const double* eps, double s, double* deps,
+                        double* ds);
+cudaError_t tc_adj_rest(dsrg_plan* p, const double* dX, const double* dZ, const double* dM,
+                        const double* dK1, const double* dK2, const double* dK3);
+cudaError_t tc_adj_assemble(dsrg_plan* p, const double* B, double* dB);
+// The CCVV kernel's adjoint epilogue (tc_split.cu), TF32x3 recompute.
+bool split_adj_alloc(dsrg_plan* p);
+cudaError_t split_launch_ccvv_adjoint(dsrg_plan* p, const double* B, const double* eps, double s,
+                                      uint16_t* s_hi, uint16_t* s_lo, long long lds, double* deps,
+                                      double* ds);
+
 // Split-path CAVV, CCAV and active-block integrals (tc_rest.cu); needs the
 // planes staged by the CCVV launch of the same call.
 int rest_xrows(const Sizes& z);
@@ -273,6 +294,10 @@ size_t split_tail_bytes(const Sizes& z);
 void rest_act_tables(const dsrg_plan* p, const double** alpha, const double** pinfo,
                      const double** tau, int* ld);
 int split_qld(const dsrg_plan* p);
+// Adjoint of F2 from the energy call's GEMM output and factor tables (split
+// plans with the tensor-core rest): dX [nC][nA][nV][nV], adds to deps, ds.
+cudaError_t launch_split_cavv_adjoint(dsrg_plan* p, const double* eps, const double* G, double s,
+                                      double* dX, double* deps, double* ds);
 
 }  // namespace dsrg
 

@@ -19,6 +19,47 @@ __device__ __forceinline__ double reg_f1(double D, double s) {
   return D == 0.0 ? 0.0 : -expm1(-2.0 * s * D * D) / D;
 }
 
+// ---------------------------------------------------------------------------
+// Regulator values and derivatives. x = s D^2.
+//   Rt = (1 - e^{-x})/D, dRt/dD = (2 x e^{-x} + expm1(-x))/D^2, dRt/ds = D e^{-x}
+//   Rv = 1 + e^{-x},     dRv/dD = -2 s D e^{-x},              dRv/ds = -D^2 e^{-x}
+// For x < 1e-4 the Maclaurin series of Sec. II.B is used:
+//   Rt = s D (1 - x/2 + x^2/6), dRt/dD = s (1 - 3x/2 + 5x^2/6).
+// The F1 regulator is Rt with s -> 2s (and dR/ds doubles).
+// ---------------------------------------------------------------------------
+struct RegD {
+  double v, dD, ds;
+};
+
+__device__ __forceinline__ RegD rt_d(double D, double s) {
+  const double x = s * D * D;
+  const double g = exp(-x);
+  RegD r;
+  if (x < 1e-4) {
+    r.v = s * D * (1.0 - 0.5 * x + x * x / 6.0);
+    r.dD = s * (1.0 - 1.5 * x + 5.0 / 6.0 * x * x);
+  } else {
+    // for x > 1/2, e^{-x} < 0.61 and e^{-x} - 1 has no cancellation: one exponential
+    const double em = x > 0.5 ? g - 1.0 : expm1(-x);
+    const double inv = 1.0 / D;
+    r.v = -em * inv;
+    r.dD = (2.0 * x * g + em) * inv * inv;
+  }
+  r.ds = D * g;
+  return r;
+}
+
+__device__ __forceinline__ RegD rv_d(double D, double s) {
+  const double g = exp(-s * D * D);
+  return RegD{1.0 + g, -2.0 * s * D * g, -D * D * g};
+}
+
+__device__ __forceinline__ RegD rf1_d(double D, double s) {
+  RegD r = rt_d(D, 2.0 * s);
+  r.ds *= 2.0;
+  return r;
+}
+
 // Sum of one double per thread over a CTA of NT threads, in a fixed order
 // (warp butterfly, then the warp sums in index order by warp 0). The result
 // is valid in thread 0. `sh` needs NT/32 doubles.

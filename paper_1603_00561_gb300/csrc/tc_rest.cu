@@ -544,6 +544,192 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of F2 for the gradient of split plans: X_u from the GEMM output Y of
+// the energy call just made (its error, about 1e-8 relative, is far below the
+// gradient's), regulators from the same factor tables. Per position (e, f)
+// (and its mirror (f, e) for E < F), with P_v = 2 X_v[e,f] - X_v[f,e]:
+//   dE/dX_u[e,f] = Rv_u s1_u + Rt_u s2_u,
+//   s1_u = sum_v G_uv Rt_v P_v,  s2_u = sum_v G_vu Rv_v P_v,
+// and the derivative of the summand with respect to D_u,
+//   X_u Rv_u' s1_u + (sum_w G_wu Rv_w X_w) P_u Rt_u',
+// goes to e_m and e_u (+) and to e_e, e_f (-); the s derivative likewise.
+// ---------------------------------------------------------------------------
+template <int NA>
+__global__ void __launch_bounds__(256) cavv_adj_tc_kernel(
+    const float* __restrict__ Y, long long ldy, int nVpad, const double* __restrict__ eps,
+    const double* __restrict__ G, double s, Sizes z, const int2* __restrict__ tps, int n_tp,
+    const double* __restrict__ alpha, const double* __restrict__ pinfo,
+    const double* __restrict__ tau1, double* __restrict__ dX, double* __restrict__ deps,
+    double* __restrict__ ds) {
+  extern __shared__ float f2s[];
+  float* sX = f2s;                              // [NA][32][33]   X_u[e,f]
+  float* sXt = sX + NA * F2_T * (F2_T + 1);     // [NA][32][33]   X_u[f,e]
+  __shared__ double sBAe[NA][F2_T], sAf[NA][F2_T], sEe[F2_T], sEf[F2_T], sG[NA * NA];
+  __shared__ double sE[NA];
+  __shared__ int sFact, sFar;
+  __shared__ double rowacc[F2_T], colacc[F2_T], uacc[NA];
+  __shared__ double red[8];
+  const int m = blockIdx.x / n_tp;
+  const int2 ab = tps[blockIdx.x % n_tp];
+  const int E0 = ab.x * F2_T, F0 = ab.y * F2_T;
+  const int ve = z.nC + z.nA;
+  const float* Ym = Y + (size_t)m * nVpad * ldy;
+  for (int k = threadIdx.x; k < NA * F2_T * F2_T; k += 256) {
+    const int u = k / (F2_T * F2_T), r = (k / F2_T) % F2_T, c = k % F2_T;
+    sX[(u * F2_T + r) * (F2_T + 1) + c] = Ym[(size_t)(E0 + r) * ldy + u * nVpad + F0 + c];
+    sXt[(u * F2_T + c) * (F2_T + 1) + r] = Ym[(size_t)(F0 + r) * ldy + u * nVpad + E0 + c];
+  }
+  if (threadIdx.x < F2_T) {
+    const int t = threadIdx.x;
+    const int e = E0 + t, f = F0 + t;
+    sEe[t] = e < z.nV ? eps[ve + e] : 0.0;
+    sEf[t] = f < z.nV ? eps[ve + f] : 0.0;
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+      const double* al = alpha + (size_t)(m * z.nA + u) * nVpad;
+      sBAe[u][t] = pinfo[4 * (m * z.nA + u) + 1] * al[E0 + t];
+      sAf[u][t] = al[F0 + t];
+    }
+    rowacc[t] = 0.0;
+    colacc[t] = 0.0;
+  }
+  if (threadIdx.x < NA * NA) sG[threadIdx.x] = G[threadIdx.x];
+  if (threadIdx.x < NA) uacc[threadIdx.x] = 0.0;
+  if (threadIdx.x == 0) {
+    int fact = 1;
+    for (int u = 0; u < NA; ++u) {
+      sE[u] = pinfo[4 * (m * z.nA + u)];
+      fact = fact && (pinfo[4 * (m * z.nA + u) + 2] != 0.0);
+    }
+    sFact = fact;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every D_u of the tile pair so far from 0 that exp(-s D_u^2) < 2^-63
+    double elo = 1e300, flo = 1e300, ehi = -1e300, fhi = -1e300;
+    for (int t = 0; t < F2_T; ++t) {
+      if (E0 + t < z.nV) elo = fmin(elo, sEe[t]), ehi = fmax(ehi, sEe[t]);
+      if (F0 + t < z.nV) flo = fmin(flo, sEf[t]), fhi = fmax(fhi, sEf[t]);
+    }
+    int far = 1;
+    for (int u = 0; u < NA; ++u) {
+      const double dhi = sE[u] - elo - flo, dlo = sE[u] - ehi - fhi;
+      const double dn = dhi <= 0.0 ? dhi : (dlo >= 0.0 ? dlo : 0.0);
+      far = far && (dhi <= -0.25 || dlo >= 0.25) && s * dn * dn > 44.0;
+    }
+    sFar = far;
+  }
+  __syncthreads();
+  const bool mirror = ab.x < ab.y;
+  const bool fact = sFact != 0;
+  const bool tile_far = sFar != 0;
+  const int c = threadIdx.x & 31;
+  const int f = F0 + c;
+  double dm = 0.0, dss = 0.0, cacc = 0.0;
+  double du[NA];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) du[u] = 0.0;
+  if (f < z.nV) {
+    for (int r = threadIdx.x >> 5; r < F2_T; r += 8) {
+      const int e = E0 + r;
+      if (e >= z.nV) break;
+      const double tau = (fact && !tile_far) ? tau1[(size_t)e * nVpad + f] : 0.0;
+      const double eef = sEe[r] + sEf[c];
+      RegD Rv[NA], Rt[NA];
+      double X[NA], Xt[NA], Dd[NA];
+      bool far = fact;
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        X[u] = sX[(u * F2_T + r) * (F2_T + 1) + c];
+        Xt[u] = sXt[(u * F2_T + r) * (F2_T + 1) + c];
+        Dd[u] = sE[u] - eef;
+        far = far && fabs(Dd[u]) >= 0.25;
+      }
+      if (far || tile_far) {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const double D = Dd[u];
+          const double g = tile_far ? 0.0 : sBAe[u][r] * sAf[u][c] * tau;
+          float r0f;
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)D));
+          const double r0 = (double)r0f;
+          const double en = fma(-D, r0, 1.0);
+          const double inv = fma(r0, en, r0);
+          const double R0 = fma(-g, r0, r0);
+          const double x = s * D * D;
+          Rt[u].v = fma(R0, en, R0);                        // (1 - g) / D
+          Rt[u].dD = fma(2.0 * x, g, g - 1.0) * inv * inv;  // (2 x g + e^{-x} - 1) / D^2
+          Rt[u].ds = D * g;
+          Rv[u].v = 1.0 + g;
+          Rv[u].dD = -2.0 * s * D * g;
+          Rv[u].ds = -D * D * g;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          Rt[u] = rt_d(Dd[u], s);
+          Rv[u] = rv_d(Dd[u], s);
+        }
+      }
+      double P[NA], Pt[NA];
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        P[u] = 2.0 * X[u] - Xt[u];
+        Pt[u] = 2.0 * Xt[u] - X[u];
+      }
+      double gsum = 0.0;
+#pragma unroll
+      for (int u = 0; u < NA; ++u) {
+        double s1 = 0.0, s2 = 0.0, s1t = 0.0, s2t = 0.0, cw = 0.0, cwt = 0.0;
+#pragma unroll
+        for (int v = 0; v < NA; ++v) {
+          const double gt = sG[u * NA + v] * Rt[v].v, gv = sG[v * NA + u] * Rv[v].v;
+          s1 = fma(gt, P[v], s1);
+          s2 = fma(gv, P[v], s2);
+          s1t = fma(gt, Pt[v], s1t);
+          s2t = fma(gv, Pt[v], s2t);
+          cw = fma(gv, X[v], cw);
+          cwt = fma(gv, Xt[v], cwt);
+        }
+        dX[(((size_t)m * NA + u) * z.nV + e) * z.nV + f] = Rv[u].v * s1 + Rt[u].v * s2;
+        if (mirror) dX[(((size_t)m * NA + u) * z.nV + f) * z.nV + e] = Rv[u].v * s1t + Rt[u].v * s2t;
+        double gD = X[u] * Rv[u].dD * s1 + cw * P[u] * Rt[u].dD;
+        double gs = X[u] * Rv[u].ds * s1 + cw * P[u] * Rt[u].ds;
+        if (mirror) {
+          gD += Xt[u] * Rv[u].dD * s1t + cwt * Pt[u] * Rt[u].dD;
+          gs += Xt[u] * Rv[u].ds * s1t + cwt * Pt[u] * Rt[u].ds;
+        }
+        du[u] += gD;
+        gsum += gD;
+        dss += gs;
+      }
+      dm += gsum;
+      atomicAdd(&rowacc[r], -gsum);
+      cacc -= gsum;
+    }
+  }
+  atomicAdd(&colacc[c], cacc);
+  const double tm = block_sum<256>(dm, red);
+  const double ts = block_sum<256>(dss, red);
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const double t = block_sum<256>(du[u], red);
+    if (threadIdx.x == 0) uacc[u] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&deps[m], tm);
+    atomicAdd(ds, ts);
+    for (int u = 0; u < NA; ++u) atomicAdd(&deps[z.nC + u], uacc[u]);
+  }
+  if (threadIdx.x < F2_T) {
+    const int e = E0 + threadIdx.x, ff = F0 + threadIdx.x;
+    if (e < z.nV) atomicAdd(&deps[ve + e], rowacc[threadIdx.x]);
+    if (ff < z.nV) atomicAdd(&deps[ve + ff], colacc[threadIdx.x]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // F3 (CCAV), spin-adapted:
 //   F3 = sum_{u,v} Hh_uv sum_{m,n,e} Z_v[m,n,e] (2 Z_u[m,n,e] - Z_u[n,m,e])
 //        (1 + exp(-s D_v^2)) (1 - exp(-s D_u^2))/D_u,
@@ -845,6 +1031,32 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
         st->Y, st->ldy, st->nVpad, st->xc, st->Gxx, z, p->act.K1, p->act.K2, p->act.K3, p->act.M);
     DSRG_LAUNCH_CHECK(p);
   }
+  return cudaSuccess;
+}
+
+// Adjoint of F2 for split plans (the gradient), after the energy call on the
+// same stream: writes dX [nC][nA][nV][nV] and adds to deps, ds.
+cudaError_t launch_split_cavv_adjoint(dsrg_plan* p, const double* eps, const double* G, double s,
+                                      double* dX, double* deps, double* ds) {
+  RestState* st = p->rest;
+  const Sizes& z = p->z;
+  const size_t sm = f2_smem_bytes(z.nA);
+  const unsigned grid = (unsigned)(z.nC * st->n_tp);
+  if (grid == 0) return cudaSuccess;
+#define F2A_LAUNCH(NA_)                                                                     \
+  case NA_:                                                                                 \
+    raise_smem_limit((const void*)cavv_adj_tc_kernel<NA_>, sm);                             \
+    cavv_adj_tc_kernel<NA_><<<grid, 256, sm, p->stream>>>(st->Y, st->ldy, st->nVpad, eps, G, s, z, \
+                                                        st->d_tp, st->n_tp, st->alpha,      \
+                                                        st->pinfo, st->tau1, dX, deps, ds); \
+    break;
+  switch (z.nA) {
+    F2A_LAUNCH(1) F2A_LAUNCH(2) F2A_LAUNCH(3) F2A_LAUNCH(4)
+    F2A_LAUNCH(5) F2A_LAUNCH(6) F2A_LAUNCH(7) F2A_LAUNCH(8)
+    default: return cudaErrorInvalidValue;
+  }
+#undef F2A_LAUNCH
+  DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
 

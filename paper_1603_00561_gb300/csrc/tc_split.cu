@@ -80,6 +80,13 @@ struct SplitWs {
     int* d_begin = nullptr;
   };
   std::vector<Group> groups;
+  // The adjoint's recompute of x and y (TF32x3 whatever the plan's precision;
+  // for BF16 plans TF32 planes of the core rows of its own): maps and descriptor
+  bool adj_ready = false;
+  void* adj_hi = nullptr;
+  void* adj_lo = nullptr;
+  CcvvMaps adj_maps;
+  void* d_mol_adj = nullptr;
 };
 
 // One molecule of a (possibly batched) CCVV launch.
@@ -107,6 +114,13 @@ struct SplitArgs {
   int* status;
   unsigned long long* counts;  // epilogue branch counters (DSRG_COUNT_CCVV_*)
   int prefetch;  // K stages ahead to prefetch into L2 (0: off)
+  // adjoint launches only: the core x virtual block of S = 2 dE/dv (BF16 hi
+  // and lo planes, row pitch lds elements) and the eps / s derivatives
+  uint16_t* s_hi;
+  uint16_t* s_lo;
+  long long lds;
+  double* deps;
+  double* ds;
 };
 
 // Operand slots of one stage: 0 = rows (i, A), 1 = (j, B), 2 = (j, A), 3 = (i, B).
@@ -204,7 +218,167 @@ __device__ __forceinline__ void ccvv_stage_mmas(uint32_t dx, uint32_t dy, uint32
   }
 }
 
-template <bool BF16>
+// Split of one FP32 value into BF16 hi + lo (f - hi is exact in FP32).
+__device__ __forceinline__ void bf16_split(float f, uint32_t& h, uint32_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(f);
+  h = __bfloat16_as_ushort(bh);
+  l = __bfloat16_as_ushort(__float2bfloat16_rn(f - __bfloat162float(bh)));
+}
+
+// 16 consecutive values of S (32-byte aligned offset) into the hi and lo planes.
+__device__ __forceinline__ void store_split16(uint16_t* hi, uint16_t* lo, long long off,
+                                              const float (&v)[16]) {
+  uint32_t ph[8], pl[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uint32_t h0, l0, h1, l1;
+    bf16_split(v[2 * k], h0, l0);
+    bf16_split(v[2 * k + 1], h1, l1);
+    ph[k] = h0 | (h1 << 16);
+    pl[k] = l0 | (l1 << 16);
+  }
+  uint4* dh = (uint4*)(hi + off);
+  uint4* dl = (uint4*)(lo + off);
+  dh[0] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+  dh[1] = make_uint4(ph[4], ph[5], ph[6], ph[7]);
+  dl[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+  dl[1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
+}
+
+// One 16-column chunk of the adjoint epilogue (F1 part of the gradient).
+// For the item's x_ab = v^{ij}_ab and y_ab = v^{ij}_ba (ordered pairs (i, j) and
+// (j, i) are both terms of Eq. (23)), the derivative of E_F1 with respect to
+// v^{ij}_ab is W^{ij}_ab = (4 x - 2 y) R and with respect to v^{ij}_ba it is
+// (4 y - 2 x) R; v^{ji} holds the same values transposed. dE/dB^Q_{ia} =
+// sum_{jb} 2 W^{ij}_ab B^Q_{jb}, so the chunk writes S = 2 W at the four
+// positions of the symmetric matrix S over the plane rows (i a), (j b):
+//   S[(i,a)][(j,b)] = S[(j,b)][(i,a)] = P = 2 (4x - 2y) R,
+//   S[(j,a)][(i,b)] = S[(i,b)][(j,a)] = Q = 2 (4y - 2x) R
+// (the duplicates of i = j or A = B are skipped). It adds q R'(D), q = x^2 -
+// x y + y^2, to the row sum `racc` and the column sums `colacc`, and q dR/ds
+// to `sacc` (the item's weight is applied once at its end).
+__device__ __forceinline__ void adjoint_chunk(
+    const SplitArgs& a, const ItemPlan& ip, uint32_t (&xr)[16], uint32_t (&yr)[16], bool rok,
+    int pth, int c0, int cend, int cbeg, int arow, int nVpad, double ca, double ha, double s,
+    const double* sEps, const double* sAlpha, const double* taucol, const float* tail,
+    const float* tail_ia, const float* tail_ja, double* colacc, int lane, double& racc,
+    double& sacc) {
+  if (rok) {
+    // the first TAIL_Q auxiliary functions in FP32 round-to-nearest
+    tail_add16(tail_ia, tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
+    if (ip.two) tail_add16(tail_ja, tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
+  }
+  float P[16], Qv[16];
+  double gd[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int cb = c0 + k;
+    const bool cok = rok && cb < cend;
+    const float xf = __uint_as_float(xr[k]);
+    const float yf = ip.two ? __uint_as_float(yr[k]) : xf;
+    const double D = ca - sEps[cb];
+    double Rv, RdD, Rds;
+    if (pth == 2) {
+      const RegD r = rf1_d(D, s);
+      Rv = r.v;
+      RdD = r.dD;
+      Rds = r.ds;
+    } else {
+      double r0;
+      asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(D));  // 1/D, seed
+      const double inv = fma(r0, fma(-D, r0, 1.0), r0);      // one Newton step
+      if (pth == 0) {
+        // exp(-2 s D^2) < 2^-63: R = 1/D, R' = -1/D^2, dR/ds = 2 D e^{-2sD^2} ~ 0
+        Rv = inv;
+        RdD = -inv * inv;
+        Rds = 0.0;
+      } else {
+        // |D| >= 1/4: g = exp(-2 s D^2) from the factor tables, 1 - g without cancellation
+        const double g = ha * sAlpha[cb] * taucol[(size_t)cb * nVpad];
+        const double em = g - 1.0;
+        const double x2 = 2.0 * s * D * D;
+        Rv = -em * inv;
+        RdD = fma(2.0 * x2, g, em) * inv * inv;
+        Rds = 2.0 * D * g;
+      }
+    }
+    // S is stored as BF16 hi + lo (16 bits): P and Q in FP32 with the FP64 regulator
+    // rounded once; q as in the energy's epilogue, its products with R' and dR/ds in FP64
+    const float rvf = (float)Rv;
+    P[k] = cok ? 2.f * fmaf(4.f, xf, -2.f * yf) * rvf : 0.f;
+    Qv[k] = cok ? 2.f * fmaf(4.f, yf, -2.f * xf) * rvf : 0.f;
+    const double q = (double)fmaf(xf, xf - yf, yf * yf);
+    const double g1 = cok ? q * RdD : 0.0;
+    gd[k] = g1;
+    racc += g1;
+    sacc += cok ? q * Rds : 0.0;
+  }
+  // column sums over the warp's 32 rows: a transposing butterfly halves the
+  // values per lane at each step; lane l ends with column
+  // 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of l), duplicated in lanes l and l ^ 1
+  double v8[8], v4[4], v2[2], v1;
+  {
+    const bool up = (lane & 16) != 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double send = up ? gd[k] : gd[k + 8];
+      v8[k] = (up ? gd[k + 8] : gd[k]) + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool up = (lane & 8) != 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double send = up ? v8[k] : v8[k + 4];
+      v4[k] = (up ? v8[k + 4] : v8[k]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  {
+    const bool up = (lane & 4) != 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double send = up ? v4[k] : v4[k + 2];
+      v2[k] = (up ? v4[k + 2] : v4[k]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+  }
+  {
+    const bool up = (lane & 2) != 0;
+    const double send = up ? v2[0] : v2[1];
+    v1 = (up ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  v1 += __shfl_xor_sync(0xffffffffu, v1, 1);
+  if ((lane & 1) == 0) {
+    const int col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                    ((lane >> 1) & 1);
+    colacc[c0 - cbeg + col] += v1;
+  }
+  if (!rok) return;
+  const long long lds = a.lds;
+  const int colb = ip.Bt * TT + c0;
+  store_split16(a.s_hi, a.s_lo, (long long)(ip.i * nVpad + arow) * lds + ip.j * nVpad + colb, P);
+  if (ip.two)
+    store_split16(a.s_hi, a.s_lo, (long long)(ip.j * nVpad + arow) * lds + ip.i * nVpad + colb, Qv);
+  if (ip.A != ip.Bt) {
+    // the transposed positions: one row per column b, the warp's 32 rows a contiguous
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (c0 + k >= cend) break;
+      uint32_t h, l;
+      bf16_split(Qv[k], h, l);
+      const long long o1 = (long long)(ip.i * nVpad + colb + k) * lds + ip.j * nVpad + arow;
+      a.s_hi[o1] = (uint16_t)h;
+      a.s_lo[o1] = (uint16_t)l;
+      if (ip.two) {
+        bf16_split(P[k], h, l);
+        const long long o2 = (long long)(ip.j * nVpad + colb + k) * lds + ip.i * nVpad + arow;
+        a.s_hi[o2] = (uint16_t)h;
+        a.s_lo[o2] = (uint16_t)l;
+      }
+    }
+  }
+}
+
+template <bool BF16, bool ADJ>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     ccvv_split_kernel(const __grid_constant__ CUtensorMap map_hi,
                       const __grid_constant__ CUtensorMap map_lo,
@@ -226,6 +400,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
   float* sEpsF = (float*)(sRed + EPI_WARPS);
   float* sCr = sEpsF + TT;  // [TT/16][2]: min, max of e over the valid columns of each 16-column chunk
   unsigned* sCnt = (unsigned*)(sCr + 2 * (TT / 16));  // [EPI_WARPS][3] epilogue blocks by regulator path
+  // adjoint epilogue: column sums per warp [EPI_WARPS][64], row sums per column
+  // half [2][TT], and the block sums of the pair and s derivatives [2][EPI_WARPS]
+  double* sColAcc = (double*)(sCnt + 3 * EPI_WARPS);
+  double* sRowAcc = sColAcc + EPI_WARPS * 64;
+  double* sRed2 = sRowAcc + 2 * TT;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int it0 = a.cta_begin[blockIdx.x], it1 = a.cta_begin[blockIdx.x + 1];
@@ -448,6 +627,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       // exp(-2 s D^2) < 2^-63 for every D of a block when 2 s D^2 > 44 (the FP32
       // range carries a margin: 46)
       const float far_d2 = 46.0f / (2.0f * (float)s);
+      // adjoint: this thread's sums of q R'(D) over its columns (row a) and of q dR/ds
+      double racc = 0.0, sacc = 0.0;
+      if constexpr (ADJ) {
+        sColAcc[(warp - 2) * 64 + lane] = 0.0;
+        sColAcc[(warp - 2) * 64 + 32 + lane] = 0.0;
+        __syncwarp();
+      }
 
       bool ok = mbar_wait(&tfull[tbuf], tphase, abort_flag, a.status);
       tc_fence_after();
@@ -468,6 +654,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           const bool away = dhi <= -0.25f || dlo >= 0.25f;
           const float dn = dhi <= 0.0f ? dhi : dlo;
           const int pth = !away ? 2 : (dn * dn > far_d2 ? 0 : (factorisable ? 1 : 2));
+          if constexpr (ADJ) {
+            adjoint_chunk(a, ip, xr, yr, rok, pth, c0, cend, cbeg, arow, nVpad, ca, ha, s, sEps,
+                          sAlpha, taucol, md->tail, tail_ia, tail_ja, sColAcc + (warp - 2) * 64,
+                          lane, racc, sacc);
+            continue;
+          }
           if (lane == 0) sCnt[3 * (warp - 2) + pth] += 1u;
           if (!rok) continue;
           // the first TAIL_Q auxiliary functions, the largest terms, in FP32
@@ -524,6 +716,46 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       if (++tbuf == 2) {
         tbuf = 0;
         tphase ^= 1u;
+      }
+      if constexpr (ADJ) {
+        // D = e_i + e_j - e_a - e_b: the item's sums of q R'(D) go to e_i and e_j with
+        // the sign +, to e_a (its rows) and e_b (its columns) with the sign -
+        const int half = (warp - 2) >> 2;
+        sRowAcc[half * TT + row] = racc;
+        double tr = racc, ts = sacc;
+        for (int o = 16; o > 0; o >>= 1) {
+          tr += __shfl_xor_sync(0xffffffffu, tr, o);
+          ts += __shfl_xor_sync(0xffffffffu, ts, o);
+        }
+        if (lane == 0) {
+          sRed2[warp - 2] = tr;
+          sRed2[EPI_WARPS + warp - 2] = ts;
+        }
+        named_bar(1, 32 * EPI_WARPS);
+        if (ok) {
+          const double w = (ip.two ? 2.0 : 1.0) * (ip.A < ip.Bt ? 2.0 : 1.0);
+          if (et < TT) {
+            const int ra = ip.A * TT + et;
+            if (ra < nV) atomicAdd(&a.deps[ve + ra], -w * (sRowAcc[et] + sRowAcc[TT + et]));
+            const int hb = et >> 6, cc = et & 63;
+            double t = 0.0;
+            for (int q = 0; q < 4; ++q) t += sColAcc[(4 * hb + q) * 64 + cc];
+            const int cb = ip.Bt * TT + et;
+            if (cb < nV) atomicAdd(&a.deps[ve + cb], -w * t);
+          } else if (et == TT) {
+            double tp = 0.0, tsum = 0.0;
+            for (int k = 0; k < EPI_WARPS; ++k) {
+              tp += sRed2[k];
+              tsum += sRed2[EPI_WARPS + k];
+            }
+            atomicAdd(&a.deps[ip.i], w * tp);
+            atomicAdd(&a.deps[ip.j], w * tp);
+            atomicAdd(a.ds, w * tsum);
+          }
+        }
+        // the sums are read before the next item clears them
+        named_bar(1, 32 * EPI_WARPS);
+        continue;
       }
       // fixed-order CTA sum of the item's contribution
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -1162,16 +1394,88 @@ cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_
   a.status = p->d_status;
   a.counts = p->d_counts;
   a.prefetch = prefetch;
+  a.s_hi = a.s_lo = nullptr;
+  a.lds = 0;
+  a.deps = a.ds = nullptr;
   const size_t sm = split_smem_bytes();
   if (bf16) {
-    raise_smem_limit((const void*)ccvv_split_kernel<true>, sm);
-    ccvv_split_kernel<true><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo, maps.hi64,
-                                                                    maps.lo64, a);
+    raise_smem_limit((const void*)ccvv_split_kernel<true, false>, sm);
+    ccvv_split_kernel<true, false><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo,
+                                                                           maps.hi64, maps.lo64, a);
   } else {
-    raise_smem_limit((const void*)ccvv_split_kernel<false>, sm);
-    ccvv_split_kernel<false><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo, maps.hi64,
-                                                                     maps.lo64, a);
+    raise_smem_limit((const void*)ccvv_split_kernel<false, false>, sm);
+    ccvv_split_kernel<false, false><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo,
+                                                                            maps.hi64, maps.lo64, a);
   }
+  DSRG_LAUNCH_CHECK(p);
+  return cudaSuccess;
+}
+
+// The adjoint's recompute of the CCVV pair blocks needs TF32 operands: a BF16x3
+// product carries each factor to 16 bits, and the element-wise errors of x and
+// y (which the energy averages away) would reach dE/dB. TF32x3 plans reuse
+// their planes and descriptor; BF16x3 plans get TF32 planes of the core rows.
+bool split_adj_alloc(dsrg_plan* p) {
+  SplitWs* w = p->split;
+  const Sizes& z = p->z;
+  if (p->prec != DSRG_PREC_BF16X3) {
+    w->adj_maps = w->cmaps;
+    w->d_mol_adj = w->d_mol;
+    w->adj_ready = true;
+    return true;
+  }
+  const long long rows = (long long)z.nC * w->nVpad;
+  const size_t plane = (size_t)rows * w->Qpad * 4;
+  if (!plan_alloc(p, &w->adj_hi, plane) || !plan_alloc(p, &w->adj_lo, plane) ||
+      !plan_alloc(p, &w->d_mol_adj, sizeof(MolDesc)))
+    return false;
+  if (cudaMemset(w->adj_hi, 0, plane) != cudaSuccess || cudaMemset(w->adj_lo, 0, plane) != cudaSuccess)
+    return false;
+  if (!split_make_ccvv_maps(&w->adj_maps, w->adj_hi, w->adj_lo, false, rows, w->Qpad)) return false;
+  MolDesc md;
+  if (cudaMemcpy(&md, w->d_mol, sizeof(MolDesc), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  md.kblocks = (w->Qpad - TAIL_Q) / (KB_BYTES / 4);
+  if (cudaMemcpy(w->d_mol_adj, &md, sizeof(MolDesc), cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  w->adj_ready = true;
+  return true;
+}
+
+// F1's part of the gradient for the plan's pairs: S (core x virtual block),
+// deps and ds (added to). The planes, tail rows and pair tables of the energy
+// call just made on the stream (same B, eps, s) are reused.
+cudaError_t split_launch_ccvv_adjoint(dsrg_plan* p, const double* B, const double* eps, double s,
+                                      uint16_t* s_hi, uint16_t* s_lo, long long lds, double* deps,
+                                      double* ds) {
+  SplitWs* w = p->split;
+  const Sizes& z = p->z;
+  if (!w->adj_ready) return cudaErrorInvalidValue;
+  if (p->prec == DSRG_PREC_BF16X3) {
+    dim3 grid(w->Qpad / 64, w->nVpad / 64, z.nC);
+    // the tail rows are rewritten with the same fl32(B) values
+    split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qpad, w->adj_hi,
+                                                            w->adj_lo, w->tail, 0);
+    DSRG_LAUNCH_CHECK(p);
+    cudaError_t e = split_set_inputs(p, w->d_mol_adj, 0, 1, &eps, &s);
+    if (e != cudaSuccess) return e;
+  }
+  SplitArgs a;
+  a.mols = (const MolDesc*)w->d_mol_adj;
+  a.items = w->d_items;
+  a.cta_begin = w->d_begin;
+  a.status = p->d_status;
+  a.counts = p->d_counts;
+  a.prefetch = 0;
+  a.s_hi = s_hi;
+  a.s_lo = s_lo;
+  a.lds = lds;
+  a.deps = deps;
+  a.ds = ds;
+  const size_t sm = split_smem_bytes() + (EPI_WARPS * 64 + 2 * TT + 2 * EPI_WARPS) * 8;
+  const CcvvMaps& m = w->adj_maps;
+  raise_smem_limit((const void*)ccvv_split_kernel<false, true>, sm);
+  ccvv_split_kernel<false, true><<<w->grid, SPLIT_THREADS, sm, p->stream>>>(m.hi, m.lo, m.hi64,
+                                                                            m.lo64, a);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }

@@ -7,12 +7,15 @@ cc-pVTZ size on 200 random entries of B plus orbital energies and s, with the
 combined bound |g_fd - g| <= 1e-6 |g| + 10 eps_mach |E| / h (the second term is
 the rounding floor of a difference quotient of a number of size |E|).
 
-Split-precision plans compute the gradient's contractions over Q and its
-GEMMs in FP32 with round-to-nearest (FP64 regulators and epilogues): their
-gradient is checked against the oracle and against the FP64 plan with a bound
-from FP32 rounding, 1e-5 of the largest entry of each gradient array (FP32
-dot products of a few thousand terms carry about sqrt(n) * 2^-24 of the sum of
-their absolute terms).
+Split-precision plans recompute the CCVV pair blocks in TF32x3 on the tensor
+cores and assemble dB as one BF16x3 tensor-core GEMM of the symmetric adjoint
+matrix S with B^T, one K stage per TMEM accumulation, summed in FP32 with
+round-to-nearest (FP64 regulators and epilogues). Each term of that GEMM
+carries the 2^-17 relative error of the BF16 hi + lo representation of S and
+B; where a dB entry sums few terms (the small systems) that error is not
+averaged down, so against the oracle the bound is 1e-5 of the largest entry
+of each array (measured up to 2.5e-6). At the cc-pVTZ size, against the FP64
+plan, the bound is the 1e-6 gradient bar (measured 3e-7).
 """
 import numpy as np
 import pytest
@@ -121,8 +124,9 @@ def test_grad_requires_flag(pk):
 
 
 def test_split_grad_against_fp64_plan_vtz(pk):
-    """cc-pVTZ size: the gradient of a BF16x3 plan (FP32 contractions) against
-    the FP64 plan's, normalised by the largest entry of each array."""
+    """cc-pVTZ size: the gradient of a BF16x3 plan (tensor-core recompute and
+    assembly) against the FP64 plan's, normalised by the largest entry of each
+    array, within the 1e-6 gradient bar."""
     p = make_problem(**CONFIGS["naphthyne-vtz-398"])
     dev = pk.to_device(p)
     res = {}
@@ -137,4 +141,4 @@ def test_split_grad_against_fp64_plan_vtz(pk):
     erre = np.abs(e32 - e64).max() / np.abs(e64).max()
     errs = abs(s32 - s64) / abs(s64)
     print("vtz split vs fp64 gradient: dB %.2e deps %.2e ds %.2e" % (errB, erre, errs))
-    assert errB < 1e-5 and erre < 1e-5 and errs < 1e-5
+    assert errB < 1e-6 and erre < 1e-6 and errs < 1e-6
