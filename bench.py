@@ -300,6 +300,7 @@ def time_batch(pk, torch, nmol, prec):
     b = pk.Batch([(m.ncore, m.nactive, m.nvirt, m.naux) for m in mols], precision=prec)
     svals = [m.s for m in mols]
     order = b.autotune(dev, svals, reps=1) if prec != "fp64" else None   # setup, not timed
+    branches = b.autotune_branches(dev, svals, reps=1)                   # setup, not timed
     out = b.energy(dev, svals)          # captures the graph
     b.energy(dev, svals, out=out)
     torch.cuda.synchronize()
@@ -323,7 +324,8 @@ def time_batch(pk, torch, nmol, prec):
     t64 = e0.elapsed_time(e1) / 1e3
     ob = out.cpu().numpy()
     err = max(abs(ob[k][4] - float(o64[k][4])) / abs(float(o64[k][4])) for k in range(nmol))
-    res = {"n_mol": nmol, "precision": prec, "item_order": order, "ms_per_batch": tb * 1e3,
+    res = {"n_mol": nmol, "precision": prec, "item_order": order, "graph_branches": branches,
+           "ms_per_batch": tb * 1e3,
            "molecules_per_s": nmol / tb, "aggregate_ccvv_tflops": flops / tb / 1e12,
            "graph_kernel_launches": b.launch_count(),
            "fp64_one_by_one_ms": t64 * 1e3, "fp64_one_by_one_molecules_per_s": nmol / t64,

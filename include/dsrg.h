@@ -212,6 +212,25 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t *batch, const double *const
                                         const double *const *lambda2, const double *s,
                                         double *out_dev);
 
+/* Concurrent branches of the per-molecule blocks (CAVV, CCAV, active block and
+ * the reductions of each molecule, which do not depend on each other): after
+ * the batched CCVV launch the graph forks into K branches, molecule m on
+ * branch m mod K, and joins them at the end. K is 1, 2 or 4 and at most
+ * min(nmol rounded down to a power of 2, 4) (each branch owns a GEMM output
+ * buffer, allocated with the plan); the default is that maximum. Setting a new
+ * K waits for the batch's stream and makes the next call capture a new graph.
+ * The energies do not depend on K. The autotuner times `reps` replays of the
+ * whole batched call for every allowed K on the given inputs (as for
+ * dsrg_mrpt2_energy_batched; out_dev receives their energies), keeps the
+ * fastest and returns it in *chosen (may be NULL). Synchronous. */
+int32_t dsrg_batch_branches(const dsrg_batch_t *batch);
+dsrg_status_t dsrg_batch_set_branches(dsrg_batch_t *batch, int32_t k);
+dsrg_status_t dsrg_batch_autotune_branches(dsrg_batch_t *batch, const double *const *B,
+                                           const double *const *eps,
+                                           const double *const *gamma1,
+                                           const double *const *lambda2, const double *s,
+                                           double *out_dev, int32_t reps, int32_t *chosen);
+
 /* Wait for the batch's stream and report device-side conditions of any molecule. */
 dsrg_status_t dsrg_batch_sync(dsrg_batch_t *batch);
 /* Kernel launches recorded in the batch's graph. */
@@ -242,6 +261,24 @@ dsrg_status_t dsrg_batch_autotune(dsrg_batch_t *batch, const double *const *B,
  * earlier; prefetch distance <= 64; no-op for FP64). The batch
  * setter waits for the batch's stream first; neither may run while a launch
  * that uses the schedule is being captured. */
+/* Persisted choices: when the environment variable DSRG_AUTOTUNE_CACHE names a
+ * file, dsrg_plan_autotune, dsrg_batch_autotune and dsrg_batch_autotune_branches
+ * first look their key up there and, if it is present, apply the stored choice
+ * without timing anything (it is returned in *chosen as usual); otherwise they
+ * time the candidates and store the winner. Keys name the tuned quantity, the
+ * GPU (device name and compute capability), the precision and the size class
+ * of the problem (single plans: core orbitals rounded up to 4, virtual tiles of
+ * 128, tensor-core K stages rounded up to 8, shard world; batches: molecule
+ * count, work items rounded up to 256, padded naux). The file is a flat JSON
+ * object {"key": integer, ...}, rewritten whole through a temporary file and a
+ * rename. The two calls below read and write it directly (no GPU needed):
+ * get returns 1 and sets *value when the key is present, 0 when it (or the
+ * file) is absent, -1 for a file that is not such an object; put returns
+ * DSRG_ERR_INVALID_ARG for a key with a quote, backslash or control character,
+ * or when the file cannot be written. */
+int32_t dsrg_tune_cache_get(const char *path, const char *key, int64_t *value);
+dsrg_status_t dsrg_tune_cache_put(const char *path, const char *key, int64_t value);
+
 int32_t dsrg_plan_item_order(const dsrg_plan_t *plan);
 int32_t dsrg_batch_item_order(const dsrg_batch_t *batch);
 dsrg_status_t dsrg_plan_set_item_order(dsrg_plan_t *plan, int32_t order);

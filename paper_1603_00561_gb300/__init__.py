@@ -260,6 +260,33 @@ class Batch:
         if st != _native.OK:
             raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
 
+    @property
+    def branches(self) -> int:
+        """Concurrent branches of the per-molecule blocks in the batched graph."""
+        return int(self.lib.dsrg_batch_branches(self.h))
+
+    @branches.setter
+    def branches(self, k: int):
+        st = self.lib.dsrg_batch_set_branches(self.h, int(k))
+        if st != _native.OK:
+            raise DSRGError(st, f"dsrg_batch_set_branches({k})")
+
+    def autotune_branches(self, inputs, s, reps: int = 2, out=None) -> int:
+        """Time the whole batched call for every allowed branch count and keep the
+        fastest (``dsrg_batch_autotune_branches``); returns it."""
+        if out is None:
+            out = torch.empty((self.n, 5), dtype=torch.float64, device=self.device)
+        P = C.c_void_p * self.n
+        cols = list(zip(*inputs))
+        ptrs = [P(*[_ptr(t) for t in col]) for col in cols]
+        svals = (C.c_double * self.n)(*[float(x) for x in s])
+        chosen = C.c_int32(-1)
+        st = self.lib.dsrg_batch_autotune_branches(self.h, *ptrs, svals, _ptr(out), int(reps),
+                                                   C.byref(chosen))
+        if st != _native.OK:
+            raise DSRGError(st, self.lib.dsrg_batch_last_error(self.h).decode())
+        return int(chosen.value)
+
     def sync(self):
         st = self.lib.dsrg_batch_sync(self.h)
         if st != _native.OK:
@@ -278,6 +305,26 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def tune_cache_get(path, key):
+    """The value stored under ``key`` in the autotuners' cache file, or None
+    (``dsrg_tune_cache_get``; no GPU needed). A malformed file raises."""
+    lib = _native.load()
+    v = C.c_int64(0)
+    r = lib.dsrg_tune_cache_get(str(path).encode(), key.encode(), C.byref(v))
+    if r < 0:
+        raise ValueError(f"{path} is not an autotune cache file")
+    return int(v.value) if r == 1 else None
+
+
+def tune_cache_put(path, key, value):
+    """Store ``value`` under ``key`` in the autotuners' cache file
+    (``dsrg_tune_cache_put``; no GPU needed)."""
+    lib = _native.load()
+    st = lib.dsrg_tune_cache_put(str(path).encode(), key.encode(), int(value))
+    if st != _native.OK:
+        raise DSRGError(st, f"dsrg_tune_cache_put({path}, {key})")
 
 
 class SemicanonicalPlan:

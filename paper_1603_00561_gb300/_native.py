@@ -30,7 +30,9 @@ EXPORTS = [
     "dsrg_mrpt2_energy_grad_ext", "dsrg_sc_plan_create", "dsrg_sc_plan_destroy", "dsrg_generalized_fock",
     "dsrg_semicanonicalize", "dsrg_sc_last_sweeps", "dsrg_sc_last_error",
     "dsrg_df_mo_transform_work_bytes", "dsrg_df_mo_transform", "dsrg_cd_factors_work_bytes",
-    "dsrg_cd_factors", "dsrg_plan_set_shard", "dsrg_shard_pairs",
+    "dsrg_cd_factors", "dsrg_plan_set_shard", "dsrg_shard_pairs", "dsrg_batch_branches",
+    "dsrg_batch_set_branches", "dsrg_batch_autotune_branches", "dsrg_tune_cache_get",
+    "dsrg_tune_cache_put",
 ]
 # indices of dsrg_plan_branch_counts
 NCOUNTERS = 8
@@ -145,6 +147,18 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.dsrg_plan_set_item_order.restype = st
     lib.dsrg_batch_set_item_order.argtypes = [vp, C.c_int32]
     lib.dsrg_batch_set_item_order.restype = st
+    lib.dsrg_batch_branches.argtypes = [vp]
+    lib.dsrg_batch_branches.restype = C.c_int32
+    lib.dsrg_batch_set_branches.argtypes = [vp, C.c_int32]
+    lib.dsrg_batch_set_branches.restype = st
+    lib.dsrg_batch_autotune_branches.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                                 C.POINTER(vp), C.POINTER(C.c_double), vp,
+                                                 C.c_int32, C.POINTER(C.c_int32)]
+    lib.dsrg_batch_autotune_branches.restype = st
+    lib.dsrg_tune_cache_get.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(C.c_int64)]
+    lib.dsrg_tune_cache_get.restype = C.c_int32
+    lib.dsrg_tune_cache_put.argtypes = [C.c_char_p, C.c_char_p, C.c_int64]
+    lib.dsrg_tune_cache_put.restype = st
     _ = dp
     _lib = lib
     return lib

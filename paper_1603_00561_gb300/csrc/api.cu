@@ -459,6 +459,22 @@ dsrg_status_t dsrg_plan_autotune(dsrg_plan_t* p, const double* B, const double* 
   if (reps < 1) return fail(p, DSRG_ERR_INVALID_ARG, "reps must be >= 1");
   if (chosen) *chosen = -1;
   if (p->prec == DSRG_PREC_FP64) return DSRG_OK;
+  // a choice stored for this GPU, precision and size class is applied without timing
+  const char* cache = tune_cache_path();
+  std::string key;
+  if (cache) {
+    const int kblocks = (split_qpad(p) - 32) / split_kb_elems(p->prec == DSRG_PREC_BF16X3);
+    key = std::string("ccvv-schedule|") + tune_gpu_name(p->device) + "|" +
+          (p->prec == DSRG_PREC_BF16X3 ? "bf16x3" : "tf32x3") + "|" +
+          tune_size_class(p->z, kblocks, p->shard_world);
+    long long v = -1;
+    if (tune_cache_get(cache, key.c_str(), &v) == 1 && v >= 0 && (v >> 16) <= 64) {
+      cudaError_t ec = split_set_order(p, (int)v);
+      if (ec != cudaSuccess) return cuda_fail(p, ec, "autotune (cached)");
+      if (chosen) *chosen = (int32_t)v;
+      return DSRG_OK;
+    }
+  }
   cudaError_t e = split_stage(p, B, eps, s);
   if (e == cudaSuccess) e = split_prepare_single(p, eps, s);
   float best_ms = 0.f;
@@ -477,6 +493,7 @@ dsrg_status_t dsrg_plan_autotune(dsrg_plan_t* p, const double* B, const double* 
   if (e != cudaSuccess) return cuda_fail(p, e, "autotune");
   st = dsrg_plan_sync(p);
   if (st != DSRG_OK) return st;
+  if (cache) tune_cache_put(cache, key.c_str(), best);  // best effort: a read-only path is no error
   if (chosen) *chosen = best;
   return DSRG_OK;
 }

@@ -8,15 +8,27 @@
 // to the CTAs by the cost-balancing scheduler of tc_split.cu. The whole call
 // (staging, the batched CCVV launch, every molecule's remaining blocks and
 // reductions) is captured once into a CUDA graph and replayed while the input
-// pointers and flow parameters stay the same.
+// pointers and flow parameters stay the same. After the batched CCVV launch the
+// molecules' other blocks are independent of each other: the graph forks them
+// into up to BATCH_MAX_BRANCHES concurrent branches (molecule m on branch
+// m mod K), so that the small per-molecule kernels fill the GPU together; each
+// branch has its own GEMM output buffer.
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "internal.cuh"
 
+constexpr int BATCH_MAX_BRANCHES = 4;
+
 struct dsrg_batch {
   int nmol = 0;
+  int branches = 1;      // concurrent branches of the per-molecule blocks (1, 2 or 4)
+  int max_branches = 1;  // branches the GEMM output buffers allow (a power of 2)
+  cudaStream_t side[BATCH_MAX_BRANCHES] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[BATCH_MAX_BRANCHES] = {};
   dsrg_precision_t prec = DSRG_PREC_FP64;
   cudaStream_t user_stream = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -24,13 +36,15 @@ struct dsrg_batch {
   std::vector<void*> allocs;
   void* hi = nullptr;
   void* lo = nullptr;
-  float* ybuf = nullptr;  // GEMM output of the CAVV/CCAV/active stage, reused molecule by molecule
+  float* ybuf = nullptr;  // GEMM outputs of the CAVV/CCAV/active stage, one per branch
+  size_t ybytes = 0;      // bytes of one of them
   dsrg::CcvvMaps maps;
   void* d_mols = nullptr;
   int4* d_items = nullptr;
   int* d_begin = nullptr;
   int grid = 0;
   int order = 0;  // item order of the batched CCVV schedule
+  std::string tune_class;  // size class of the batch in the autotuners' cache keys
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;
@@ -65,6 +79,14 @@ void bfree(dsrg_batch* b) {
   b->allocs.clear();
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   b->cap_stream = nullptr;
+  for (int k = 0; k < BATCH_MAX_BRANCHES; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    b->side[k] = nullptr;
+    b->ev_join[k] = nullptr;
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  b->ev_fork = nullptr;
 }
 
 dsrg_status_t bfail(dsrg_batch* b, dsrg_status_t st, const std::string& m) {
@@ -89,6 +111,17 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
   b->prec = prec;
   b->user_stream = (cudaStream_t)cuda_stream;
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return DSRG_ERR_CUDA;
+  }
+  b->max_branches = nmol >= 4 ? 4 : (nmol >= 2 ? 2 : 1);
+  b->branches = b->max_branches;
+  bool streams_ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; streams_ok && k < b->max_branches; ++k)
+    streams_ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!streams_ok) {
+    bfree(b);
     delete b;
     return DSRG_ERR_CUDA;
   }
@@ -118,7 +151,8 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
   }
   const int elt = bf16 ? 2 : 4;
   if (split) {
-    // molecules run one after another on one stream: one GEMM output buffer serves all
+    // one GEMM output buffer per branch: molecule m uses buffer m mod max_branches,
+    // and the molecules of one branch run one after another
     size_t ybytes = 0;
     for (int m = 0; m < nmol; ++m) {
       const dsrg_sizes_t& s = sizes[m];
@@ -127,12 +161,13 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
       const size_t yb = dsrg::rest_supported(z) ? dsrg::rest_y_bytes(z) : 0;
       ybytes = yb > ybytes ? yb : ybytes;
     }
-    if (ybytes > 0 && !balloc(b, (void**)&b->ybuf, ybytes)) {
+    ybytes = (ybytes + 255) / 256 * 256;
+    if (ybytes > 0 && !balloc(b, (void**)&b->ybuf, ybytes * b->max_branches)) {
       bfree(b);
       delete b;
       return DSRG_ERR_OOM;
     }
-    b->ws_bytes += ybytes;
+    b->ybytes = ybytes;
     const size_t plane = (size_t)rows * Qld * elt;
     if (!balloc(b, &b->hi, plane) || !balloc(b, &b->lo, plane)) {
       bfree(b);
@@ -153,7 +188,7 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
     sh.lo = split ? (char*)b->lo + (size_t)row_base[m] * Qld * elt : nullptr;
     sh.Qld = Qld;
     sh.row_base = row_base[m];
-    sh.y = b->ybuf;
+    sh.y = b->ybuf ? b->ybuf + (m % b->max_branches) * (b->ybytes / sizeof(float)) : nullptr;
     dsrg_status_t st =
         dsrg::create_plan(&b->plans[m], &sizes[m], prec, b->cap_stream, flags, split ? &sh : nullptr);
     if (st != DSRG_OK) {
@@ -178,6 +213,8 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     b->grid = (int)items.size() < nsm ? (int)items.size() : nsm;
+    b->tune_class = "n" + std::to_string(nmol) + "-i" + std::to_string((items.size() + 255) / 256 * 256) +
+                    "-q" + std::to_string(Qld);
     dsrg::split_schedule(items, cost, b->grid, sched, begin);
     if (!balloc(b, &b->d_mols, mols.size()) ||
         !balloc(b, (void**)&b->d_items, sched.size() * sizeof(int4)) ||
@@ -199,6 +236,16 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
 }  // extern "C"
 
 namespace {
+// Key of an autotuner choice for this batch in the persisted cache.
+std::string batch_key(const dsrg_batch* b, const char* what) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const char* prec = b->prec == DSRG_PREC_BF16X3 ? "bf16x3" : (b->prec == DSRG_PREC_TF32X3 ? "tf32x3" : "fp64");
+  std::string cls = b->tune_class;
+  if (cls.empty()) cls = "n" + std::to_string(b->nmol);
+  return std::string(what) + "|" + dsrg::tune_gpu_name(dev) + "|" + prec + "|" + cls;
+}
+
 // Rebuild the batched CCVV schedule for item order `order` (same item count).
 cudaError_t batch_set_order(dsrg_batch* b, int order) {
   const bool bf16 = b->prec == DSRG_PREC_BF16X3;
@@ -230,6 +277,18 @@ dsrg_status_t dsrg_batch_autotune(dsrg_batch_t* b, const double* const* B, const
     if (!B[m] || !eps[m]) return bfail(b, DSRG_ERR_INVALID_ARG, "B and eps must not be NULL");
     if (std::isnan(s[m]) || std::isinf(s[m]) || s[m] < 0.0)
       return bfail(b, DSRG_ERR_INVALID_ARG, "bad s");
+  }
+  const char* cache = dsrg::tune_cache_path();
+  const std::string key = cache ? batch_key(b, "batch-ccvv-schedule") : std::string();
+  if (cache) {
+    long long v = -1;
+    if (dsrg::tune_cache_get(cache, key.c_str(), &v) == 1 && v >= 0 && (v >> 16) <= 64) {
+      if (b->user_stream) cudaStreamSynchronize(b->user_stream);
+      cudaError_t ec = batch_set_order(b, (int)v);
+      if (ec != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(ec));
+      if (chosen) *chosen = (int32_t)v;
+      return DSRG_OK;
+    }
   }
   cudaStream_t st = b->user_stream;
   dsrg_plan* p0 = b->plans[0];
@@ -272,6 +331,7 @@ dsrg_status_t dsrg_batch_autotune(dsrg_batch_t* b, const double* const* B, const
     if (stt != DSRG_OK) return bfail(b, stt, "a device-side wait ran out");
   }
   // the schedule arrays keep their addresses: a captured graph stays valid
+  if (cache) dsrg::tune_cache_put(cache, key.c_str(), best);
   if (chosen) *chosen = best;
   return DSRG_OK;
 }
@@ -357,10 +417,26 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
                                     b->grid, b->prec == DSRG_PREC_BF16X3, b->order >> 16);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
+    // the per-molecule blocks: fork into K branches, molecule m on branch m mod K
+    const int K = b->branches;
+    if (st == DSRG_OK && K > 1) {
+      e = cudaEventRecord(b->ev_fork, b->cap_stream);
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+      if (e != cudaSuccess) st = DSRG_ERR_CUDA;
+    }
     for (int m = 0; m < n && st == DSRG_OK; ++m) {
       dsrg_plan* p = b->plans[m];
+      p->stream = K > 1 ? b->side[m % K] : b->cap_stream;
       st = dsrg::run_rest(p, B[m], eps[m], gamma1 ? gamma1[m] : nullptr,
                           lambda2 ? lambda2[m] : nullptr, nullptr, nullptr, s[m], out_dev + 5 * m);
+    }
+    if (K > 1) {
+      // join every branch that was forked, also after a failure, so that the capture ends
+      for (int k = 0; k < K; ++k) {
+        cudaError_t ej = cudaEventRecord(b->ev_join[k], b->side[k]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->cap_stream, b->ev_join[k], 0);
+        if (ej != cudaSuccess && st == DSRG_OK) st = DSRG_ERR_CUDA;
+      }
     }
     for (int m = 0; m < n; ++m) b->launches += b->plans[m]->launches;
     cudaGraph_t graph = nullptr;
@@ -384,6 +460,84 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
 }
 
 int32_t dsrg_batch_launch_count(const dsrg_batch_t* b) { return b ? b->launches : -1; }
+
+int32_t dsrg_batch_branches(const dsrg_batch_t* b) { return b ? b->branches : -1; }
+
+dsrg_status_t dsrg_batch_set_branches(dsrg_batch_t* b, int32_t k) {
+  if (!b || (k != 1 && k != 2 && k != 4) || k > b->max_branches) return DSRG_ERR_INVALID_ARG;
+  if (k == b->branches) return DSRG_OK;
+  if (b->user_stream) cudaStreamSynchronize(b->user_stream);
+  // the next call captures a new graph
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->key.clear();
+  b->branches = k;
+  return DSRG_OK;
+}
+
+dsrg_status_t dsrg_batch_autotune_branches(dsrg_batch_t* b, const double* const* B,
+                                           const double* const* eps,
+                                           const double* const* gamma1,
+                                           const double* const* lambda2, const double* s,
+                                           double* out_dev, int32_t reps, int32_t* chosen) {
+  if (!b || reps < 1) return DSRG_ERR_INVALID_ARG;
+  if (chosen) *chosen = -1;
+  const char* cache = dsrg::tune_cache_path();
+  const std::string key = cache ? batch_key(b, "batch-branches") : std::string();
+  if (cache) {
+    long long v = -1;
+    if (dsrg::tune_cache_get(cache, key.c_str(), &v) == 1 && (v == 1 || v == 2 || v == 4) &&
+        v <= b->max_branches) {
+      dsrg_status_t rc = dsrg_batch_set_branches(b, (int32_t)v);
+      if (rc == DSRG_OK && chosen) *chosen = (int32_t)v;
+      return rc;
+    }
+  }
+  cudaStream_t st = b->user_stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+  }
+  dsrg_status_t rs = DSRG_OK;
+  float best_ms = 0.f;
+  int best = b->branches;
+  bool first = true;
+  for (int k = 1; k <= b->max_branches && rs == DSRG_OK; k *= 2) {
+    rs = dsrg_batch_set_branches(b, k);
+    // the first call captures the graph; then one untimed and `reps` timed replays
+    for (int r = 0; rs == DSRG_OK && r <= reps + 1; ++r) {
+      if (r == 2 && cudaEventRecord(e0, st) != cudaSuccess) rs = DSRG_ERR_CUDA;
+      if (rs == DSRG_OK) rs = dsrg_mrpt2_energy_batched(b, B, eps, gamma1, lambda2, s, out_dev);
+    }
+    if (rs != DSRG_OK) break;
+    float ms = 0.f;
+    e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rs = bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
+      break;
+    }
+    if (first || ms < best_ms) {
+      best_ms = ms;
+      best = k;
+    }
+    first = false;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs != DSRG_OK) return rs;
+  rs = dsrg_batch_set_branches(b, best);
+  if (rs == DSRG_OK) rs = dsrg_batch_sync(b);
+  if (rs == DSRG_OK && cache) dsrg::tune_cache_put(cache, key.c_str(), best);
+  if (rs == DSRG_OK && chosen) *chosen = best;
+  return rs;
+}
 
 dsrg_status_t dsrg_batch_sync(dsrg_batch_t* b) {
   if (!b) return DSRG_ERR_INVALID_ARG;

@@ -249,6 +249,14 @@ GemmArgs batched(GemmArgs g, int nb, long long sa, long long sb, long long sc);
 // FP64 (64 x 64 tiles, FP64 FMA) on stream st; accumulate = 1 adds to C.
 cudaError_t launch_gemm_fp64(cudaStream_t st, const GemmArgs& g);
 
+// Persisted autotuner choices (tune_cache.cu): a flat JSON object in the file
+// named by DSRG_AUTOTUNE_CACHE. get: 1 found, 0 absent, -1 malformed file.
+int tune_cache_get(const char* path, const char* key, long long* value);
+bool tune_cache_put(const char* path, const char* key, long long value);
+const char* tune_cache_path();  // NULL: no cache
+std::string tune_gpu_name(int device);
+std::string tune_size_class(const Sizes& z, int kblocks, int world);
+
 // Gradient (grad.cu).
 bool grad_alloc(dsrg_plan* p);
 void grad_free(dsrg_plan* p);

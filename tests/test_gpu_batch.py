@@ -86,3 +86,66 @@ def test_batch_uneven_recipe_against_oracle(pk):
                 assert out[m][k] == 0.0
             else:
                 assert abs(out[m][k] - ref[name]) / abs(ref[name]) <= bar, (m, name)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
+def test_branches_do_not_change_the_energies(pk, prec):
+    """The per-molecule blocks forked into 1, 2 or 4 concurrent graph branches
+    (molecule m on branch m mod K, one GEMM output buffer per branch) give the
+    same energies bit for bit; the branch autotuner keeps an allowed K."""
+    mols = _mols(SPECS)
+    batch = pk.Batch([(p.ncore, p.nactive, p.nvirt, p.naux) for p in mols], precision=prec)
+    dev = [pk.to_device(p) for p in mols]
+    s = [p.s for p in mols]
+    assert batch.branches == 4
+    res = {}
+    for k in (1, 2, 4):
+        batch.branches = k
+        res[k] = batch.energy(dev, s).cpu().numpy()
+        batch.sync()
+    assert np.array_equal(res[1], res[2]) and np.array_equal(res[1], res[4])
+    with pytest.raises(pk.DSRGError):
+        batch.branches = 3
+    k = batch.autotune_branches(dev, s, reps=1)
+    assert k in (1, 2, 4) and batch.branches == k
+    assert np.array_equal(batch.energy(dev, s).cpu().numpy(), res[1])
+    small = pk.Batch([(p.ncore, p.nactive, p.nvirt, p.naux) for p in mols[:3]], precision=prec)
+    assert small.branches == 2          # three molecules: at most two buffers
+    with pytest.raises(pk.DSRGError):
+        small.branches = 4
+
+
+def test_autotune_cache_is_written_and_applied(pk, tmp_path, monkeypatch):
+    """With DSRG_AUTOTUNE_CACHE set, the tuners store their winners under keys of
+    GPU, precision and size class; a stored choice is applied without timing."""
+    import json
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("DSRG_AUTOTUNE_CACHE", str(path))
+    p = make_problem(6, 2, 300, 120, s=0.5, seed=7)
+    dev = pk.to_device(p)
+    plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision="bf16x3")
+    e0 = plan.energy(*dev, p.s).cpu().numpy()
+    code = plan.autotune(dev[0], dev[1], p.s, reps=1)
+    data = json.loads(path.read_text())
+    keys = [k for k in data if k.startswith("ccvv-schedule|")]
+    assert len(keys) == 1 and data[keys[0]] == code and "|bf16x3|" in keys[0]
+    # a different stored choice is taken as it is
+    other = 9 if code != 9 else 17
+    pk.tune_cache_put(path, keys[0], other)
+    plan2 = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision="bf16x3")
+    assert plan2.autotune(dev[0], dev[1], p.s, reps=1) == other
+    assert plan2.item_order == other
+    assert np.array_equal(plan2.energy(*dev, p.s).cpu().numpy(), e0)
+    # batches: the schedule and the branch count
+    mols = _mols(SPECS[:4])
+    bd = [pk.to_device(m) for m in mols]
+    s = [m.s for m in mols]
+    batch = pk.Batch([(m.ncore, m.nactive, m.nvirt, m.naux) for m in mols], precision="bf16x3")
+    c = batch.autotune(bd, s, reps=1)
+    k = batch.autotune_branches(bd, s, reps=1)
+    data = json.loads(path.read_text())
+    bkeys = {k2.split("|")[0]: v for k2, v in data.items() if k2.startswith("batch")}
+    assert bkeys == {"batch-ccvv-schedule": c, "batch-branches": k}
+    batch2 = pk.Batch([(m.ncore, m.nactive, m.nvirt, m.naux) for m in mols], precision="bf16x3")
+    assert batch2.autotune(bd, s, reps=1) == c and batch2.autotune_branches(bd, s, reps=1) == k
+    assert batch2.branches == k
