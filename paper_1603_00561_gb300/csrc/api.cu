@@ -468,7 +468,7 @@ dsrg_status_t dsrg_plan_autotune(dsrg_plan_t* p, const double* B, const double* 
           (p->prec == DSRG_PREC_BF16X3 ? "bf16x3" : "tf32x3") + "|" +
           tune_size_class(p->z, kblocks, p->shard_world);
     long long v = -1;
-    if (tune_cache_get(cache, key.c_str(), &v) == 1 && v >= 0 && (v >> 16) <= 64) {
+    if (tune_cache_get(cache, key.c_str(), &v) == 1 && split_code_valid(v)) {
       cudaError_t ec = split_set_order(p, (int)v);
       if (ec != cudaSuccess) return cuda_fail(p, ec, "autotune (cached)");
       if (chosen) *chosen = (int32_t)v;
@@ -501,7 +501,7 @@ dsrg_status_t dsrg_plan_autotune(dsrg_plan_t* p, const double* B, const double* 
 int32_t dsrg_plan_item_order(const dsrg_plan_t* p) { return p ? split_order(p) : -1; }
 
 dsrg_status_t dsrg_plan_set_item_order(dsrg_plan_t* p, int32_t order) {
-  if (!p || order < 0 || (order >> 16) > 64) return DSRG_ERR_INVALID_ARG;
+  if (!p || !split_code_valid(order)) return DSRG_ERR_INVALID_ARG;
   if (p->prec == DSRG_PREC_FP64) return DSRG_OK;
   cudaError_t e = split_set_order(p, order);
   return e == cudaSuccess ? DSRG_OK : cuda_fail(p, e, "item order");

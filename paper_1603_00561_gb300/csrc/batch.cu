@@ -216,8 +216,19 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
     b->tune_class = "n" + std::to_string(nmol) + "-i" + std::to_string((items.size() + 255) / 256 * 256) +
                     "-q" + std::to_string(Qld);
     dsrg::split_schedule(items, cost, b->grid, sched, begin);
+    // the item array is sized for the larger list of the column-halves shape
+    size_t max_items = 0;
+    {
+      std::vector<int4> it2;
+      std::vector<double> c2;
+      for (int m = 0; m < nmol; ++m) {
+        const int kblocks = dsrg::split_plane_qpad(b->plans[m]->z) / dsrg::split_kb_elems(bf16);
+        dsrg::split_item_list(b->plans[m]->z, m, kblocks, it2, c2, 1 << 24);
+      }
+      max_items = it2.size();
+    }
     if (!balloc(b, &b->d_mols, mols.size()) ||
-        !balloc(b, (void**)&b->d_items, sched.size() * sizeof(int4)) ||
+        !balloc(b, (void**)&b->d_items, max_items * sizeof(int4)) ||
         !balloc(b, (void**)&b->d_begin, begin.size() * sizeof(int)) ||
         cudaMemcpy(b->d_mols, mols.data(), mols.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
@@ -254,7 +265,7 @@ cudaError_t batch_set_order(dsrg_batch* b, int order) {
   std::vector<int> begin;
   for (int m = 0; m < b->nmol; ++m) {
     const int kblocks = dsrg::split_plane_qpad(b->plans[m]->z) / dsrg::split_kb_elems(bf16);
-    dsrg::split_item_list(b->plans[m]->z, m, kblocks, items, cost, order & 0xffff);
+    dsrg::split_item_list(b->plans[m]->z, m, kblocks, items, cost, order);
   }
   dsrg::split_schedule(items, cost, b->grid, sched, begin);
   cudaError_t e = cudaMemcpy(b->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
@@ -282,7 +293,7 @@ dsrg_status_t dsrg_batch_autotune(dsrg_batch_t* b, const double* const* B, const
   const std::string key = cache ? batch_key(b, "batch-ccvv-schedule") : std::string();
   if (cache) {
     long long v = -1;
-    if (dsrg::tune_cache_get(cache, key.c_str(), &v) == 1 && v >= 0 && (v >> 16) <= 64) {
+    if (dsrg::tune_cache_get(cache, key.c_str(), &v) == 1 && dsrg::split_code_valid(v)) {
       if (b->user_stream) cudaStreamSynchronize(b->user_stream);
       cudaError_t ec = batch_set_order(b, (int)v);
       if (ec != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(ec));
@@ -311,7 +322,7 @@ dsrg_status_t dsrg_batch_autotune(dsrg_batch_t* b, const double* const* B, const
       if (r == 1) e = cudaEventRecord(e0, st);
       if (e == cudaSuccess)
         e = dsrg::split_launch_ccvv(p0, b->maps, b->d_mols, b->d_items, b->d_begin,
-                                    b->grid, bf16, b->order >> 16);
+                                    b->grid, bf16, b->order);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -341,7 +352,7 @@ int32_t dsrg_batch_item_order(const dsrg_batch_t* b) {
 }
 
 dsrg_status_t dsrg_batch_set_item_order(dsrg_batch_t* b, int32_t order) {
-  if (!b || order < 0 || (order >> 16) > 64) return DSRG_ERR_INVALID_ARG;
+  if (!b || !dsrg::split_code_valid(order)) return DSRG_ERR_INVALID_ARG;
   if (b->prec == DSRG_PREC_FP64) return DSRG_OK;
   if (b->user_stream) cudaStreamSynchronize(b->user_stream);
   cudaError_t e = batch_set_order(b, order);
@@ -414,7 +425,7 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
       e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
       if (e == cudaSuccess)
         e = dsrg::split_launch_ccvv(p0, b->maps, b->d_mols, b->d_items, b->d_begin,
-                                    b->grid, b->prec == DSRG_PREC_BF16X3, b->order >> 16);
+                                    b->grid, b->prec == DSRG_PREC_BF16X3, b->order);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
     // the per-molecule blocks: fork into K branches, molecule m on branch m mod K

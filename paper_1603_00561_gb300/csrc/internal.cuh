@@ -204,18 +204,25 @@ void split_group_rows(const dsrg_plan* p, int g, int* h0, int* h1);
 cudaError_t split_launch_group(dsrg_plan* p, int g);
 cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols, int first, int n,
                              const double* const* eps, const double* s);
+// `code`: the schedule code of the items (its prefetch and shape fields are used)
 cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_mols,
                               const int4* d_items, const int* d_begin, int grid, bool bf16,
-                              int prefetch);
-// items of pairs whose index is not = rank (mod world) are left out
+                              int code);
+// items of pairs whose index is not = rank (mod world) are left out; `code` is a
+// schedule code (its order and column-halves fields are used)
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
-                     std::vector<double>& cost, int order, int rank = 0, int world = 1);
+                     std::vector<double>& cost, int code, int rank = 0, int world = 1);
 // the shard of core pair index k (pairs i <= j in row-major order)
 __host__ __device__ inline bool pair_in_shard(int k, int rank, int world) {
   return world <= 1 || k % world == rank;
 }
 extern const int SPLIT_ORDERS[];
 extern const int N_SPLIT_ORDERS;
+// Schedule code: item order (bits 0-15), L2 prefetch distance in K stages
+// (bits 16-23, at most 64), every virtual tile split into column halves (bit 24).
+bool split_code_valid(long long code);
+int split_code_prefetch(int code);
+bool split_code_halves(int code);
 cudaError_t split_set_order(dsrg_plan* p, int order);
 int split_order(const dsrg_plan* p);
 cudaError_t split_time_ccvv(dsrg_plan* p, int reps, float* ms);

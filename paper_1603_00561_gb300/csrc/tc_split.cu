@@ -132,10 +132,16 @@ struct ItemPlan {
   int nload;            // slots to load: 0 .. nload-1 of the list `load`
   int load[4];          // slot ids to load
   int g1a, g1b, g2a, g2b;
-  int nB;               // MMA N: the columns of virtual tile Bt rounded up to 16
+  int nB;               // MMA N: the item's columns rounded up to 16
+  int ncols;            // the item's valid columns (virtual orbitals of tile Bt from cofs)
+  int cofs;             // first column of the item within tile Bt (0 or 64)
+  int boff;             // byte offset of the B operand rows in an A slot (diagonal tile pairs)
   bool narrow;          // B-only slots (1, 3) of this item load 64 rows (nB <= 64, A != Bt)
 };
 
+// HALVES: the launch's items may be column halves (bits 14-15 of z); without
+// it every item is a whole tile and the column shape folds to constants.
+template <bool HALVES>
 __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const MolDesc** mdp) {
   ItemPlan ip;
   const int4 it = a.items[idx];
@@ -145,13 +151,20 @@ __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const
   ip.i = it.y >> 16;
   ip.j = it.y & 0xffff;
   ip.A = it.z >> 16;
-  ip.Bt = it.z & 0xffff;
+  ip.Bt = it.z & 0x3fff;
+  // column shape (bits 14-15): 0 the whole tile Bt, 1 its columns 0-63, 2 its columns 64-127
+  const int hc = HALVES ? (it.z >> 14) & 3 : 0;
+  ip.cofs = hc == 2 ? 64 : 0;
   ip.slot = it.w;
   ip.p = it.w / md->n_tp;
   ip.two = ip.i != ip.j;
   const bool dt = ip.A == ip.Bt;
-  const int nb = min(TT, md->nV - ip.Bt * TT);
+  const int nb = min(hc == 0 ? TT : TT / 2, md->nV - ip.Bt * TT - ip.cofs);
   ip.nB = (nb + 15) & ~15;
+  ip.ncols = nb;
+  // a diagonal tile pair reads its B operand from the A slots, cofs rows in
+  // (a whole number of 512-byte swizzle atoms)
+  ip.boff = dt ? ip.cofs * KB_BYTES : 0;
   // slots 1 = (j, B) and 3 = (i, B) of an off-diagonal tile pair are read only as
   // B operands (N rows); on a diagonal tile pair every slot is also an A operand
   ip.narrow = !dt && ip.nB <= 64;
@@ -178,9 +191,9 @@ __device__ __forceinline__ ItemPlan plan_item(const SplitArgs& a, int idx, const
 __device__ __forceinline__ int slot_row(const ItemPlan& ip, int slot, int nVpad) {
   switch (slot) {
     case 0: return ip.i * nVpad + ip.A * TT;
-    case 1: return ip.j * nVpad + ip.Bt * TT;
+    case 1: return ip.j * nVpad + ip.Bt * TT + ip.cofs;
     case 2: return ip.j * nVpad + ip.A * TT;
-    default: return ip.i * nVpad + ip.Bt * TT;
+    default: return ip.i * nVpad + ip.Bt * TT + ip.cofs;
   }
 }
 
@@ -200,8 +213,8 @@ __device__ __forceinline__ void ccvv_stage_mmas(uint32_t dx, uint32_t dy, uint32
     const uint32_t off = (uint32_t)((1 - k) * 32);
     const uint64_t a1h = desc_sw64(sb + (ip.g1a * 2 + 0) * SLOT_BYTES + off);
     const uint64_t a1l = desc_sw64(sb + (ip.g1a * 2 + 1) * SLOT_BYTES + off);
-    const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + off);
-    const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + off);
+    const uint64_t b1h = desc_sw64(sb + (ip.g1b * 2 + 0) * SLOT_BYTES + ip.boff + off);
+    const uint64_t b1l = desc_sw64(sb + (ip.g1b * 2 + 1) * SLOT_BYTES + ip.boff + off);
     const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
     tc_mma<BF16>(dx, a1l, b1h, idesc, acc0);
     tc_mma<BF16, 1>(dx, a1h, b1l, idesc, 1u);
@@ -209,8 +222,8 @@ __device__ __forceinline__ void ccvv_stage_mmas(uint32_t dx, uint32_t dy, uint32
     if (ip.two) {
       const uint64_t a2h = desc_sw64(sb + (ip.g2a * 2 + 0) * SLOT_BYTES + off);
       const uint64_t a2l = desc_sw64(sb + (ip.g2a * 2 + 1) * SLOT_BYTES + off);
-      const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + off);
-      const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + off);
+      const uint64_t b2h = desc_sw64(sb + (ip.g2b * 2 + 0) * SLOT_BYTES + ip.boff + off);
+      const uint64_t b2l = desc_sw64(sb + (ip.g2b * 2 + 1) * SLOT_BYTES + ip.boff + off);
       tc_mma<BF16>(dy, a2l, b2h, idesc, acc0);
       tc_mma<BF16, 1>(dy, a2h, b2l, idesc, 1u);
       tc_mma<BF16, 2>(dy, a2h, b2h, idesc, 1u);
@@ -265,8 +278,9 @@ __device__ __forceinline__ void adjoint_chunk(
     double& sacc) {
   if (rok) {
     // the first TAIL_Q auxiliary functions in FP32 round-to-nearest
-    tail_add16(tail_ia, tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
-    if (ip.two) tail_add16(tail_ja, tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
+    tail_add16(tail_ia, tail + (size_t)(ip.j * nVpad + ip.Bt * TT + ip.cofs + c0) * TAIL_Q, xr);
+    if (ip.two)
+      tail_add16(tail_ja, tail + (size_t)(ip.i * nVpad + ip.Bt * TT + ip.cofs + c0) * TAIL_Q, yr);
   }
   float P[16], Qv[16];
   double gd[16];
@@ -354,7 +368,7 @@ __device__ __forceinline__ void adjoint_chunk(
   }
   if (!rok) return;
   const long long lds = a.lds;
-  const int colb = ip.Bt * TT + c0;
+  const int colb = ip.Bt * TT + ip.cofs + c0;
   store_split16(a.s_hi, a.s_lo, (long long)(ip.i * nVpad + arow) * lds + ip.j * nVpad + colb, P);
   if (ip.two)
     store_split16(a.s_hi, a.s_lo, (long long)(ip.j * nVpad + arow) * lds + ip.i * nVpad + colb, Qv);
@@ -378,7 +392,7 @@ __device__ __forceinline__ void adjoint_chunk(
   }
 }
 
-template <bool BF16, bool ADJ>
+template <bool BF16, bool ADJ, bool HALVES>
 __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     ccvv_split_kernel(const __grid_constant__ CUtensorMap map_hi,
                       const __grid_constant__ CUtensorMap map_lo,
@@ -396,7 +410,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   double* sEps = (double*)(smem + STAGES * STAGE_BYTES + 256);
   double* sAlpha = sEps + TT;
-  double* sRed = sAlpha + TT;
+  double* sRed = sAlpha + TT;                 // [EPI_WARPS] warp sums
   float* sEpsF = (float*)(sRed + EPI_WARPS);
   float* sCr = sEpsF + TT;  // [TT/16][2]: min, max of e over the valid columns of each 16-column chunk
   unsigned* sCnt = (unsigned*)(sCr + 2 * (TT / 16));  // [EPI_WARPS][3] epilogue blocks by regulator path
@@ -447,13 +461,58 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       constexpr int KE = KB_BYTES / (BF16 ? 2 : 4);
       for (int idx = it0; ok && idx < it1; ++idx) {
         const MolDesc* md;
-        const ItemPlan ip = plan_item(a, idx, &md);
+        const ItemPlan ip = plan_item<HALVES>(a, idx, &md);
         const int kblocks = md->kblocks, row0 = md->row0, nVpad = md->nVpad;
+        if (a.prefetch == 0) {
+          // The common path. The producer thread is close to the critical path (8
+          // TMA issues per stage against 12 MMAs), so everything that does not
+          // change along K is set up once per item: rows, maps, shared-memory
+          // offsets, L2 policies of the loaded slots and the stage's bytes.
+          const int nl = ip.nload;
+          int srow[4];
+          uint32_t soff[4];
+          const CUtensorMap* mh[4];
+          const CUtensorMap* ml[4];
+          uint32_t bytes = 0;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const int sl = l < nl ? ip.load[l] : 0;
+            // B-only slots (odd ids) of a narrow tile: 64 rows
+            const bool half = ip.narrow && (sl & 1);
+            srow[l] = row0 + slot_row(ip, sl, nVpad);
+            soff[l] = (uint32_t)(sl * 2 * SLOT_BYTES);
+            mh[l] = half ? &map_hi64 : &map_hi;
+            ml[l] = half ? &map_lo64 : &map_lo;
+            if (l < nl) bytes += half ? SLOT_BYTES : 2 * SLOT_BYTES;
+          }
+          const int kq0 = md->kq0 + (kblocks - 1) * KE;
+          for (int kb = 0; kb < kblocks; ++kb) {
+            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.status)) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = tiles + stage * STAGE_BYTES;
+            mbar_expect_tx(&full[stage], bytes);
+            const int kq = kq0 - kb * KE;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+              if (l >= nl) break;
+              tma_load_2d(st + soff[l], mh[l], &full[stage], kq, srow[l]);
+              tma_load_2d(st + soff[l] + SLOT_BYTES, ml[l], &full[stage], kq, srow[l]);
+            }
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          continue;
+        }
+        // with L2 prefetch (a schedule option the autotuner has never kept)
         // the next item of this CTA, for prefetches that run past this one
         const MolDesc* mdn = md;
         ItemPlan ipn = ip;
         const bool has_next = idx + 1 < it1;
-        if (has_next) ipn = plan_item(a, idx + 1, &mdn);
+        if (has_next) ipn = plan_item<HALVES>(a, idx + 1, &mdn);
         for (int kb = 0; kb < kblocks; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.status)) {
             ok = false;
@@ -468,7 +527,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           for (int l = 0; l < ip.nload; ++l) {
             const int sl = ip.load[l];
             const int row = row0 + slot_row(ip, sl, nVpad);
-            // B-only slots (odd ids) of a narrow last tile: the first 64 rows
+            // B-only slots (odd ids) of a narrow tile: 64 rows
             const bool half = ip.narrow && (sl & 1);
             tma_load_2d(st + (sl * 2 + 0) * SLOT_BYTES, half ? &map_hi64 : &map_hi, &full[stage], kq,
                         row);
@@ -526,7 +585,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       bool issued = false;
       for (int idx = it0; ok && idx < it1; ++idx) {
         const MolDesc* md;
-        const ItemPlan ip = plan_item(a, idx, &md);
+        const ItemPlan ip = plan_item<HALVES>(a, idx, &md);
         const int kblocks = md->kblocks;
         if (!mbar_wait(&tempty[tbuf], tphase ^ 1u, abort_flag, a.status)) {
           ok = false;
@@ -570,7 +629,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     const int et = threadIdx.x - 64;           // 0..255
     const int quarter = warp & 3;              // TMEM lanes this warp may access
     const int row = quarter * 32 + lane;       // tile row held by this thread
-    const int cbeg = ((warp - 2) >> 2) * 64;   // this warp's half of the columns
+    const int wh = (warp - 2) >> 2;            // this warp's half of the item's columns
     int tbuf = 0;
     uint32_t tphase = 0;
     // 32-row x 16-column blocks of this warp by regulator path (lane 0 counts
@@ -578,7 +637,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
     if (et < 3 * EPI_WARPS) sCnt[et] = 0u;
     for (int idx = it0; idx < it1; ++idx) {
       const MolDesc* md;
-      const ItemPlan ip = plan_item(a, idx, &md);
+      const ItemPlan ip = plan_item<HALVES>(a, idx, &md);
       const int nV = md->nV, nVpad = md->nVpad;
       const int ve = md->nC + md->nA;
       const double* eps = md->eps;
@@ -587,8 +646,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       const double* alpha = md->alpha + (size_t)ip.p * nVpad;
       const bool factorisable = pi[2] != 0.0;
       named_bar(1, 32 * EPI_WARPS);
+      // warp half wh takes the item's columns 64 wh .. 64 wh + 63 (a half item: half 0 alone)
+      const int cbeg = wh * 64;
       if (et < TT) {
-        const int b = ip.Bt * TT + et;
+        const int b = ip.Bt * TT + ip.cofs + et;
         const double eb = (b < nV) ? eps[ve + b] : 0.0;
         sEps[et] = eb;
         sEpsF[et] = (float)eb;
@@ -598,7 +659,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       if (et < TT / 16) {
         // range of e over the valid columns of chunk et (FP32: it only picks a path)
         float lo = 3.0e38f, hi = -3.0e38f;
-        for (int c = 16 * et; c < 16 * et + 16 && ip.Bt * TT + c < nV; ++c) {
+        for (int c = 16 * et; c < 16 * et + 16 && c < ip.ncols; ++c) {
           lo = fminf(lo, sEpsF[c]);
           hi = fmaxf(hi, sEpsF[c]);
         }
@@ -612,10 +673,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
       const double ca = E - ea;
       const float caf = (float)ca;
       const double ha = rok ? beta * alpha[arow] : 0.0;
-      const int ncols = min(TT, nV - ip.Bt * TT);
-      const int cend = min(cbeg + 64, ncols);
+      const int cend = min(cbeg + 64, ip.ncols);
       const double s = md->s;
-      const double* taucol = md->tau + (size_t)(ip.Bt * TT) * nVpad + arow;
+      const double* taucol = md->tau + (size_t)(ip.Bt * TT + ip.cofs) * nVpad + arow;
       const float* tail_ia = md->tail + (size_t)(ip.i * nVpad + arow) * TAIL_Q;
       const float* tail_ja = md->tail + (size_t)(ip.j * nVpad + arow) * TAIL_Q;
       // range of E - e_a over this warp's valid rows (FP32)
@@ -664,9 +724,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           if (!rok) continue;
           // the first TAIL_Q auxiliary functions, the largest terms, in FP32
           // round-to-nearest (the tensor cores took the rest)
-          tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + c0) * TAIL_Q, xr);
+          tail_add16(tail_ia, md->tail + (size_t)(ip.j * nVpad + ip.Bt * TT + ip.cofs + c0) * TAIL_Q,
+                     xr);
           if (ip.two)
-            tail_add16(tail_ja, md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + c0) * TAIL_Q, yr);
+            tail_add16(tail_ja,
+                       md->tail + (size_t)(ip.i * nVpad + ip.Bt * TT + ip.cofs + c0) * TAIL_Q, yr);
           if (pth == 0) {
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -737,11 +799,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
           if (et < TT) {
             const int ra = ip.A * TT + et;
             if (ra < nV) atomicAdd(&a.deps[ve + ra], -w * (sRowAcc[et] + sRowAcc[TT + et]));
-            const int hb = et >> 6, cc = et & 63;
-            double t = 0.0;
-            for (int q = 0; q < 4; ++q) t += sColAcc[(4 * hb + q) * 64 + cc];
-            const int cb = ip.Bt * TT + et;
-            if (cb < nV) atomicAdd(&a.deps[ve + cb], -w * t);
+            // item column et: warp half et / 64, position et % 64 in its warps' sums
+            if (et < ip.ncols) {
+              const int hb = et >> 6, cc = et & 63;
+              double t = 0.0;
+              for (int q = 0; q < 4; ++q) t += sColAcc[(4 * hb + q) * 64 + cc];
+              atomicAdd(&a.deps[ve + ip.Bt * TT + ip.cofs + et], -w * t);
+            }
           } else if (et == TT) {
             double tp = 0.0, tsum = 0.0;
             for (int k = 0; k < EPI_WARPS; ++k) {
@@ -757,16 +821,22 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 1)
         named_bar(1, 32 * EPI_WARPS);
         continue;
       }
-      // fixed-order CTA sum of the item's contribution
+      // fixed-order sums of the item's 64-column halves: warp butterfly, then the
+      // four warps of each warp half in index order. A half item is processed by
+      // warp half 0 alone, so the sum of a tile's column half does not depend on
+      // whether the tile ran whole or as halves. Partial slot 2 * (pair tile-pair
+      // index) + (column half of the tile).
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) sRed[warp - 2] = acc;
       named_bar(1, 32 * EPI_WARPS);
       if (et == 0) {
-        if (pi[2] == 0.0) atomicAdd(&a.counts[DSRG_COUNT_CCVV_UNFACTORABLE], 1ull);
+        if (pi[2] == 0.0 && ip.cofs == 0) atomicAdd(&a.counts[DSRG_COUNT_CCVV_UNFACTORABLE], 1ull);
         const double w = (ip.two ? 2.0 : 1.0) * (ip.A < ip.Bt ? 2.0 : 1.0);
-        double t = 0.0;
-        for (int k = 0; k < EPI_WARPS; ++k) t += sRed[k];
-        md->partials[ip.slot] = ok ? w * t : 0.0;
+        const double t0 = sRed[0] + sRed[1] + sRed[2] + sRed[3];
+        const double t1 = sRed[4] + sRed[5] + sRed[6] + sRed[7];
+        double* part = md->partials + 2 * ip.slot;
+        part[ip.cofs / 64] = ok ? w * t0 : 0.0;
+        if (!HALVES) part[1] = ok ? w * t1 : 0.0;
       }
       // after an abort the loop keeps running without waits, so that all
       // epilogue warps keep meeting at the same named barriers
@@ -984,9 +1054,12 @@ bool split_make_ccvv_maps(CcvvMaps* m, void* hi, void* lo, bool bf16, long long 
          split_make_map(&m->lo64, lo, bf16, rows, Qld, KB_BYTES, TT / 2);
 }
 
+// Partial slots of the CCVV energy: one per 64-column half of every (pair,
+// tile pair), 2 per tile pair, so that a half's sum is the same whether its
+// tile runs whole or as column halves.
 int split_ccvv_blocks(const dsrg_plan* p) {
   const int nT = (p->z.nV + TT - 1) / TT;
-  return p->n_pairs * (nT * (nT + 1) / 2);
+  return p->n_pairs * (nT * (nT + 1) / 2) * 2;
 }
 
 // Rows of one molecule's planes: (h, e) for every hole h and padded virtual e,
@@ -1034,19 +1107,36 @@ void split_schedule(const std::vector<int4>& items, const std::vector<double>& c
 // Consecutive items run at the same time on different SMs, so the order sets
 // which operand tiles share the L2 at any moment.
 void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& items,
-                     std::vector<double>& cost, int order, int rank, int world) {
+                     std::vector<double>& cost, int code, int rank, int world) {
   const int nT = (z.nV + TT - 1) / TT, nC = z.nC;
   const int n_tp = nT * (nT + 1) / 2;
+  const int order = code & 0xffff;
+  const bool halves = split_code_halves(code);
   auto pair_index = [&](int i, int j) { return i * nC - i * (i - 1) / 2 + (j - i); };
   auto tp_index = [&](int A, int B) { return A * nT - A * (A - 1) / 2 + (B - A); };
   auto push = [&](int i, int j, int A, int B) {
     if (!pair_in_shard(pair_index(i, j), rank, world)) return;
-    items.push_back(make_int4(mol, (i << 16) | j, (A << 16) | B, pair_index(i, j) * n_tp + tp_index(A, B)));
+    const int y = (i << 16) | j;
+    const int slot = pair_index(i, j) * n_tp + tp_index(A, B);
     // MMA work: one GEMM for i = j, else two; plus a fixed share for the
     // epilogue. The narrower last tile is not weighted down: equal costs keep
     // the deal round-robin, so that the items running at the same time share
     // operand slabs in L2 (weighting it by width measured 7% slower)
-    cost.push_back((double)kblocks * (i == j ? 1.0 : 2.0) + 24.0);
+    const double c = ((double)kblocks * (i == j ? 1.0 : 2.0) + 24.0) * (halves ? 0.5 : 1.0);
+    // column shape in bits 14-15 of z (halves only): a tile of more than 64
+    // columns as two half items, a narrower one as one
+    const int width = z.nV - B * TT < TT ? z.nV - B * TT : TT;
+    if (halves) {
+      items.push_back(make_int4(mol, y, (A << 16) | (1 << 14) | B, slot));
+      cost.push_back(c);
+      if (width > TT / 2) {
+        items.push_back(make_int4(mol, y, (A << 16) | (2 << 14) | B, slot));
+        cost.push_back(c);
+      }
+    } else {
+      items.push_back(make_int4(mol, y, (A << 16) | B, slot));
+      cost.push_back(c);
+    }
   };
   const int G = order >> 1;
   if (G <= 0) {
@@ -1075,11 +1165,16 @@ void split_item_list(const Sizes& z, int mol, int kblocks, std::vector<int4>& it
 }
 
 // Schedule codes the autotuner tries: item order (low 16 bits, pair-major
-// first) and L2 prefetch distance in K stages (bits 16 and up).
+// first), L2 prefetch distance in K stages (bits 16-23) and column halves
+// (bit 24; without prefetch only: prefetching has never paid).
 #define DSRG_ORDERS(PF) (PF << 16), (PF << 16) | (2 << 1), (PF << 16) | (4 << 1), (PF << 16) | (8 << 1), \
     (PF << 16) | (4 << 1) | 1, (PF << 16) | (8 << 1) | 1, (PF << 16) | (64 << 1)
-const int SPLIT_ORDERS[] = {DSRG_ORDERS(0), DSRG_ORDERS(4), DSRG_ORDERS(12)};
+const int SPLIT_ORDERS[] = {DSRG_ORDERS(0), DSRG_ORDERS(1 << 8), DSRG_ORDERS(4), DSRG_ORDERS(12)};
 #undef DSRG_ORDERS
+
+bool split_code_valid(long long c) { return c >= 0 && (c >> 25) == 0 && ((c >> 16) & 0xff) <= 64; }
+int split_code_prefetch(int c) { return (c >> 16) & 0xff; }
+bool split_code_halves(int c) { return ((c >> 24) & 1) != 0; }
 const int N_SPLIT_ORDERS = sizeof(SPLIT_ORDERS) / sizeof(SPLIT_ORDERS[0]);
 
 bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
@@ -1145,7 +1240,8 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
   std::vector<int4> items, sched;
   std::vector<double> cost;
   std::vector<int> begin;
-  split_item_list(z, 0, md.kblocks, items, cost, 0);
+  // sized for the larger item list (every tile in column halves)
+  split_item_list(z, 0, md.kblocks, items, cost, 1 << 24);
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
   w->grid = (int)items.size() < nsm ? (int)items.size() : nsm;
@@ -1161,7 +1257,7 @@ cudaError_t split_set_order(dsrg_plan* p, int order) {
   std::vector<int4> items, sched;
   std::vector<double> cost;
   std::vector<int> begin;
-  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, order & 0xffff, p->shard_rank,
+  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, order, p->shard_rank,
                   p->shard_world);
   split_schedule(items, cost, w->grid, sched, begin);
   cudaError_t e = cudaMemcpy(w->d_items, sched.data(), sched.size() * sizeof(int4), cudaMemcpyHostToDevice);
@@ -1198,7 +1294,9 @@ bool split_alloc_groups(dsrg_plan* p, const std::vector<int>& bounds) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device);
   std::vector<int4> items;
   std::vector<double> cost;
-  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, 0, p->shard_rank, p->shard_world);
+  // group sizes for the larger item list (every tile in column halves)
+  split_item_list(p->z, 0, w->Qpad / w->kb_elems, items, cost, 1 << 24, p->shard_rank,
+                  p->shard_world);
   w->groups.resize(ngroups);
   for (int g = 0; g < ngroups; ++g) {
     SplitWs::Group& G = w->groups[g];
@@ -1231,7 +1329,7 @@ cudaError_t split_launch_group(dsrg_plan* p, int g) {
   const SplitWs::Group& G = w->groups[g];
   if (G.n == 0) return cudaSuccess;
   return split_launch_ccvv(p, w->cmaps, w->d_mol, G.d_items, G.d_begin, G.grid,
-                           p->prec == DSRG_PREC_BF16X3, w->order >> 16);
+                           p->prec == DSRG_PREC_BF16X3, w->order);
 }
 
 int split_order(const dsrg_plan* p) { return p->split ? p->split->order : -1; }
@@ -1251,7 +1349,7 @@ cudaError_t split_time_ccvv(dsrg_plan* p, int reps, float* ms) {
   e = cudaEventRecord(e0, p->stream);
   for (int r = 0; e == cudaSuccess && r < reps; ++r)
     e = split_launch_ccvv(p, w->cmaps, w->d_mol, w->d_items, w->d_begin, w->grid, bf16,
-                          w->order >> 16);
+                          w->order);
   if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   if (e == cudaSuccess) {
@@ -1384,9 +1482,19 @@ cudaError_t split_set_inputs(dsrg_plan* p, void* d_mols_v, int first, int n,
   return cudaSuccess;
 }
 
+template <bool BF16, bool ADJ, bool HALVES>
+static void launch_ccvv_instance(dsrg_plan* p, const CcvvMaps& m, int grid, size_t sm,
+                                 const SplitArgs& a) {
+  raise_smem_limit((const void*)ccvv_split_kernel<BF16, ADJ, HALVES>, sm);
+  ccvv_split_kernel<BF16, ADJ, HALVES><<<grid, SPLIT_THREADS, sm, p->stream>>>(m.hi, m.lo, m.hi64,
+                                                                              m.lo64, a);
+}
+
 cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_mols,
                               const int4* d_items, const int* d_begin, int grid, bool bf16,
-                              int prefetch) {
+                              int code) {
+  const int prefetch = split_code_prefetch(code);
+  const bool halves = split_code_halves(code);
   SplitArgs a;
   a.mols = (const MolDesc*)d_mols;
   a.items = d_items;
@@ -1398,15 +1506,14 @@ cudaError_t split_launch_ccvv(dsrg_plan* p, const CcvvMaps& maps, const void* d_
   a.lds = 0;
   a.deps = a.ds = nullptr;
   const size_t sm = split_smem_bytes();
-  if (bf16) {
-    raise_smem_limit((const void*)ccvv_split_kernel<true, false>, sm);
-    ccvv_split_kernel<true, false><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo,
-                                                                           maps.hi64, maps.lo64, a);
-  } else {
-    raise_smem_limit((const void*)ccvv_split_kernel<false, false>, sm);
-    ccvv_split_kernel<false, false><<<grid, SPLIT_THREADS, sm, p->stream>>>(maps.hi, maps.lo,
-                                                                            maps.hi64, maps.lo64, a);
-  }
+  if (bf16 && halves)
+    launch_ccvv_instance<true, false, true>(p, maps, grid, sm, a);
+  else if (bf16)
+    launch_ccvv_instance<true, false, false>(p, maps, grid, sm, a);
+  else if (halves)
+    launch_ccvv_instance<false, false, true>(p, maps, grid, sm, a);
+  else
+    launch_ccvv_instance<false, false, false>(p, maps, grid, sm, a);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
@@ -1472,10 +1579,10 @@ cudaError_t split_launch_ccvv_adjoint(dsrg_plan* p, const double* B, const doubl
   a.deps = deps;
   a.ds = ds;
   const size_t sm = split_smem_bytes() + (EPI_WARPS * 64 + 2 * TT + 2 * EPI_WARPS) * 8;
-  const CcvvMaps& m = w->adj_maps;
-  raise_smem_limit((const void*)ccvv_split_kernel<false, true>, sm);
-  ccvv_split_kernel<false, true><<<w->grid, SPLIT_THREADS, sm, p->stream>>>(m.hi, m.lo, m.hi64,
-                                                                            m.lo64, a);
+  if (split_code_halves(w->order))
+    launch_ccvv_instance<false, true, true>(p, w->adj_maps, w->grid, sm, a);
+  else
+    launch_ccvv_instance<false, true, false>(p, w->adj_maps, w->grid, sm, a);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
@@ -1491,7 +1598,7 @@ cudaError_t launch_split_ccvv(dsrg_plan* p, const double* B, const double* eps, 
   if (e != cudaSuccess) return e;
   if ((e = split_prepare_single(p, eps, s)) != cudaSuccess) return e;
   return split_launch_ccvv(p, w->cmaps, w->d_mol, w->d_items,
-                           w->d_begin, w->grid, p->prec == DSRG_PREC_BF16X3, w->order >> 16);
+                           w->d_begin, w->grid, p->prec == DSRG_PREC_BF16X3, w->order);
 }
 
 }  // namespace dsrg

@@ -14,7 +14,8 @@ from dsrg_synth import batch_sizes, make_problem
 pytestmark = pytest.mark.gpu
 
 ORDERS = {0, 2 << 1, 4 << 1, 8 << 1, (4 << 1) | 1, (8 << 1) | 1, 64 << 1}
-CANDIDATES = {(pf << 16) | o for pf in (0, 4, 12) for o in ORDERS}
+# prefetch 0, 4 or 12 K stages; without prefetch also every tile in column halves (bit 24)
+CANDIDATES = {(pf << 16) | o for pf in (0, 4, 12, 1 << 8) for o in ORDERS}
 
 
 @pytest.fixture(scope="module")
