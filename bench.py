@@ -48,20 +48,16 @@ NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # keyed by (workload, precision, item order); summaries under profiles/. Any
 # other combination, or a kernel changed since the capture, reports null.
 TRAFFIC = {
-    ("naphthyne-v5z-1240", "bf16x3", 0): 12917796992,
-    ("naphthyne-v5z-1240", "bf16x3", 4): 7441687488,
-    ("naphthyne-v5z-1240", "bf16x3", 8): 14148086656,
-    ("naphthyne-v5z-1240", "bf16x3", 16): 18160743488,
-    ("naphthyne-v5z-1240", "bf16x3", 9): 10657107840,
-    ("naphthyne-v5z-1240", "bf16x3", 17): 12629118592,
-    ("naphthyne-v5z-1240", "bf16x3", 128): 20207734336,
-    ("naphthyne-v5z-1240", "bf16x3", 262144): 30338915328,
-    ("naphthyne-v5z-1240", "bf16x3", 262148): 37821449728,
-    ("naphthyne-v5z-1240", "bf16x3", 262152): 44162787776,
-    ("naphthyne-v5z-1240", "bf16x3", 262160): 49224539776,
-    ("naphthyne-v5z-1240", "bf16x3", 262153): 39407163776,
-    ("naphthyne-v5z-1240", "bf16x3", 262161): 38555878336,
-    ("naphthyne-v5z-1240", "bf16x3", 262272): 35005312896,
+    # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the current CCVV kernel,
+    # whole tiles without prefetch (profiles/ccvv_dram_per_order_naphthyne-v5z-1240.md); other
+    # codes report null
+    ("naphthyne-v5z-1240", "bf16x3", 0): 18808265472 + 3898368,
+    ("naphthyne-v5z-1240", "bf16x3", 4): 9346629376 + 3872768,
+    ("naphthyne-v5z-1240", "bf16x3", 8): 14072587776 + 3752960,
+    ("naphthyne-v5z-1240", "bf16x3", 16): 19147768320 + 3742464,
+    ("naphthyne-v5z-1240", "bf16x3", 9): 15875443200 + 3923712,
+    ("naphthyne-v5z-1240", "bf16x3", 17): 14867894528 + 3962880,
+    ("naphthyne-v5z-1240", "bf16x3", 128): 20477330176 + 3740928,
 }
 
 

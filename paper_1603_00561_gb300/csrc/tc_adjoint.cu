@@ -15,9 +15,10 @@
 // (three products, as the energy). Its K index runs over plane rows whose
 // terms do not decay, so the truncating FP32 accumulator of the tensor cores
 // must not carry the whole sum: every K stage (32 values) is its own
-// accumulation in TMEM, which the epilogue adds in FP32 round-to-nearest into
-// registers; every AG_L1 stages the register sums go into a second FP32 sum
-// in shared memory, and the two are added in FP64 at the end.
+// accumulation in TMEM every AG_CH = 2 stages (64 values, 12 MMAs), which the
+// epilogue adds in FP32 round-to-nearest into registers; every AG_L1 of those
+// the register sums go into a second FP32 sum in shared memory, and the two
+// are added in FP64 at the end.
 //
 // Roles (one CTA per SM, persistent): warp 0 TMA producer, warp 1 TMEM
 // allocator and MMA issuer, warps 2-9 epilogue (two warps per TMEM lane
@@ -39,8 +40,9 @@ constexpr int AG_TILE = AG_BM * AG_KB;        // 8 KB: one operand tile of one p
 constexpr int AG_STAGE_BYTES = 4 * AG_TILE;   // S hi, S lo, B^T hi, B^T lo
 constexpr int AG_THREADS = 320;
 constexpr int AG_EPI = 8;
-constexpr int AG_NBUF = 4;                    // TMEM accumulators of one K stage each
-constexpr int AG_L1 = 16;                     // stages summed in registers before the shared-memory sum
+constexpr int AG_NBUF = 4;                    // TMEM accumulators
+constexpr int AG_CH = 2;                      // K stages per TMEM accumulation (12 MMAs)
+constexpr int AG_L1 = 16;                     // accumulations summed in registers before the shared-memory sum
 constexpr uint32_t AG_TMEM_COLS = AG_NBUF * AG_BN;
 constexpr int AG_BAND = 12;                   // m tiles per band of the item order
 
@@ -295,7 +297,8 @@ __global__ void __launch_bounds__(AG_THREADS, 1)
       bool ok = true, issued = false;
       for (int it = blockIdx.x; ok && it < n_items; it += gridDim.x) {
         for (int kb = 0; kb < g.kblocks; ++kb) {
-          if (!mbar_wait(&tempty[tb], tphase ^ 1u, abort_flag, g.status) ||
+          const int sub = kb % AG_CH;  // stage within the TMEM accumulation
+          if ((sub == 0 && !mbar_wait(&tempty[tb], tphase ^ 1u, abort_flag, g.status)) ||
               !mbar_wait(&full[stage], phase, abort_flag, g.status)) {
             ok = false;
             break;
@@ -309,21 +312,23 @@ __global__ void __launch_bounds__(AG_THREADS, 1)
             const uint64_t ah = desc_sw64(sa + off), al = desc_sw64(sa + AG_TILE + off);
             const uint64_t bh = desc_sw64(sa + 2 * AG_TILE + off);
             const uint64_t bl = desc_sw64(sa + 3 * AG_TILE + off);
-            // a fresh accumulation per stage: lo.hi, hi.lo (keeps A), hi.hi (reuses it)
-            tc_mma<true>(d, al, bh, idesc, k > 0 ? 1u : 0u);
+            // a fresh accumulation every AG_CH stages: lo.hi, hi.lo (keeps A), hi.hi (reuses it)
+            tc_mma<true>(d, al, bh, idesc, (sub > 0 || k > 0) ? 1u : 0u);
             tc_mma<true, 1>(d, ah, bl, idesc, 1u);
             tc_mma<true, 2>(d, ah, bh, idesc, 1u);
           }
           issued = true;
           tc_commit(&empty[stage]);
-          tc_commit(&tfull[tb]);
           if (++stage == AG_STAGES) {
             stage = 0;
             phase ^= 1u;
           }
-          if (++tb == AG_NBUF) {
-            tb = 0;
-            tphase ^= 1u;
+          if (sub == AG_CH - 1) {
+            tc_commit(&tfull[tb]);
+            if (++tb == AG_NBUF) {
+              tb = 0;
+              tphase ^= 1u;
+            }
           }
         }
       }
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(AG_THREADS, 1)
         sL2[c * 256 + et] = 0.f;
       }
       int nl1 = 0;
-      for (int kb = 0; kb < g.kblocks; ++kb) {
+      for (int kc = 0; kc < g.kblocks / AG_CH; ++kc) {
         if (ok) ok = mbar_wait(&tfull[tb], tphase, abort_flag, g.status);
         tc_fence_after();
         if (ok) {
@@ -502,7 +507,8 @@ cudaError_t tc_adj_assemble(dsrg_plan* p, const double* B, double* dB) {
   AdjGemmArgs g;
   g.m_tiles = w->m_tiles;
   g.n_tiles = w->n_tiles;
-  g.kblocks = w->lds / (AG_KB / 2);
+  g.kblocks = w->lds / (AG_KB / 2);  // lds is a multiple of 64: an even number of stages
+  if (g.kblocks % AG_CH != 0) return cudaErrorInvalidValue;
   g.Q = z.Q;
   g.nH = z.nH;
   g.nA = z.nA;
