@@ -215,8 +215,8 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t *batch, const double *const
 /* Concurrent branches of the per-molecule blocks (CAVV, CCAV, active block and
  * the reductions of each molecule, which do not depend on each other): after
  * the batched CCVV launch the graph forks into K branches, molecule m on
- * branch m mod K, and joins them at the end. K is 1, 2 or 4 and at most
- * min(nmol rounded down to a power of 2, 4) (each branch owns a GEMM output
+ * branch m mod K, and joins them at the end. K is 1, 2, 4 or 8 and at most
+ * min(nmol rounded down to a power of 2, 8) (each branch owns a GEMM output
  * buffer, allocated with the plan); the default is that maximum. Setting a new
  * K waits for the batch's stream and makes the next call capture a new graph.
  * The energies do not depend on K. The autotuner times `reps` replays of the

@@ -20,11 +20,11 @@
 
 #include "internal.cuh"
 
-constexpr int BATCH_MAX_BRANCHES = 4;
+constexpr int BATCH_MAX_BRANCHES = 8;
 
 struct dsrg_batch {
   int nmol = 0;
-  int branches = 1;      // concurrent branches of the per-molecule blocks (1, 2 or 4)
+  int branches = 1;      // concurrent branches of the per-molecule blocks (1, 2, 4 or 8)
   int max_branches = 1;  // branches the GEMM output buffers allow (a power of 2)
   cudaStream_t side[BATCH_MAX_BRANCHES] = {};
   cudaEvent_t ev_fork = nullptr;
@@ -114,7 +114,8 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
     delete b;
     return DSRG_ERR_CUDA;
   }
-  b->max_branches = nmol >= 4 ? 4 : (nmol >= 2 ? 2 : 1);
+  b->max_branches = 1;
+  while (b->max_branches * 2 <= BATCH_MAX_BRANCHES && b->max_branches * 2 <= nmol) b->max_branches *= 2;
   b->branches = b->max_branches;
   bool streams_ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; streams_ok && k < b->max_branches; ++k)
@@ -475,7 +476,7 @@ int32_t dsrg_batch_launch_count(const dsrg_batch_t* b) { return b ? b->launches 
 int32_t dsrg_batch_branches(const dsrg_batch_t* b) { return b ? b->branches : -1; }
 
 dsrg_status_t dsrg_batch_set_branches(dsrg_batch_t* b, int32_t k) {
-  if (!b || (k != 1 && k != 2 && k != 4) || k > b->max_branches) return DSRG_ERR_INVALID_ARG;
+  if (!b || (k != 1 && k != 2 && k != 4 && k != 8) || k > b->max_branches) return DSRG_ERR_INVALID_ARG;
   if (k == b->branches) return DSRG_OK;
   if (b->user_stream) cudaStreamSynchronize(b->user_stream);
   // the next call captures a new graph
@@ -499,7 +500,7 @@ dsrg_status_t dsrg_batch_autotune_branches(dsrg_batch_t* b, const double* const*
   const std::string key = cache ? batch_key(b, "batch-branches") : std::string();
   if (cache) {
     long long v = -1;
-    if (dsrg::tune_cache_get(cache, key.c_str(), &v) == 1 && (v == 1 || v == 2 || v == 4) &&
+    if (dsrg::tune_cache_get(cache, key.c_str(), &v) == 1 && (v == 1 || v == 2 || v == 4 || v == 8) &&
         v <= b->max_branches) {
       dsrg_status_t rc = dsrg_batch_set_branches(b, (int32_t)v);
       if (rc == DSRG_OK && chosen) *chosen = (int32_t)v;

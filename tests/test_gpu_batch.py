@@ -90,7 +90,7 @@ def test_batch_uneven_recipe_against_oracle(pk):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp64"])
 def test_branches_do_not_change_the_energies(pk, prec):
-    """The per-molecule blocks forked into 1, 2 or 4 concurrent graph branches
+    """The per-molecule blocks forked into 1, 2 or 4 (of at most 8) concurrent graph branches
     (molecule m on branch m mod K, one GEMM output buffer per branch) give the
     same energies bit for bit; the branch autotuner keeps an allowed K."""
     mols = _mols(SPECS)
