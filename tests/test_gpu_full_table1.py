@@ -80,7 +80,7 @@ def test_energy_with_lambda3_and_f1(pk, prec, nC, nA, nV, Q, s, seed):
         assert ref["terms"]["J"] != 0.0 and ref["terms"]["K"] != 0.0
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("nC,nA,nV,Q,s,seed", [CASES[0], CASES[1], CASES[3]])
 def test_gradient_with_lambda3_and_f1(pk, prec, nC, nA, nV, Q, s, seed):
     p = make_problem(nC, nA, nV, Q, s=s, seed=seed, with_lambda3=nA > 0, with_f1=True)

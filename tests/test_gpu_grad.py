@@ -40,7 +40,7 @@ SMALL = [(3, 2, 20, 30, 0.5, 0), (4, 1, 33, 17, 0.9, 1), (2, 3, 40, 25, 0.3, 2),
          (2, 5, 12, 10, 0.7, 4), (10, 4, 60, 200, 0.5, 0)]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("nC,nA,nV,Q,s,seed", SMALL)
 def test_grad_matches_oracle_autograd(pk, prec, nC, nA, nV, Q, s, seed):
     p = make_problem(nC, nA, nV, Q, s=s, seed=seed)
@@ -123,22 +123,23 @@ def test_grad_requires_flag(pk):
         plan.energy_grad(*pk.to_device(p), p.s)
 
 
-def test_split_grad_against_fp64_plan_vtz(pk):
-    """cc-pVTZ size: the gradient of a BF16x3 plan (tensor-core recompute and
+@pytest.mark.parametrize("split", ["bf16x3", "tf32x3"])
+def test_split_grad_against_fp64_plan_vtz(pk, split):
+    """cc-pVTZ size: the gradient of a split plan (tensor-core recompute and
     assembly) against the FP64 plan's, normalised by the largest entry of each
     array, within the 1e-6 gradient bar."""
     p = make_problem(**CONFIGS["naphthyne-vtz-398"])
     dev = pk.to_device(p)
     res = {}
-    for prec in ("fp64", "bf16x3"):
+    for prec in ("fp64", split):
         plan = pk.Plan(p.ncore, p.nactive, p.nvirt, p.naux, precision=prec, grad=True)
         out, dB, de, ds = plan.energy_grad(*dev, p.s)
         plan.sync()
         res[prec] = (dB.cpu().numpy(), de.cpu().numpy(), float(ds.cpu()[0]))
         plan.close()
-    (b64, e64, s64), (b32, e32, s32) = res["fp64"], res["bf16x3"]
+    (b64, e64, s64), (b32, e32, s32) = res["fp64"], res[split]
     errB = np.abs(b32 - b64).max() / np.abs(b64).max()
     erre = np.abs(e32 - e64).max() / np.abs(e64).max()
     errs = abs(s32 - s64) / abs(s64)
-    print("vtz split vs fp64 gradient: dB %.2e deps %.2e ds %.2e" % (errB, erre, errs))
+    print("vtz %s vs fp64 gradient: dB %.2e deps %.2e ds %.2e" % (split, errB, erre, errs))
     assert errB < 1e-6 and erre < 1e-6 and errs < 1e-6

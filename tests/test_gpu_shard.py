@@ -22,7 +22,7 @@ def pk():
     return pk
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("world", [2, 3])
 def test_shards_sum_to_the_molecule(pk, prec, world):
     p = make_problem(7, 2, 150, 80, s=0.5, seed=51)
