@@ -115,25 +115,34 @@ def test_split_vtz_against_fp64_path(pk, prec):
         assert r <= SPLIT_BAR, k
 
 
+_V5Z_FP64 = {}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("s", [0.1, 0.5, 1.0])
-def test_split_v5z_s_sweep(pk, s):
-    """Quintuple-zeta size, s in {0.1, 0.5, 1.0}: BF16x3 against the FP64 GPU
-    path per block, and sampled pair energies against the oracle."""
+def test_split_v5z_s_sweep(pk, s, prec):
+    """Quintuple-zeta size, s in {0.1, 0.5, 1.0}: BF16x3 and TF32x3 against the
+    FP64 GPU path per block, and sampled pair energies against the oracle."""
     cfg = dict(CONFIGS["naphthyne-v5z-1240"])
     cfg["s"] = s
     p = make_problem(**cfg)
-    gs, ps = _run(pk, p, "bf16x3")
-    g64, p64 = _run(pk, p, "fp64")
-    tol = split_tol("bf16x3", p.naux)
+    gs, ps = _run(pk, p, prec)
+    if s not in _V5Z_FP64:
+        _V5Z_FP64[s] = _run(pk, p, "fp64")
+    g64, p64 = _V5Z_FP64[s]
     for k in BLOCKS:
         rel = abs(gs[k] - g64[k]) / abs(g64[k])
-        print(f"v5z s={s} {k:7s} split={gs[k]:+.12e} fp64={g64[k]:+.12e} rel={rel:.2e}")
-        assert rel <= split_tol("bf16x3", p.naux, k)
+        print(f"v5z {prec} s={s} {k:7s} split={gs[k]:+.12e} fp64={g64[k]:+.12e} rel={rel:.2e}")
+        assert rel <= split_tol(prec, p.naux, k)
         assert rel <= SPLIT_BAR, k
     sample = [(0, 0), (3, 19), (23, 23)]
     ref = odsrg.ccvv_pair_energies(p.B, p.eps, p.s, p.ncore, p.nactive, p.nvirt, pairs=sample).numpy()
     for (m, n) in sample:
-        assert abs(ps[m, n] - ref[m, n]) / abs(ref[m, n]) <= 2 * tol
+        r = abs(ps[m, n] - ref[m, n]) / abs(ref[m, n])
+        print(f"v5z {prec} s={s} pair ({m},{n}) rel vs oracle {r:.2e}")
+        # one pair is a sum of fewer, positive terms: the CCVV bound holds for it too
+        assert r <= split_tol(prec, p.naux)
+        assert r <= SPLIT_BAR
         assert abs(p64[m, n] - ref[m, n]) / abs(ref[m, n]) <= 1e-10
 
 
