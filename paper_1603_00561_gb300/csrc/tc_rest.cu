@@ -406,6 +406,9 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
   // sBAe = beta_u * alpha_u(e): the row factor of exp(-s D^2) with the pair factor folded in
   __shared__ double sBAe[NA][F2_T], sAf[NA][F2_T], sEe[F2_T], sEf[F2_T], sG[NA * NA];
   __shared__ double sE[NA];
+  // FP32 copies: e_e + e_f and E_u for the path test and the reciprocal seed;
+  // G as FP32 head + FP32 remainder for the far path's FP32 sums
+  __shared__ float sEeF[F2_T], sEfF[F2_T], sEF[NA], sGh[NA * NA], sGl[NA * NA];
   __shared__ int sFact, sFar;
   __shared__ double red[8];
   const int m = blockIdx.x / n_tp;
@@ -423,6 +426,8 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
     const int e = E0 + t, f = F0 + t;
     sEe[t] = e < z.nV ? eps[ve + e] : 0.0;
     sEf[t] = f < z.nV ? eps[ve + f] : 0.0;
+    sEeF[t] = (float)sEe[t];
+    sEfF[t] = (float)sEf[t];
 #pragma unroll
     for (int u = 0; u < NA; ++u) {
       const double* al = alpha + (size_t)(m * z.nA + u) * nVpad;
@@ -430,11 +435,17 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
       sAf[u][t] = al[F0 + t];
     }
   }
-  if (threadIdx.x < NA * NA) sG[threadIdx.x] = G[threadIdx.x];
+  if (threadIdx.x < NA * NA) {
+    const double g = G[threadIdx.x];
+    sG[threadIdx.x] = g;
+    sGh[threadIdx.x] = (float)g;
+    sGl[threadIdx.x] = (float)(g - (double)(float)g);
+  }
   if (threadIdx.x == 0) {
     int fact = 1;
     for (int u = 0; u < NA; ++u) {
       sE[u] = pinfo[4 * (m * z.nA + u)];
+      sEF[u] = (float)sE[u];
       fact = fact && (pinfo[4 * (m * z.nA + u) + 2] != 0.0);
     }
     sFact = fact;
@@ -471,55 +482,80 @@ __global__ void __launch_bounds__(256) cavv_f2_kernel(const float* __restrict__ 
       if (e >= z.nV) break;
       const double tau = (fact && !tile_far) ? tau1[(size_t)e * nVpad + f] : 0.0;
       const double eef = sEe[r] + sEf[c];
-      double Rv[NA], Rt[NA], Dd[NA];
-      float X[NA], Xt[NA], Df[NA];
+      const float eeff = sEeF[r] + sEfF[c];
+      float X[NA], Xt[NA];
       bool far = fact;
 #pragma unroll
       for (int u = 0; u < NA; ++u) {
         X[u] = sX[(u * F2_T + r) * (F2_T + 1) + c];
         Xt[u] = sXt[(u * F2_T + r) * (F2_T + 1) + c];
-        Dd[u] = sE[u] - eef;
-        Df[u] = (float)Dd[u];
-        // the threshold is not sharp (both paths are accurate near it): FP32 compare
-        far = far && fabsf(Df[u]) >= 0.25f;
+        // D_u in FP32 (a few ulp): the path test, whose threshold is not sharp
+        // (both paths are accurate near it), and below the reciprocal seed
+        far = far && fabsf(sEF[u] - eeff) >= 0.25f;
       }
       if (far || tile_far) {
-        // every D_u away from 0: FP64 regulators (from the factor tables, or
-        // Rv = 1, Rt = 1/D where exp(-s D^2) is below FP64 precision), the
-        // exchange combination Q_uv = X_u (2 X_v - Xt_v) [+ mirror] in FP32
+        // every D_u away from 0 (|D_u| >= 1/4): Rt_u = (1 - g_u) / D_u in FP64
+        // (g_u = exp(-s D_u^2) from the factor tables, or 0 where it is below FP64
+        // precision; 1/D_u an FP32 seed and one FP64 Newton step). The exchange
+        // combination Q_uv = X_u (2 X_v - Xt_v) [+ mirror], the smooth factor
+        // Rv_u = 1 + g_u in [1, 2) and the u sums with G_uv run in FP32 with
+        // round-to-nearest (unbiased; G as head + remainder, so its own rounding
+        // is not a systematic error); each v sum meets Rt_v in FP64. The
+        // remainder sums take Rt in FP32 (they are 2^-24 of the head sums).
+        double Rt[NA];
+        float a[NA], at[NA], rtf[NA];
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
-          const double D = Dd[u];
+          const double D = sE[u] - eef;
           const double g = tile_far ? 0.0 : sBAe[u][r] * sAf[u][c] * tau;
           float r0f;
-          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(Df[u]));
+          asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(sEF[u] - eeff));
           const double r0 = (double)r0f;
           const double en = fma(-D, r0, 1.0);
           const double R0 = fma(-g, r0, r0);
           Rt[u] = fma(R0, en, R0);
-          Rv[u] = 1.0 + g;
+          const float gf = (float)g;
+          const float w = 1.0f + gf;
+          a[u] = w * X[u];
+          at[u] = w * Xt[u];
+          rtf[u] = (1.0f - gf) * r0f;
         }
+        // sum_u G_uv Rv_u Q_uv = (2 X_v - Xt_v) sum_u G_uv Rv_u X_u
+        //                       [+ (2 Xt_v - X_v) sum_u G_uv Rv_u Xt_u for the mirror]
         double t = 0.0;
+        float tl = 0.0f;
 #pragma unroll
         for (int v = 0; v < NA; ++v) {
-          const float dv = 2.0f * X[v] - Xt[v], dtv = 2.0f * Xt[v] - X[v];
-          double cv = 0.0;
+          float zh = 0.0f, zl = 0.0f, zth = 0.0f, ztl = 0.0f;
 #pragma unroll
           for (int u = 0; u < NA; ++u) {
-            const float q = mirror ? fmaf(X[u], dv, Xt[u] * dtv) : X[u] * dv;
-            cv = fma(sG[u * NA + v] * Rv[u], (double)q, cv);
+            // volatile: reloaded per position instead of held in 2 NA^2 registers
+            const float gh = ((volatile float*)sGh)[u * NA + v];
+            const float gl = ((volatile float*)sGl)[u * NA + v];
+            zh = fmaf(gh, a[u], zh);
+            zl = fmaf(gl, a[u], zl);
+            if (mirror) {
+              zth = fmaf(gh, at[u], zth);
+              ztl = fmaf(gl, at[u], ztl);
+            }
           }
-          t = fma(cv, Rt[v], t);
+          const float dv = 2.0f * X[v] - Xt[v], dtv = 2.0f * Xt[v] - X[v];
+          const float ch = mirror ? fmaf(dv, zh, dtv * zth) : dv * zh;
+          const float cl = mirror ? fmaf(dv, zl, dtv * ztl) : dv * zl;
+          t = fma((double)ch, Rt[v], t);
+          tl = fmaf(cl, rtf[v], tl);
         }
-        acc += t;
+        acc += t + (double)tl;
       } else {
         // a D_u near 0 (or a pair whose factors could overflow): expm1 regulators
         // and the exchange combination in FP64
         ++near;
+        double Rv[NA], Rt[NA];
 #pragma unroll
         for (int u = 0; u < NA; ++u) {
-          Rt[u] = reg_t(Dd[u], s);
-          Rv[u] = reg_v(Dd[u], s);
+          const double D = sE[u] - eef;
+          Rt[u] = reg_t(D, s);
+          Rv[u] = reg_v(D, s);
         }
         double t1 = 0.0, t2 = 0.0;
 #pragma unroll
