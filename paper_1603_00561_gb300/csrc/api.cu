@@ -328,16 +328,14 @@ static dsrg_status_t check_common(dsrg_plan* p, const double* B, const double* e
 }  // extern "C"
 
 namespace dsrg {
-// Everything after the CCVV launch: CAVV, CCAV, active block, final reduction.
-dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
-                       const double* L, const double* L3, const double* F1, double s, double* out) {
+// The blocks besides CCVV: CAVV, CCAV and the active block (they do not read
+// the CCVV partials, so they may run beside the CCVV launch).
+dsrg_status_t run_blocks(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                         const double* L, const double* L3, const double* F1, double s) {
   cudaError_t e;
-  if (p->shard_rank != 0) {
-    // another rank's plan computes CAVV, CCAV and the active block; this
-    // rank's segments of them stay at the zeros set by dsrg_plan_set_shard
-    if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
-    return DSRG_OK;
-  }
+  // on a shard of rank > 0 another rank's plan computes these blocks; this
+  // rank's segments of them stay at the zeros set by dsrg_plan_set_shard
+  if (p->shard_rank != 0) return DSRG_OK;
   if (p->rest_tc) {
     // one tensor-core GEMM feeds CAVV, CCAV and the active-block integrals
     if ((e = launch_split_rest(p, B, eps, G, s)) != cudaSuccess) return cuda_fail(p, e, "cavv/ccav");
@@ -347,8 +345,20 @@ dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const d
   }
   if ((e = launch_active(p, B, eps, G, L, L3, F1, s, p->rest_tc)) != cudaSuccess)
     return cuda_fail(p, e, "active");
-  if ((e = launch_final_reduce(p, out)) != cudaSuccess) return cuda_fail(p, e, "reduce");
   return DSRG_OK;
+}
+
+// The final reduction of every block's partials into out[5].
+dsrg_status_t run_reduce(dsrg_plan* p, double* out) {
+  const cudaError_t e = launch_final_reduce(p, out);
+  return e == cudaSuccess ? DSRG_OK : cuda_fail(p, e, "reduce");
+}
+
+// Everything after the CCVV launch: CAVV, CCAV, active block, final reduction.
+dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                       const double* L, const double* L3, const double* F1, double s, double* out) {
+  const dsrg_status_t st = run_blocks(p, B, eps, G, L, L3, F1, s);
+  return st != DSRG_OK ? st : run_reduce(p, out);
 }
 }  // namespace dsrg
 

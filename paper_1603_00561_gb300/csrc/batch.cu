@@ -28,6 +28,7 @@ struct dsrg_batch {
   int max_branches = 1;  // branches the GEMM output buffers allow (a power of 2)
   cudaStream_t side[BATCH_MAX_BRANCHES] = {};
   cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_ccvv = nullptr;  // the CCVV work of every molecule is done
   cudaEvent_t ev_join[BATCH_MAX_BRANCHES] = {};
   dsrg_precision_t prec = DSRG_PREC_FP64;
   cudaStream_t user_stream = nullptr;
@@ -87,6 +88,8 @@ void bfree(dsrg_batch* b) {
   }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   b->ev_fork = nullptr;
+  if (b->ev_ccvv) cudaEventDestroy(b->ev_ccvv);
+  b->ev_ccvv = nullptr;
 }
 
 dsrg_status_t bfail(dsrg_batch* b, dsrg_status_t st, const std::string& m) {
@@ -117,7 +120,8 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
   b->max_branches = 1;
   while (b->max_branches * 2 <= BATCH_MAX_BRANCHES && b->max_branches * 2 <= nmol) b->max_branches *= 2;
   b->branches = b->max_branches;
-  bool streams_ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  bool streams_ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&b->ev_ccvv, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; streams_ok && k < b->max_branches; ++k)
     streams_ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
@@ -421,26 +425,39 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
       e = split ? dsrg::split_stage(p, B[m], eps[m], s[m]) : dsrg::launch_ccvv_fp64(p, B[m], eps[m], s[m]);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
-    if (st == DSRG_OK && split) {
-      dsrg_plan* p0 = b->plans[0];
-      e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
-      if (e == cudaSuccess)
-        e = dsrg::split_launch_ccvv(p0, b->maps, b->d_mols, b->d_items, b->d_begin,
-                                    b->grid, b->prec == DSRG_PREC_BF16X3, b->order);
-      if (e != cudaSuccess) st = DSRG_ERR_CUDA;
-    }
-    // the per-molecule blocks: fork into K branches, molecule m on branch m mod K
+    // the per-molecule blocks: fork into K branches, molecule m on branch m mod K.
+    // CAVV, CCAV and the active block do not read the CCVV partials: the branches
+    // start on them beside the batched CCVV launch and wait for it only before
+    // their final reductions.
     const int K = b->branches;
     if (st == DSRG_OK && K > 1) {
       e = cudaEventRecord(b->ev_fork, b->cap_stream);
       for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
+    if (st == DSRG_OK && split) {
+      dsrg_plan* p0 = b->plans[0];
+      p0->stream = b->cap_stream;
+      e = dsrg::split_set_inputs(p0, b->d_mols, 0, n, eps, s);
+      if (e == cudaSuccess)
+        e = dsrg::split_launch_ccvv(p0, b->maps, b->d_mols, b->d_items, b->d_begin,
+                                    b->grid, b->prec == DSRG_PREC_BF16X3, b->order);
+      if (e != cudaSuccess) st = DSRG_ERR_CUDA;
+    }
+    if (st == DSRG_OK && K > 1 && cudaEventRecord(b->ev_ccvv, b->cap_stream) != cudaSuccess)
+      st = DSRG_ERR_CUDA;
     for (int m = 0; m < n && st == DSRG_OK; ++m) {
       dsrg_plan* p = b->plans[m];
       p->stream = K > 1 ? b->side[m % K] : b->cap_stream;
-      st = dsrg::run_rest(p, B[m], eps[m], gamma1 ? gamma1[m] : nullptr,
-                          lambda2 ? lambda2[m] : nullptr, nullptr, nullptr, s[m], out_dev + 5 * m);
+      st = dsrg::run_blocks(p, B[m], eps[m], gamma1 ? gamma1[m] : nullptr,
+                            lambda2 ? lambda2[m] : nullptr, nullptr, nullptr, s[m]);
+    }
+    for (int k = 0; st == DSRG_OK && k < K && K > 1; ++k)
+      if (cudaStreamWaitEvent(b->side[k], b->ev_ccvv, 0) != cudaSuccess) st = DSRG_ERR_CUDA;
+    for (int m = 0; m < n && st == DSRG_OK; ++m) {
+      dsrg_plan* p = b->plans[m];
+      p->stream = K > 1 ? b->side[m % K] : b->cap_stream;
+      st = dsrg::run_reduce(p, out_dev + 5 * m);
     }
     if (K > 1) {
       // join every branch that was forked, also after a failure, so that the capture ends

@@ -173,6 +173,9 @@ dsrg_status_t create_plan(dsrg_plan_t** out, const dsrg_sizes_t* sz, dsrg_precis
                           void* cuda_stream, uint32_t flags, const SplitShare* share);
 dsrg_status_t run_rest(dsrg_plan* p, const double* B, const double* eps, const double* G,
                        const double* L, const double* L3, const double* F1, double s, double* out);
+dsrg_status_t run_blocks(dsrg_plan* p, const double* B, const double* eps, const double* G,
+                         const double* L, const double* L3, const double* F1, double s);
+dsrg_status_t run_reduce(dsrg_plan* p, double* out);
 
 // Split planes shared by several molecules (tc_split.cu).
 bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_base,
