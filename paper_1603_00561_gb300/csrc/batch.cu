@@ -29,6 +29,7 @@ struct dsrg_batch {
   cudaStream_t side[BATCH_MAX_BRANCHES] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_ccvv = nullptr;  // the CCVV work of every molecule is done
+  cudaEvent_t ev_staged[BATCH_MAX_BRANCHES] = {};  // a branch's molecules staged
   cudaEvent_t ev_join[BATCH_MAX_BRANCHES] = {};
   dsrg_precision_t prec = DSRG_PREC_FP64;
   cudaStream_t user_stream = nullptr;
@@ -83,8 +84,10 @@ void bfree(dsrg_batch* b) {
   for (int k = 0; k < BATCH_MAX_BRANCHES; ++k) {
     if (b->side[k]) cudaStreamDestroy(b->side[k]);
     if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    if (b->ev_staged[k]) cudaEventDestroy(b->ev_staged[k]);
     b->side[k] = nullptr;
     b->ev_join[k] = nullptr;
+    b->ev_staged[k] = nullptr;
   }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   b->ev_fork = nullptr;
@@ -124,7 +127,8 @@ dsrg_status_t dsrg_batch_plan(dsrg_batch_t** out, int32_t nmol, const dsrg_sizes
                     cudaEventCreateWithFlags(&b->ev_ccvv, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; streams_ok && k < b->max_branches; ++k)
     streams_ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+                 cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->ev_staged[k], cudaEventDisableTiming) == cudaSuccess;
   if (!streams_ok) {
     bfree(b);
     delete b;
@@ -418,21 +422,30 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t* b, const double* const* B,
     if (e != cudaSuccess) return bfail(b, DSRG_ERR_CUDA, cudaGetErrorString(e));
     dsrg_status_t st = DSRG_OK;
     const bool split = b->prec != DSRG_PREC_FP64;
+    // The work is forked into K branches, molecule m on branch m mod K: each branch
+    // stages its molecules (split: planes and pair tables; FP64: the CCVV kernel
+    // itself). The batched CCVV launch waits for every branch's staging. CAVV, CCAV
+    // and the active block read only the staged planes and write their own
+    // partials, so they start beside the CCVV launch; each branch waits for it
+    // only before its molecules' final reductions.
+    const int K = b->branches;
+    if (K > 1) {
+      e = cudaEventRecord(b->ev_fork, b->cap_stream);
+      for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+      if (e != cudaSuccess) st = DSRG_ERR_CUDA;
+    }
     for (int m = 0; m < n && st == DSRG_OK; ++m) {
       dsrg_plan* p = b->plans[m];
-      p->stream = b->cap_stream;
+      p->stream = K > 1 ? b->side[m % K] : b->cap_stream;
       p->launches = 0;
       e = split ? dsrg::split_stage(p, B[m], eps[m], s[m]) : dsrg::launch_ccvv_fp64(p, B[m], eps[m], s[m]);
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
-    // the per-molecule blocks: fork into K branches, molecule m on branch m mod K.
-    // CAVV, CCAV and the active block do not read the CCVV partials: the branches
-    // start on them beside the batched CCVV launch and wait for it only before
-    // their final reductions.
-    const int K = b->branches;
-    if (st == DSRG_OK && K > 1) {
-      e = cudaEventRecord(b->ev_fork, b->cap_stream);
-      for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+    if (st == DSRG_OK && split && K > 1) {
+      for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->ev_staged[k], b->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_stream, b->ev_staged[k], 0);
+      }
       if (e != cudaSuccess) st = DSRG_ERR_CUDA;
     }
     if (st == DSRG_OK && split) {
