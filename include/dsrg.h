@@ -212,10 +212,13 @@ dsrg_status_t dsrg_mrpt2_energy_batched(dsrg_batch_t *batch, const double *const
                                         const double *const *lambda2, const double *s,
                                         double *out_dev);
 
-/* Concurrent branches of the per-molecule blocks (CAVV, CCAV, active block and
- * the reductions of each molecule, which do not depend on each other): after
- * the batched CCVV launch the graph forks into K branches, molecule m on
- * branch m mod K, and joins them at the end. K is 1, 2, 4 or 8 and at most
+/* Concurrent branches of the per-molecule work (staging of the planes and pair
+ * tables, CAVV, CCAV, the active block and the reductions of each molecule,
+ * which do not depend on each other): the graph forks into K branches,
+ * molecule m on branch m mod K. The batched CCVV launch waits for every
+ * branch's staging; the other blocks run beside it, and each branch waits for
+ * it only before its final reductions; the branches join at the end. K is 1,
+ * 2, 4 or 8 and at most
  * min(nmol rounded down to a power of 2, 8) (each branch owns a GEMM output
  * buffer, allocated with the plan); the default is that maximum. Setting a new
  * K waits for the batch's stream and makes the next call capture a new graph.
