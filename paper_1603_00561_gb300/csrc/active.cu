@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(256) gram_aavv_kernel(const double* __restrict
 // P1[xu][yv] = sum_ef M_xu[ef] M_yv[ef] R, P2[xu][yv] = sum_ef M_xu[ef] M_vy[ef] R
 // (M_vy[e,f] = M_yv[f,e]) with R = (1 + exp(-s D_xu^2)) (1 - exp(-s D_yv^2))/D_yv.
 constexpr int ACTVV_BLOCKS = 152;
+constexpr int ACTVV_CH = 64;      // positions (e, f) per chunk of the active VV sums
 
 // Factor tables of exp(-s D_p^2), D_p = E_p - e_e - e_f for the active pairs
 // p = (x, u), E_p = e_x + e_u: exp(-s E_p^2) exp(2 s E_p e_e) exp(2 s E_p e_f)
@@ -448,7 +449,10 @@ __global__ void __launch_bounds__(256) actvv_kernel(const double* __restrict__ e
 // Same sums for small active spaces, with the regulators of each active pair
 // evaluated once per (e,f): Rv(D_xu) and Rt(D_yv) for the nA^2 pairs, then the
 // nA^4 products P1 += (M_xu Rv_xu)(M_yv Rt_yv), P2 += (M_xu Rv_xu)(M_vy Rt_yv).
-template <int NA>
+// F32 (split-precision plans, as actvv_gen_kernel): the regulated factors are
+// rounded to FP32 and each thread's sums over up to ACTVV_CH positions run in
+// FP32 with round-to-nearest, the chunk sums in FP64; the regulators stay FP64.
+template <int NA, bool F32>
 __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restrict__ eps, double s,
                                                           Sizes z, const double* __restrict__ M,
                                                           ActFact F, double* __restrict__ part) {
@@ -465,8 +469,13 @@ __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restri
     fact = fact && F.pinfo[4 * p + 2] != 0.0;
   }
   double acc1[NA4], acc2[NA4];
+  float f1[NA4], f2[NA4];
+  int cnt = 0;
 #pragma unroll
-  for (int c = 0; c < NA4; ++c) acc1[c] = acc2[c] = 0.0;
+  for (int c = 0; c < NA4; ++c) {
+    acc1[c] = acc2[c] = 0.0;
+    f1[c] = f2[c] = 0.0f;
+  }
   for (size_t k = (size_t)blockIdx.x * 256 + threadIdx.x; k < nV2; k += (size_t)gridDim.x * 256) {
     const int e = (int)(k / z.nV), f = (int)(k % z.nV);
     const double ef = eps[ve + e] + eps[ve + f];
@@ -483,14 +492,48 @@ __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restri
       mr[p] = m[p] * rv;
       mq[p] = rt;
     }
+    if constexpr (F32) {
+      float a[NA2], b[NA2], c[NA2];
 #pragma unroll
-    for (int p = 0; p < NA2; ++p)
-#pragma unroll
-      for (int q = 0; q < NA2; ++q) {
-        const int qt = (q % NA) * NA + q / NA;
-        acc1[p * NA2 + q] = fma(mr[p], m[q] * mq[q], acc1[p * NA2 + q]);
-        acc2[p * NA2 + q] = fma(mr[p], m[qt] * mq[q], acc2[p * NA2 + q]);
+      for (int p = 0; p < NA2; ++p) {
+        const int pt = (p % NA) * NA + p / NA;
+        a[p] = (float)mr[p];
+        b[p] = (float)(m[p] * mq[p]);
+        c[p] = (float)(m[pt] * mq[p]);
       }
+#pragma unroll
+      for (int p = 0; p < NA2; ++p)
+#pragma unroll
+        for (int q = 0; q < NA2; ++q) {
+          f1[p * NA2 + q] = fmaf(a[p], b[q], f1[p * NA2 + q]);
+          f2[p * NA2 + q] = fmaf(a[p], c[q], f2[p * NA2 + q]);
+        }
+      if (++cnt == ACTVV_CH) {
+        cnt = 0;
+#pragma unroll
+        for (int o = 0; o < NA4; ++o) {
+          acc1[o] += (double)f1[o];
+          acc2[o] += (double)f2[o];
+          f1[o] = f2[o] = 0.0f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < NA2; ++p)
+#pragma unroll
+        for (int q = 0; q < NA2; ++q) {
+          const int qt = (q % NA) * NA + q / NA;
+          acc1[p * NA2 + q] = fma(mr[p], m[q] * mq[q], acc1[p * NA2 + q]);
+          acc2[p * NA2 + q] = fma(mr[p], m[qt] * mq[q], acc2[p * NA2 + q]);
+        }
+    }
+  }
+  if constexpr (F32) {
+#pragma unroll
+    for (int o = 0; o < NA4; ++o) {
+      acc1[o] += (double)f1[o];
+      acc2[o] += (double)f2[o];
+    }
   }
 #pragma unroll
   for (int c = 0; c < NA4; ++c) {
@@ -509,7 +552,6 @@ __global__ void __launch_bounds__(256) actvv_small_kernel(const double* __restri
 // (nA^2 regulator pairs per position; D_p' = D_p), then accumulates
 // P1[p][q] += a_p b_q and P2[p][q] += a_p c_q (M_vy = M_(yv)') over the chunk,
 // each thread holding a fixed set of (p, q).
-constexpr int ACTVV_CH = 64;
 
 // F32 (split-precision plans): the regulated factors are rounded to FP32 and each
 // 64-term chunk of the sum over (e, f) runs in FP32 on CUDA cores (round to
@@ -1261,10 +1303,16 @@ cudaError_t launch_active(dsrg_plan* p, const double* B, const double* eps, cons
     break;
     switch (z.nA) {
       case 1:
-        actvv_small_kernel<1><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
+        if (ints_ready)
+          actvv_small_kernel<1, true><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
+        else
+          actvv_small_kernel<1, false><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
         break;
       case 2:
-        actvv_small_kernel<2><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
+        if (ints_ready)
+          actvv_small_kernel<2, true><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
+        else
+          actvv_small_kernel<2, false><<<ACTVV_BLOCKS, 256, 0, st>>>(eps, s, z, w.M, F, w.P12part);
         break;
       ACTVV_GEN(3) ACTVV_GEN(4) ACTVV_GEN(5) ACTVV_GEN(6) ACTVV_GEN(7) ACTVV_GEN(8)
       default: {
