@@ -977,7 +977,7 @@ __device__ double term_value(int term, long o, const Sizes& z, const ActDims& d,
 }
 
 constexpr int TERM_NT = 128;
-constexpr int TERM_BLOCKS = 304;  // CTAs per term, grid-stride over its outer index
+constexpr int TERM_BLOCKS = 608;  // CTAs per term, grid-stride over its outer index
 
 __global__ void __launch_bounds__(TERM_NT) terms_kernel(Sizes z, TermArgs t,
                                                         double* __restrict__ partials) {
