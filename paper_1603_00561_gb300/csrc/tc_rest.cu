@@ -882,6 +882,9 @@ struct RestState {
   double* tau1 = nullptr;
   int2* d_tp = nullptr;
   int n_tp = 0;
+  // tau1 was written by the pair tables of the CCVV kernel (split_stage_tables)
+  // queued before this call's CAVV tables: those skip it
+  bool tau1_staged = false;
 };
 
 int rest_xrows(const Sizes& z) {
@@ -956,6 +959,15 @@ bool rest_alloc(dsrg_plan* p, float* shared_y) {
          cudaSuccess;
 }
 
+// tau1 for the CCVV pair tables to fill (exp(-s t^2), whose square is their
+// own exp(-2 s t^2)); the next CAVV tables of this plan then skip it.
+double* rest_take_tau1(dsrg_plan* p) {
+  RestState* st = p->rest;
+  if (!st) return nullptr;
+  st->tau1_staged = true;
+  return st->tau1;
+}
+
 void rest_act_tables(const dsrg_plan* p, const double** alpha, const double** pinfo,
                      const double** tau, int* ld) {
   const RestState* st = p->rest;
@@ -1021,7 +1033,11 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     DSRG_LAUNCH_CHECK(p);
   }
   {
-    const size_t n = (size_t)z.nH * z.nA * st->nVpad + (size_t)st->nVpad * st->nVpad;
+    // the pair-independent table tau1 comes with the CCVV pair tables when they were
+    // staged for this call
+    const size_t n = (size_t)z.nH * z.nA * st->nVpad +
+                     (st->tau1_staged ? 0 : (size_t)st->nVpad * st->nVpad);
+    st->tau1_staged = false;
     cavv_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(eps, s, z, st->nVpad,
                                                                       st->alpha, st->pinfo, st->tau1);
     DSRG_LAUNCH_CHECK(p);

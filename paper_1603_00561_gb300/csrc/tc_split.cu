@@ -949,7 +949,8 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
 __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Sizes z,
                                     const int2* __restrict__ pairs, int n_pairs, int nVpad,
                                     double* __restrict__ alpha, double* __restrict__ pinfo,
-                                    double* __restrict__ tau, double* __restrict__ trange) {
+                                    double* __restrict__ tau, double* __restrict__ trange,
+                                    double* __restrict__ tau_s) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int ve = z.nC + z.nA;
   const size_t na = (size_t)n_pairs * nVpad, nt = (size_t)nVpad * nVpad;
@@ -974,12 +975,19 @@ __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Si
   } else if (k < na + nt) {
     const size_t r = k - na;
     const int a = (int)(r / nVpad), b = (int)(r % nVpad);
-    double v = 0.0;
+    double v = 0.0, v1 = 0.0;
     if (a < z.nV && b < z.nV) {
       const double t = eps[ve + a] + eps[ve + b];
-      v = exp(-2.0 * s * t * t);
+      if (tau_s) {
+        // the CAVV tables' exp(-s t^2) as well; this table is its square
+        v1 = exp(-s * t * t);
+        v = v1 * v1;
+      } else {
+        v = exp(-2.0 * s * t * t);
+      }
     }
     tau[r] = v;
+    if (tau_s) tau_s[r] = v1;
   } else if (k < na + nt + (size_t)(nVpad / TT)) {
     const int t = (int)(k - na - nt);
     double lo = 1e300, hi = -1e300;
@@ -1405,8 +1413,9 @@ cudaError_t split_stage_rows(dsrg_plan* p, const double* B, int h0, int h1) {
 cudaError_t split_stage_tables(dsrg_plan* p, const double* eps, double s) {
   SplitWs* w = p->split;
   const size_t n = (size_t)p->n_pairs * w->nVpad + (size_t)w->nVpad * w->nVpad + w->nT;
+  double* tau_s = p->rest ? rest_take_tau1(p) : nullptr;
   split_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
-      eps, s, p->z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange);
+      eps, s, p->z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange, tau_s);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
