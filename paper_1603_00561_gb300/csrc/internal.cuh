@@ -309,6 +309,7 @@ const float* split_tail_ptr(const dsrg_plan* p);  // [plane rows + 256][32] fl32
 size_t split_tail_bytes(const Sizes& z);
 // Factor tables of exp(-s D^2) for the active pairs and the pair-independent
 // table, formed by launch_split_rest of the same call.
+__global__ void abs_max_kernel(const double* __restrict__ x, int n, double* __restrict__ out);
 double* rest_take_tau1(dsrg_plan* p);
 void rest_act_tables(const dsrg_plan* p, const double** alpha, const double** pinfo,
                      const double** tau, int* ld);

@@ -345,7 +345,7 @@ __global__ void xx_gram_kernel(const double* __restrict__ Xq, int T, int Q, doub
 // sums of the active block).
 __global__ void cavv_tables_kernel(const double* __restrict__ eps, double s, Sizes z, int nVpad,
                                    double* __restrict__ alpha, double* __restrict__ pinfo,
-                                   double* __restrict__ tau1) {
+                                   double* __restrict__ tau1, const double* __restrict__ vmaxp) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int ve = z.nC + z.nA;
   const int nmu = (z.nC + z.nA) * z.nA;
@@ -356,8 +356,7 @@ __global__ void cavv_tables_kernel(const double* __restrict__ eps, double s, Siz
     const double E = eps[m] + eps[z.nC + u];
     alpha[k] = (b < z.nV) ? exp(2.0 * s * E * eps[ve + b]) : 0.0;
     if (b == 0) {
-      double vmax = 0.0;
-      for (int v = 0; v < z.nV; ++v) vmax = fmax(vmax, fabs(eps[ve + v]));
+      const double vmax = *vmaxp;  // max |e_v| over the virtual orbitals
       // factors are multiplied left to right (pair, row, column, table); the partial
       // products carry -sE^2 + 2sE e_e (+ 2sE e_f), bounded by the sum of magnitudes
       const bool ok = (s * E * E + 4.0 * s * fabs(E) * vmax <= 700.0) &&
@@ -880,6 +879,7 @@ struct RestState {
   double* alpha = nullptr;
   double* pinfo = nullptr;
   double* tau1 = nullptr;
+  double* vmax = nullptr;  // max |e_v| over the virtual orbitals
   int2* d_tp = nullptr;
   int n_tp = 0;
   // tau1 was written by the pair tables of the CCVV kernel (split_stage_tables)
@@ -949,6 +949,7 @@ bool rest_alloc(dsrg_plan* p, float* shared_y) {
        plan_alloc(p, (void**)&st->alpha, (size_t)z.nH * z.nA * st->nVpad * 8) &&
        plan_alloc(p, (void**)&st->pinfo, (size_t)z.nH * z.nA * 4 * 8) &&
        plan_alloc(p, (void**)&st->tau1, (size_t)st->nVpad * st->nVpad * 8) &&
+       plan_alloc(p, (void**)&st->vmax, 8) &&
        plan_alloc(p, (void**)&st->d_tp, (size_t)st->n_tp * sizeof(int2));
   if (!ok) return false;
   const int nt = (z.nV + F2_T - 1) / F2_T;
@@ -1038,8 +1039,10 @@ cudaError_t launch_split_rest(dsrg_plan* p, const double* B, const double* eps, 
     const size_t n = (size_t)z.nH * z.nA * st->nVpad +
                      (st->tau1_staged ? 0 : (size_t)st->nVpad * st->nVpad);
     st->tau1_staged = false;
-    cavv_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(eps, s, z, st->nVpad,
-                                                                      st->alpha, st->pinfo, st->tau1);
+    abs_max_kernel<<<1, 256, 0, stream>>>(eps + z.nC + z.nA, z.nV, st->vmax);
+    DSRG_LAUNCH_CHECK(p);
+    cavv_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+        eps, s, z, st->nVpad, st->alpha, st->pinfo, st->tau1, st->vmax);
     DSRG_LAUNCH_CHECK(p);
   }
   {

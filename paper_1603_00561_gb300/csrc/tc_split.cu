@@ -67,6 +67,7 @@ struct SplitWs {
   double* pinfo = nullptr;  // [n_pairs][4]      E_p, exp(-2 s E_p^2), factorisable flag
   double* tau = nullptr;    // [nVpad][nVpad]    exp(-2 s (e_a + e_b)^2)
   double* trange = nullptr; // [nT][2]           min, max of e over the virtuals of a tile
+  double* vmax = nullptr;   // max |e_v| over the virtual orbitals (pair tables)
   void* d_mol = nullptr;    // device MolDesc of this molecule
   int4* d_items = nullptr;  // single-molecule schedule
   int* d_begin = nullptr;
@@ -942,6 +943,23 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
   }
 }
 
+// max |x_k| over n values into *out: one CTA, strided per-thread maxima and a
+// tree (a maximum is exact, so the order does not matter). NaN entries are
+// skipped, as fmax does.
+__global__ void __launch_bounds__(256) abs_max_kernel(const double* __restrict__ x, int n,
+                                                      double* __restrict__ out) {
+  __shared__ double sm[256];
+  double m = 0.0;
+  for (int k = threadIdx.x; k < n; k += 256) m = fmax(m, fabs(x[k]));
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sm[0];
+}
+
 // Per-pair factors of exp(-2 s D^2) with D = E - e_a - e_b:
 //   exp(-2 s E^2) * exp(4 s E e_a) * exp(4 s E e_b) * exp(-2 s (e_a + e_b)^2).
 // A pair is factorisable when every partial product of these factors, taken in
@@ -950,7 +968,7 @@ __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Si
                                     const int2* __restrict__ pairs, int n_pairs, int nVpad,
                                     double* __restrict__ alpha, double* __restrict__ pinfo,
                                     double* __restrict__ tau, double* __restrict__ trange,
-                                    double* __restrict__ tau_s) {
+                                    double* __restrict__ tau_s, const double* __restrict__ vmaxp) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int ve = z.nC + z.nA;
   const size_t na = (size_t)n_pairs * nVpad, nt = (size_t)nVpad * nVpad;
@@ -960,8 +978,7 @@ __global__ void split_tables_kernel(const double* __restrict__ eps, double s, Si
     const double E = eps[ij.x] + eps[ij.y];
     alpha[k] = (b < z.nV) ? exp(4.0 * s * E * eps[ve + b]) : 0.0;
     if (b == 0) {
-      double vmax = 0.0;
-      for (int v = 0; v < z.nV; ++v) vmax = fmax(vmax, fabs(eps[ve + v]));
+      const double vmax = *vmaxp;  // max |e_v| over the virtual orbitals
       // the epilogue multiplies left to right, exp(-2sE^2) * alpha_a * alpha_b * tau:
       // the partial products carry the exponents -2sE^2 + 4sE e_a (+ 4sE e_b), which
       // for E e > 0 grow past each single factor's, so their sum of magnitudes is bounded
@@ -1213,6 +1230,7 @@ bool split_alloc_at(dsrg_plan* p, void* hi, void* lo, int Qld, long long row_bas
        plan_alloc(p, (void**)&w->pinfo, (size_t)p->n_pairs * 4 * 8) &&
        plan_alloc(p, (void**)&w->tau, (size_t)w->nVpad * w->nVpad * 8) &&
        plan_alloc(p, (void**)&w->trange, (size_t)w->nT * 2 * 8) &&
+       plan_alloc(p, (void**)&w->vmax, 8) &&
        plan_alloc(p, (void**)&w->d_mol, sizeof(MolDesc)) &&
        plan_alloc(p, (void**)&w->tail, split_tail_bytes(z));
   if (!ok) return false;
@@ -1412,10 +1430,13 @@ cudaError_t split_stage_rows(dsrg_plan* p, const double* B, int h0, int h1) {
 // Pair tables of the regulator (they read eps only).
 cudaError_t split_stage_tables(dsrg_plan* p, const double* eps, double s) {
   SplitWs* w = p->split;
+  abs_max_kernel<<<1, 256, 0, p->stream>>>(eps + p->z.nC + p->z.nA, p->z.nV, w->vmax);
+  DSRG_LAUNCH_CHECK(p);
   const size_t n = (size_t)p->n_pairs * w->nVpad + (size_t)w->nVpad * w->nVpad + w->nT;
   double* tau_s = p->rest ? rest_take_tau1(p) : nullptr;
   split_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
-      eps, s, p->z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange, tau_s);
+      eps, s, p->z, p->d_pairs, p->n_pairs, w->nVpad, w->alpha, w->pinfo, w->tau, w->trange, tau_s,
+      w->vmax);
   DSRG_LAUNCH_CHECK(p);
   return cudaSuccess;
 }
