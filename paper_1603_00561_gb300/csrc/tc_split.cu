@@ -873,46 +873,53 @@ __device__ __forceinline__ float tf32_rne(float x) {
   return __uint_as_float(u);
 }
 
-// 64 x 64 tiles: coalesced 8-byte reads along the particle index, then each
-// thread splits 16 consecutive Q of one row and writes them as 16-byte stores.
-// The split is of fl32(B): hi = rn(fl32(B)), lo = rn(fl32(B) - hi); the
-// difference from splitting B itself is below 2^-24 relative, under the
-// dropped lo*lo product.
+// One thread per plane row (h, a) and 16 consecutive Q: the lanes of a warp take
+// 32 consecutive a, so every load of one Q is 256 contiguous bytes of B, and each
+// thread then writes its row's 16 values per plane as 16-byte stores (no shared
+// memory, no barrier: each thread keeps 16 loads in flight). A block is 32 rows
+// by 8 Q chunks of 16. The split is of fl32(B): hi = rn(fl32(B)),
+// lo = rn(fl32(B) - hi); the difference from splitting B itself is below 2^-24
+// relative, under the dropped lo*lo product.
 template <bool BF16>
 __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restrict__ B, Sizes z,
                                                            int nVpad, int Qld,
                                                            void* __restrict__ hi,
                                                            void* __restrict__ lo,
                                                            float* __restrict__ tail, int h0) {
-  __shared__ double t[64][65];
-  const int q0 = blockIdx.x * 64, a0 = blockIdx.y * 64, h = h0 + blockIdx.z;
-  for (int k = threadIdx.x; k < 64 * 64; k += 256) {
-    const int r = k >> 6, c = k & 63;
-    const int q = q0 + r, a = a0 + c;
-    t[r][c] = (q < z.Q && a < z.nV) ? B[bidx(z, q, h, z.nA + a)] : 0.0;
+  const int lane = threadIdx.x & 31;
+  const int a = blockIdx.y * 32 + lane;
+  const int q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 16;
+  const int h = h0 + blockIdx.z;
+  if (q0 >= Qld) return;
+  double x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int q = q0 + k;
+    x[k] = (q < z.Q && a < z.nV) ? B[bidx(z, q, h, z.nA + a)] : 0.0;
   }
-  __syncthreads();
-  if (q0 == 0) {
+  // one FP64 operation per element (the FP64 pipe is the scarce one): xf = fl32(x)
+  float xf[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) xf[k] = (float)x[k];
+  const size_t row = (size_t)h * nVpad + a;
+  if (q0 < TAIL_Q) {
     // fl32(B) of the first TAIL_Q auxiliary functions, row-major per plane row
-    for (int k = threadIdx.x; k < 64 * TAIL_Q; k += 256) {
-      const int c = k / TAIL_Q, q = k % TAIL_Q;
-      tail[((size_t)h * nVpad + a0 + c) * TAIL_Q + q] = (float)t[q][c];
-    }
+    float4* tr = (float4*)(tail + row * TAIL_Q + q0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tr[j] = make_float4(xf[4 * j], xf[4 * j + 1], xf[4 * j + 2], xf[4 * j + 3]);
   }
-  const int ar = threadIdx.x >> 2, qq = (threadIdx.x & 3) * 16;
-  const size_t o = ((size_t)h * nVpad + a0 + ar) * Qld + q0 + qq;
+  const size_t o = row * Qld + q0;
   if (BF16) {
+    // hi = bf16(xf); xf - hi is exact in FP32; lo = bf16(xf - hi)
     uint32_t ph[8], pl[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       uint32_t wh = 0, wl = 0;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        // one FP64 operation per element (the FP64 pipe is the scarce one):
-        // xf = fl32(x); hi = bf16(xf); xf - hi is exact in FP32; lo = bf16(xf - hi)
-        const float xf = (float)t[qq + 2 * j + k][ar];
-        const __nv_bfloat16 xh = __float2bfloat16_rn(xf);
-        const __nv_bfloat16 xl = __float2bfloat16_rn(xf - __bfloat162float(xh));
+        const float f = xf[2 * j + k];
+        const __nv_bfloat16 xh = __float2bfloat16_rn(f);
+        const __nv_bfloat16 xl = __float2bfloat16_rn(f - __bfloat162float(xh));
         wh |= (uint32_t)__bfloat16_as_ushort(xh) << (16 * k);
         wl |= (uint32_t)__bfloat16_as_ushort(xl) << (16 * k);
       }
@@ -933,9 +940,8 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const double* __restr
       float vh[4], vl[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float xf = (float)t[qq + 4 * j + k][ar];
-        vh[k] = tf32_rne(xf);
-        vl[k] = tf32_rne(xf - vh[k]);  // exact in FP32
+        vh[k] = tf32_rne(xf[4 * j + k]);
+        vl[k] = tf32_rne(xf[4 * j + k] - vh[k]);  // exact in FP32
       }
       dh[j] = make_float4(vh[0], vh[1], vh[2], vh[3]);
       dl[j] = make_float4(vl[0], vl[1], vl[2], vl[3]);
@@ -1416,7 +1422,7 @@ cudaError_t split_stage_rows(dsrg_plan* p, const double* B, int h0, int h1) {
   SplitWs* w = p->split;
   const Sizes& z = p->z;
   if (h1 <= h0) return cudaSuccess;
-  dim3 grid(w->Qpad / 64, w->nVpad / 64, h1 - h0);
+  dim3 grid((w->Qpad + 127) / 128, w->nVpad / 32, h1 - h0);
   if (p->prec == DSRG_PREC_BF16X3)
     split_planes_kernel<true><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qld, w->hi, w->lo,
                                                            w->tail, h0);
@@ -1588,7 +1594,7 @@ cudaError_t split_launch_ccvv_adjoint(dsrg_plan* p, const double* B, const doubl
   const Sizes& z = p->z;
   if (!w->adj_ready) return cudaErrorInvalidValue;
   if (p->prec == DSRG_PREC_BF16X3) {
-    dim3 grid(w->Qpad / 64, w->nVpad / 64, z.nC);
+    dim3 grid((w->Qpad + 127) / 128, w->nVpad / 32, z.nC);
     // the tail rows are rewritten with the same fl32(B) values
     split_planes_kernel<false><<<grid, 256, 0, p->stream>>>(B, z, w->nVpad, w->Qpad, w->adj_hi,
                                                             w->adj_lo, w->tail, 0);
